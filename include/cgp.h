@@ -1,0 +1,182 @@
+/*
+ * cgp.h -- C ABI of the GB300 coarse-grid incremental pressure-projection (CGP) library.
+ *
+ * The library advances the incompressible Navier-Stokes equations (paper Eqs. 1-4)
+ * with the incremental pressure-correction scheme of Section 2.1 (BDF2, Eqs. 5-16)
+ * discretised by P1/P1 finite elements (Eqs. 17-20), solving the Poisson problem for
+ * the pressure increment phi on a mesh k levels coarser than the velocity mesh
+ * (Section 2.2, Eqs. 21-26).  All arithmetic of a time step runs in CUDA kernels on
+ * one GPU; the host only enqueues work.
+ *
+ * Conventions shared by every entry point
+ *  - Return value: CGP_OK (0) or a negative CGP_E* code; nothing throws across the ABI.
+ *    cgp_last_error() gives a message for the last failure on the calling thread.
+ *  - Streams: a cudaStream_t passed as cgp_stream_t (NULL = the legacy default stream).
+ *    Calls enqueue work on it and return without synchronising unless stated.
+ *  - Memory: inputs are copied; the caller keeps ownership of every pointer it passes.
+ *    A mesh owns device memory it allocates itself; a solver lives entirely inside the
+ *    caller-supplied workspace (cgp_workspace_size bytes, 256-byte aligned, device
+ *    memory) and allocates nothing else on the device.
+ *  - `where` arguments: CGP_HOST = pointer is host memory (the call synchronises the
+ *    stream), CGP_DEVICE = pointer is device memory (the call only enqueues copies).
+ *  - Vertex order: level l's vertices are the first N_l vertices of level l+1; fields
+ *    are returned in the finest level's order.  Velocities are interleaved (u0,v0,u1,...).
+ */
+#ifndef CGP_H
+#define CGP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct cgp_mesh cgp_mesh;      /* opaque, library-owned */
+typedef struct cgp_solver cgp_solver;  /* opaque, lives in caller workspace */
+typedef struct CUstream_st* cgp_stream_t;  /* identical to cudaStream_t */
+
+enum {
+    CGP_OK = 0,
+    CGP_EINVAL = -1,      /* bad mesh, parameters or arguments */
+    CGP_ENOTCONV = -2,    /* an iterative solve hit its iteration cap (the step completed with its last iterate) */
+    CGP_EBREAKDOWN = -3,  /* a Krylov recurrence broke down (zero denominator) */
+    CGP_ENONFINITE = -4,  /* a residual became NaN or Inf */
+    CGP_ETIMEOUT = -5,    /* a bounded device wait expired */
+    CGP_ECUDA = -6,       /* a CUDA runtime call failed */
+    CGP_ENOMEM = -7       /* workspace too small / allocation failed */
+};
+
+/* per-vertex boundary flags (bitwise OR); see cgp_mesh_desc */
+enum { CGP_VEL_DIR = 1, CGP_PHI_ZERO = 2 };
+
+/* built-in problem statements (boundary data, body force, initial state) */
+enum {
+    CGP_BC_CAVITY = 0,       /* [0,1]^2, u=(bc_param[0],0) on y=1 with 0<x<1, u=0 on the rest of the boundary */
+    CGP_BC_CHANNEL = 1,      /* u=(4 Umax y(H-y)/H^2, 0) on x=0 (Umax=bc_param[0], H=bc_param[1]), u=0 elsewhere on VEL_DIR */
+    CGP_BC_TG = 2,           /* Taylor-Green vortex, paper Eqs. 28-30 */
+    CGP_BC_TG_PERIODIC = 3   /* Taylor-Green with amplitude cos(2 pi t) and the body force that makes it exact */
+};
+enum { CGP_FP64 = 0, CGP_MIXED = 1 };                   /* precision of the coarse Poisson solve */
+enum { CGP_GUESS_ZERO = 0, CGP_GUESS_PREV = 1 };          /* initial guess of the coarse Poisson solve */
+enum { CGP_MASS_CONSISTENT = 0, CGP_MASS_LUMPED = 1 };    /* mass matrix of Eqs. 25-26 (lumped = Eq. 27) */
+enum { CGP_HOST = 0, CGP_DEVICE = 1 };
+
+/* Base (coarsest) mesh.  All pointers are host memory, read during cgp_mesh_create.
+ * Triangles must be counter-clockwise with positive area; every vertex must be used.
+ * vert_tag: CGP_VEL_DIR marks the Dirichlet velocity boundary Gamma_D (Eqs. 3, 10);
+ * CGP_PHI_ZERO marks vertices where phi = 0 (the traction boundary Gamma_N, Eq. 14).
+ * n_levels (0..4) uniform 1->4 refinements are built (Section 2.2). */
+typedef struct {
+    int32_t n_vert, n_tri;
+    const double* xy;          /* 2*n_vert, interleaved */
+    const int32_t* tri;        /* 3*n_tri */
+    const uint8_t* vert_tag;   /* n_vert */
+    int32_t n_levels;
+} cgp_mesh_desc;
+
+/* Parameters of a run (paper Section 3's Re, delta t, chi and coarsening level k). */
+typedef struct {
+    double Re, dt;
+    int32_t chi;               /* 0 = standard form, 1 = rotational form (Eq. 16 / Eq. 26) */
+    int32_t k;                 /* pressure-increment mesh = finest level - k (0 <= k <= n_levels) */
+    double tol_mom;            /* relative residual of the momentum solve (Eq. 21) */
+    double tol_poisson;        /* relative residual of the coarse Poisson solve (Eq. 23) */
+    double tol_mass;           /* relative residual of the mass-matrix solves (Eqs. 25, 26) */
+    int32_t max_it_mom, max_it_poisson, max_it_mass;
+    int32_t precision;         /* CGP_FP64 | CGP_MIXED */
+    int32_t guess;             /* CGP_GUESS_* */
+    int32_t mass_mode;         /* CGP_MASS_* */
+    int32_t bc_kind;           /* CGP_BC_* */
+    double bc_param[4];
+    int32_t use_graph;         /* 1: replay each step as a CUDA graph with device-side loop control */
+} cgp_params;
+
+/* Per-run statistics. */
+typedef struct {
+    int64_t steps;             /* steps taken since assembly / cgp_set_fields */
+    double t;                  /* current time */
+    int32_t it_mom, it_poisson, it_corr, it_mass;          /* iterations of the last step */
+    int64_t sum_it_mom, sum_it_poisson, sum_it_corr, sum_it_mass;
+    double res_mom, res_poisson;                           /* last relative residuals (max over components) */
+    int32_t status;            /* first non-zero CGP_E* code seen by any solve, else 0 */
+} cgp_stats;
+
+/* Library message for the last failing call of this thread ("" if none). */
+const char* cgp_last_error(void);
+
+/* ---- mesh hierarchy (Section 2.2: V_1 c ... c V_{n_levels+1} by subdividing each
+ * triangle into four).  Vertex N_l + e of level l+1 is the midpoint of edge e of
+ * level l, edges ranked by ascending (min vertex, max vertex); triangle t=(a,b,c)
+ * has children 4t+0=(a,m_ab,m_ca), 4t+1=(m_ab,b,m_bc), 4t+2=(m_ca,m_bc,c),
+ * 4t+3=(m_ab,m_bc,m_ca); a midpoint of a boundary edge gets the AND of its end
+ * flags, of an interior edge 0.  Built on the device; synchronises `stream`. */
+int cgp_mesh_create(const cgp_mesh_desc* desc, cgp_stream_t stream, cgp_mesh** out);
+/* Sizes of level `level` (0 = base).  nnz = entries of its vertex-adjacency CSR. */
+int cgp_mesh_level_info(const cgp_mesh* mesh, int32_t level, int32_t* n_vert, int32_t* n_tri, int64_t* nnz);
+/* Copy level arrays to host buffers (any may be NULL; synchronises).  parents holds
+ * the 2 end points of each vertex added at this level (2*(N_l - N_{l-1}) ints). */
+int cgp_mesh_get_level(const cgp_mesh* mesh, int32_t level, double* xy, int32_t* tri, uint8_t* tag,
+                       int32_t* rowptr, int32_t* col, int32_t* parents);
+void cgp_mesh_destroy(cgp_mesh* mesh);
+
+/* ---- solver ---- */
+/* Workspace bytes cgp_assemble needs for this mesh and parameters. */
+int cgp_workspace_size(const cgp_mesh* mesh, const cgp_params* params, size_t* bytes);
+/* Assemble the static P1 operators (Eqs. 17-20) on the velocity level and, by
+ * rediscretisation, on the pressure-increment level (Section 2.2), and set the
+ * initial state of the problem kind.  workspace: device memory of at least
+ * cgp_workspace_size bytes that must outlive the solver.  The mesh must outlive it too. */
+int cgp_assemble(const cgp_mesh* mesh, const cgp_params* params, void* workspace, size_t ws_bytes,
+                 cgp_stream_t stream, cgp_solver** out);
+/* Replace the state: U (2*N_f), Uprev (2*N_f, may be NULL = U), P (N_f), time t. */
+int cgp_set_fields(cgp_solver* s, const double* U, const double* Uprev, const double* P, double t,
+                   int32_t where, cgp_stream_t stream);
+/* Advance n_steps time steps, each Eqs. 21-26: momentum solve on the fine level,
+ * injection to the pressure level, coarse Poisson solve for phi, prolongation,
+ * velocity correction and pressure update (chi = 0: P += phi_f; chi = 1: the
+ * consistent-mass rotational update of Eq. 26).  Asynchronous; solver status is
+ * latched on the device and reported by cgp_get_fields. */
+int cgp_step(cgp_solver* s, int32_t n_steps, cgp_stream_t stream);
+/* Copy U (2*N_f) and P (N_f) (either may be NULL) and the stats; synchronises. Returns
+ * the latched solver status (CGP_OK, CGP_ENOTCONV, ...) after a successful copy. */
+int cgp_get_fields(cgp_solver* s, double* U, double* P, double* t, cgp_stats* stats,
+                   int32_t where, cgp_stream_t stream);
+
+/* Intermediate vectors of the last step (for checking each equation separately). */
+enum {
+    CGP_VEC_U = 0,        /* 2*N_f  U^{n+1} */
+    CGP_VEC_UPREV = 1,    /* 2*N_f  U^n */
+    CGP_VEC_P = 2,        /* N_f    P^{n+1} */
+    CGP_VEC_UTILDE = 3,   /* 2*N_f  intermediate velocity of Eq. 21 */
+    CGP_VEC_RHS_C = 4,    /* N_c    right-hand side of Eq. 23 (after the range projection) */
+    CGP_VEC_PHI_C = 5,    /* N_c    coarse solution of Eq. 23 (after the mean fix) */
+    CGP_VEC_PHI_F = 6     /* N_f    prolonged increment of Eq. 24 */
+};
+int cgp_get_vector(cgp_solver* s, int32_t which, double* out, int32_t where, cgp_stream_t stream);
+/* Overwrite U, UPREV, P or PHI_C (the previous coarse increment, which is the initial
+ * guess of the next Poisson solve under CGP_GUESS_PREV): restores a checkpoint. */
+int cgp_set_vector(cgp_solver* s, int32_t which, const double* in, int32_t where, cgp_stream_t stream);
+/* Values of a static operator on its level's CSR pattern (cgp_mesh_get_level). */
+enum { CGP_MAT_M = 0, CGP_MAT_K = 1, CGP_MAT_CX = 2, CGP_MAT_CY = 3,      /* velocity level */
+       CGP_MAT_KC = 4, CGP_MAT_CXC = 5, CGP_MAT_CYC = 6,                   /* pressure level */
+       CGP_MAT_A = 7 };                                                    /* last momentum matrix */
+int cgp_get_matrix(cgp_solver* s, int32_t which, double* vals, int32_t where, cgp_stream_t stream);
+/* Sizes: fine/coarse vertex counts and the CSR entry counts of both levels. */
+int cgp_solver_info(const cgp_solver* s, int32_t* n_fine, int32_t* n_coarse, int64_t* nnz_fine, int64_t* nnz_coarse);
+
+/* Eq. 23 alone: solve K_c phi = rhs (N_c values; phi=0 rows and the pure-Neumann
+ * projection/mean fix as in a step) with the configured precision and tolerance.
+ * phi also gives the initial guess when params.guess = CGP_GUESS_PREV.
+ * Returns the solve status; iterations through *iters (may be NULL). Synchronises. */
+int cgp_poisson_solve(cgp_solver* s, const double* rhs, double* phi, int32_t* iters,
+                      int32_t where, cgp_stream_t stream);
+/* Eq. 24 alone: phi_f (N_f) = prolongation of phi_c (N_c) over the k levels. */
+int cgp_prolong(cgp_solver* s, const double* phi_c, double* phi_f, int32_t where, cgp_stream_t stream);
+
+void cgp_solver_destroy(cgp_solver* s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CGP_H */

@@ -1,0 +1,342 @@
+"""Thin ctypes binding of ``include/cgp.h`` (argument marshalling only).
+
+The functions below carry the C names and call straight into ``libcgp.so``; every
+step of the method runs in the library's CUDA kernels.  PyTorch is used only for
+device memory (the solver workspace) and for the current CUDA stream.  If the
+library has not been built, :func:`load` raises: there is no fallback path.
+"""
+
+import ctypes
+import os
+from ctypes import POINTER, byref, c_double, c_int32, c_int64, c_size_t, c_uint8, c_void_p
+
+import numpy as np
+
+from . import build as _build
+
+CGP_OK, CGP_EINVAL, CGP_ENOTCONV, CGP_EBREAKDOWN, CGP_ENONFINITE, CGP_ETIMEOUT, CGP_ECUDA, CGP_ENOMEM = \
+    0, -1, -2, -3, -4, -5, -6, -7
+CGP_VEL_DIR, CGP_PHI_ZERO = 1, 2
+CGP_BC_CAVITY, CGP_BC_CHANNEL, CGP_BC_TG, CGP_BC_TG_PERIODIC = 0, 1, 2, 3
+CGP_FP64, CGP_MIXED = 0, 1
+CGP_GUESS_ZERO, CGP_GUESS_PREV = 0, 1
+CGP_MASS_CONSISTENT, CGP_MASS_LUMPED = 0, 1
+CGP_HOST, CGP_DEVICE = 0, 1
+(CGP_VEC_U, CGP_VEC_UPREV, CGP_VEC_P, CGP_VEC_UTILDE, CGP_VEC_RHS_C, CGP_VEC_PHI_C,
+ CGP_VEC_PHI_F) = range(7)
+(CGP_MAT_M, CGP_MAT_K, CGP_MAT_CX, CGP_MAT_CY, CGP_MAT_KC, CGP_MAT_CXC, CGP_MAT_CYC,
+ CGP_MAT_A) = range(8)
+
+_ERRNAMES = {0: "CGP_OK", -1: "CGP_EINVAL", -2: "CGP_ENOTCONV", -3: "CGP_EBREAKDOWN",
+             -4: "CGP_ENONFINITE", -5: "CGP_ETIMEOUT", -6: "CGP_ECUDA", -7: "CGP_ENOMEM"}
+
+
+class CgpError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s (%d): %s" % (_ERRNAMES.get(code, "?"), code, msg))
+        self.code = code
+
+
+class MeshDesc(ctypes.Structure):
+    _fields_ = [("n_vert", c_int32), ("n_tri", c_int32), ("xy", POINTER(c_double)),
+                ("tri", POINTER(c_int32)), ("vert_tag", POINTER(c_uint8)), ("n_levels", c_int32)]
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("Re", c_double), ("dt", c_double), ("chi", c_int32), ("k", c_int32),
+                ("tol_mom", c_double), ("tol_poisson", c_double), ("tol_mass", c_double),
+                ("max_it_mom", c_int32), ("max_it_poisson", c_int32), ("max_it_mass", c_int32),
+                ("precision", c_int32), ("guess", c_int32), ("mass_mode", c_int32), ("bc_kind", c_int32),
+                ("bc_param", c_double * 4), ("use_graph", c_int32)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("steps", c_int64), ("t", c_double), ("it_mom", c_int32), ("it_poisson", c_int32),
+                ("it_corr", c_int32), ("it_mass", c_int32), ("sum_it_mom", c_int64),
+                ("sum_it_poisson", c_int64), ("sum_it_corr", c_int64), ("sum_it_mass", c_int64),
+                ("res_mom", c_double), ("res_poisson", c_double), ("status", c_int32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_SIGS = {
+    "cgp_last_error": (ctypes.c_char_p, []),
+    "cgp_mesh_create": (c_int32, [POINTER(MeshDesc), c_void_p, POINTER(c_void_p)]),
+    "cgp_mesh_level_info": (c_int32, [c_void_p, c_int32, POINTER(c_int32), POINTER(c_int32), POINTER(c_int64)]),
+    "cgp_mesh_get_level": (c_int32, [c_void_p, c_int32, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
+                                     c_void_p]),
+    "cgp_mesh_destroy": (None, [c_void_p]),
+    "cgp_workspace_size": (c_int32, [c_void_p, POINTER(Params), POINTER(c_size_t)]),
+    "cgp_assemble": (c_int32, [c_void_p, POINTER(Params), c_void_p, c_size_t, c_void_p, POINTER(c_void_p)]),
+    "cgp_set_fields": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_double, c_int32, c_void_p]),
+    "cgp_step": (c_int32, [c_void_p, c_int32, c_void_p]),
+    "cgp_get_fields": (c_int32, [c_void_p, c_void_p, c_void_p, POINTER(c_double), POINTER(Stats), c_int32,
+                                 c_void_p]),
+    "cgp_get_vector": (c_int32, [c_void_p, c_int32, c_void_p, c_int32, c_void_p]),
+    "cgp_set_vector": (c_int32, [c_void_p, c_int32, c_void_p, c_int32, c_void_p]),
+    "cgp_get_matrix": (c_int32, [c_void_p, c_int32, c_void_p, c_int32, c_void_p]),
+    "cgp_solver_info": (c_int32, [c_void_p, POINTER(c_int32), POINTER(c_int32), POINTER(c_int64),
+                                  POINTER(c_int64)]),
+    "cgp_poisson_solve": (c_int32, [c_void_p, c_void_p, c_void_p, POINTER(c_int32), c_int32, c_void_p]),
+    "cgp_prolong": (c_int32, [c_void_p, c_void_p, c_void_p, c_int32, c_void_p]),
+    "cgp_solver_destroy": (None, [c_void_p]),
+}
+
+_LIB = None
+
+
+def load(build_if_missing=True):
+    """Load libcgp.so (building it first if asked); raises if it cannot be had."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    path = _build.LIB
+    if build_if_missing:
+        path = _build.build()
+    if not os.path.exists(path):
+        raise RuntimeError("libcgp.so is not built (run __graft_entry__.build())")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in _SIGS.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _LIB = lib
+    return lib
+
+
+def exported_symbols():
+    return list(_SIGS)
+
+
+def _check(rc, allow=()):
+    if rc != CGP_OK and rc not in allow:
+        raise CgpError(rc, load().cgp_last_error().decode())
+    return rc
+
+
+def _ptr(a):
+    """Device or host address of a torch tensor / numpy array (None -> NULL)."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        return c_void_p(a.data_ptr())
+    return a.ctypes.data_as(c_void_p)
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return c_void_p(torch.cuda.current_stream().cuda_stream)
+    if hasattr(stream, "cuda_stream"):
+        return c_void_p(stream.cuda_stream)
+    return c_void_p(stream)
+
+
+# ---------------------------------------------------------------- C-named wrappers
+def cgp_last_error():
+    return load().cgp_last_error().decode()
+
+
+def cgp_mesh_create(xy, tri, tag, n_levels, stream=None):
+    xy = np.ascontiguousarray(xy, dtype=np.float64)
+    tri = np.ascontiguousarray(tri, dtype=np.int32)
+    tag = np.ascontiguousarray(tag, dtype=np.uint8)
+    d = MeshDesc(int(xy.shape[0]), int(tri.shape[0]), xy.ctypes.data_as(POINTER(c_double)),
+                 tri.ctypes.data_as(POINTER(c_int32)), tag.ctypes.data_as(POINTER(c_uint8)), int(n_levels))
+    out = c_void_p()
+    _check(load().cgp_mesh_create(byref(d), _stream(stream), byref(out)))
+    return out
+
+
+def cgp_mesh_level_info(mesh, level):
+    nv, nt, nnz = c_int32(), c_int32(), c_int64()
+    _check(load().cgp_mesh_level_info(mesh, level, byref(nv), byref(nt), byref(nnz)))
+    return nv.value, nt.value, nnz.value
+
+
+def cgp_mesh_get_level(mesh, level):
+    nv, nt, nnz = cgp_mesh_level_info(mesh, level)
+    nv_prev = cgp_mesh_level_info(mesh, level - 1)[0] if level > 0 else nv
+    xy = np.empty((nv, 2)); tri = np.empty((nt, 3), np.int32); tag = np.empty(nv, np.uint8)
+    rp = np.empty(nv + 1, np.int32); col = np.empty(nnz, np.int32)
+    par = np.empty((max(nv - nv_prev, 0), 2), np.int32)
+    _check(load().cgp_mesh_get_level(mesh, level, _ptr(xy), _ptr(tri), _ptr(tag), _ptr(rp), _ptr(col),
+                                     _ptr(par) if level > 0 else None))
+    return {"xy": xy, "tri": tri, "tag": tag, "rowptr": rp, "col": col, "parents": par}
+
+
+def cgp_mesh_destroy(mesh):
+    load().cgp_mesh_destroy(mesh)
+
+
+def make_params(Re, dt, chi=0, k=1, tol_mom=1e-10, tol_poisson=1e-10, tol_mass=1e-12, max_it_mom=500,
+                max_it_poisson=20000, max_it_mass=500, precision=CGP_FP64, guess=CGP_GUESS_PREV,
+                mass_mode=CGP_MASS_CONSISTENT, bc_kind=CGP_BC_CAVITY, bc_param=(1.0, 0.0, 0.0, 0.0),
+                use_graph=1):
+    p = Params()
+    p.Re, p.dt, p.chi, p.k = Re, dt, chi, k
+    p.tol_mom, p.tol_poisson, p.tol_mass = tol_mom, tol_poisson, tol_mass
+    p.max_it_mom, p.max_it_poisson, p.max_it_mass = max_it_mom, max_it_poisson, max_it_mass
+    p.precision, p.guess, p.mass_mode, p.bc_kind = precision, guess, mass_mode, bc_kind
+    for i in range(4):
+        p.bc_param[i] = bc_param[i] if i < len(bc_param) else 0.0
+    p.use_graph = use_graph
+    return p
+
+
+def cgp_workspace_size(mesh, params):
+    n = c_size_t()
+    _check(load().cgp_workspace_size(mesh, byref(params), byref(n)))
+    return n.value
+
+
+def cgp_assemble(mesh, params, workspace, stream=None):
+    out = c_void_p()
+    nbytes = workspace.numel() * workspace.element_size()
+    _check(load().cgp_assemble(mesh, byref(params), _ptr(workspace), nbytes, _stream(stream), byref(out)))
+    return out
+
+
+def cgp_set_fields(solver, U, Uprev, P, t, where=CGP_HOST, stream=None):
+    if where == CGP_HOST:
+        U = np.ascontiguousarray(U, dtype=np.float64)
+        Uprev = None if Uprev is None else np.ascontiguousarray(Uprev, dtype=np.float64)
+        P = np.ascontiguousarray(P, dtype=np.float64)
+    _check(load().cgp_set_fields(solver, _ptr(U), _ptr(Uprev), _ptr(P), float(t), where, _stream(stream)))
+
+
+def cgp_step(solver, n_steps, stream=None):
+    _check(load().cgp_step(solver, int(n_steps), _stream(stream)))
+
+
+def cgp_get_fields(solver, U=None, P=None, where=CGP_HOST, stream=None, allow=(CGP_ENOTCONV,)):
+    """Returns (U, P, t, stats, status).  With where=CGP_HOST new numpy arrays are made."""
+    nf = cgp_solver_info(solver)[0]
+    if where == CGP_HOST:
+        U = np.empty((nf, 2)) if U is None else U
+        P = np.empty(nf) if P is None else P
+    t = c_double()
+    st = Stats()
+    rc = load().cgp_get_fields(solver, _ptr(U), _ptr(P), byref(t), byref(st), where, _stream(stream))
+    if rc == CGP_ECUDA or rc == CGP_EINVAL:
+        _check(rc)
+    _check(rc, allow=allow)
+    return U, P, t.value, st.as_dict(), rc
+
+
+def cgp_solver_info(solver):
+    nf, nc, zf, zc = c_int32(), c_int32(), c_int64(), c_int64()
+    _check(load().cgp_solver_info(solver, byref(nf), byref(nc), byref(zf), byref(zc)))
+    return nf.value, nc.value, zf.value, zc.value
+
+
+def cgp_get_vector(solver, which, stream=None):
+    nf, nc, _, _ = cgp_solver_info(solver)
+    n = {CGP_VEC_U: 2 * nf, CGP_VEC_UPREV: 2 * nf, CGP_VEC_P: nf, CGP_VEC_UTILDE: 2 * nf,
+         CGP_VEC_RHS_C: nc, CGP_VEC_PHI_C: nc, CGP_VEC_PHI_F: nf}[which]
+    out = np.empty(n)
+    _check(load().cgp_get_vector(solver, which, _ptr(out), CGP_HOST, _stream(stream)))
+    return out.reshape(-1, 2) if n == 2 * nf and which in (CGP_VEC_U, CGP_VEC_UPREV, CGP_VEC_UTILDE) else out
+
+
+def cgp_set_vector(solver, which, data, stream=None):
+    data = np.ascontiguousarray(data, dtype=np.float64)
+    _check(load().cgp_set_vector(solver, which, _ptr(data), CGP_HOST, _stream(stream)))
+
+
+def cgp_get_matrix(solver, which, stream=None):
+    nf, nc, zf, zc = cgp_solver_info(solver)
+    out = np.empty(zc if which in (CGP_MAT_KC, CGP_MAT_CXC, CGP_MAT_CYC) else zf)
+    _check(load().cgp_get_matrix(solver, which, _ptr(out), CGP_HOST, _stream(stream)))
+    return out
+
+
+def cgp_poisson_solve(solver, rhs, phi0=None, stream=None, allow=(CGP_ENOTCONV,)):
+    nc = cgp_solver_info(solver)[1]
+    rhs = np.ascontiguousarray(rhs, dtype=np.float64)
+    phi = np.zeros(nc) if phi0 is None else np.array(phi0, dtype=np.float64)
+    it = c_int32()
+    rc = load().cgp_poisson_solve(solver, _ptr(rhs), _ptr(phi), byref(it), CGP_HOST, _stream(stream))
+    _check(rc, allow=allow)
+    return phi, it.value, rc
+
+
+def cgp_prolong(solver, phi_c, stream=None):
+    nf, nc, _, _ = cgp_solver_info(solver)
+    phi_c = np.ascontiguousarray(phi_c, dtype=np.float64)
+    out = np.empty(nf)
+    _check(load().cgp_prolong(solver, _ptr(phi_c), _ptr(out), CGP_HOST, _stream(stream)))
+    return out
+
+
+def cgp_solver_destroy(solver):
+    load().cgp_solver_destroy(solver)
+
+
+# ---------------------------------------------------------------- convenience objects
+class Mesh:
+    """Owns a cgp_mesh built from a base mesh (xy, tri, tag) with n_levels refinements."""
+
+    def __init__(self, xy, tri, tag, n_levels, stream=None):
+        self.handle = cgp_mesh_create(xy, tri, tag, n_levels, stream)
+        self.n_levels = n_levels
+
+    def level(self, l):
+        return cgp_mesh_get_level(self.handle, l)
+
+    def info(self, l):
+        return cgp_mesh_level_info(self.handle, l)
+
+    def close(self):
+        if self.handle:
+            cgp_mesh_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Solver:
+    """Owns a cgp_solver and its torch-allocated device workspace."""
+
+    def __init__(self, mesh, params, stream=None):
+        import torch
+        self.mesh = mesh
+        self.params = params
+        nbytes = cgp_workspace_size(mesh.handle, params)
+        self.workspace = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+        self.handle = cgp_assemble(mesh.handle, params, self.workspace, stream)
+        self.nf, self.nc, self.nnzf, self.nnzc = cgp_solver_info(self.handle)
+
+    def step(self, n=1, stream=None):
+        cgp_step(self.handle, n, stream)
+
+    def fields(self, stream=None):
+        return cgp_get_fields(self.handle, stream=stream)
+
+    def vector(self, which):
+        return cgp_get_vector(self.handle, which)
+
+    def matrix(self, which):
+        return cgp_get_matrix(self.handle, which)
+
+    def set_fields(self, U, Uprev, P, t):
+        cgp_set_fields(self.handle, U, Uprev, P, t)
+
+    def set_vector(self, which, data):
+        cgp_set_vector(self.handle, which, data)
+
+    def close(self):
+        if self.handle:
+            cgp_solver_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,668 @@
+// One CGP time step on the device (paper Section 2.2, Eqs. 21-26) and its host
+// orchestration: eager launches with host-polled loop control, or a CUDA graph whose
+// Krylov loops are conditional WHILE nodes driven by the kernels themselves.
+#include <cstring>
+
+#include "flows.cuh"
+#include "solver.cuh"
+
+namespace cgp {
+
+constexpr int kLanes = 8;   // lanes per CSR row in the SpMV kernels
+
+// ---------------------------------------------------------------- per-vertex kernels
+__global__ void k_init_state(int nf, const double* __restrict__ xy, const uint8_t* __restrict__ tag, BcParams bc,
+                             double dt, double* __restrict__ U, double* __restrict__ Uprev, double* __restrict__ P,
+                             double* __restrict__ tdev) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i == 0) *tdev = 0.0;
+    if (i >= nf) return;
+    const double x = xy[2 * i], y = xy[2 * i + 1];
+    double u, v, p;
+    if (exact_field(bc, x, y, 0.0, u, v, p)) {
+        U[2 * i] = u;
+        U[2 * i + 1] = v;
+        P[i] = p;
+        exact_field(bc, x, y, -dt, u, v, p);
+        Uprev[2 * i] = u;
+        Uprev[2 * i + 1] = v;
+        return;
+    }
+    u = v = 0.0;
+    if (tag[i] & CGP_VEL_DIR) dirichlet_value(bc, x, y, 0.0, u, v);
+    U[2 * i] = Uprev[2 * i] = u;
+    U[2 * i + 1] = Uprev[2 * i + 1] = v;
+    P[i] = 0.0;
+}
+
+// w = 2 U^n - U^{n-1} (Eq. 5's extrapolated advecting field), h = dt F^{n+1} + 2 U^n - 1/2 U^{n-1}
+__global__ void k_mom_prep(int nf, const double* __restrict__ U, const double* __restrict__ Uprev,
+                           const double* __restrict__ xy, BcParams bc, const double* __restrict__ tdev, double dt,
+                           double* __restrict__ w, double* __restrict__ h) {
+    const double tn = *tdev + dt;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nf; i += gridDim.x * blockDim.x) {
+        double2 u = reinterpret_cast<const double2*>(U)[i];
+        double2 up = reinterpret_cast<const double2*>(Uprev)[i];
+        double fx = 0.0, fy = 0.0;
+        if (bc.kind == CGP_BC_TG_PERIODIC) body_force(bc, xy[2 * i], xy[2 * i + 1], tn, fx, fy);
+        reinterpret_cast<double2*>(w)[i] = make_double2(2.0 * u.x - up.x, 2.0 * u.y - up.y);
+        reinterpret_cast<double2*>(h)[i] =
+            make_double2(dt * fx + (2.0 * u.x - 0.5 * up.x), dt * fy + (2.0 * u.y - 0.5 * up.y));
+    }
+}
+
+// Row i of the momentum system of Eq. 21:
+//   A = 3/2 M + dt N(w) + dt/Re K,  N_ij = sum_T |T|/12 (W_T + w_i) . grad psi_j
+//   b = dt (Cx^T P, Cy^T P) + M h     (pressure term in weak form, see the readings)
+// Dirichlet rows: identity row, b = u_D(t^{n+1}).  Also x0 = w (u_D on Dirichlet rows), dinv.
+__global__ void k_mom_assemble(int nf, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                               const int32_t* __restrict__ vt_ptr, const int32_t* __restrict__ vt_list,
+                               const int32_t* __restrict__ tri, const double* __restrict__ geo,
+                               const int32_t* __restrict__ vtslot, const double* __restrict__ S,
+                               const double* __restrict__ M, const double* __restrict__ CxT,
+                               const double* __restrict__ CyT, const double* __restrict__ P,
+                               const double* __restrict__ w, const double* __restrict__ h,
+                               const uint8_t* __restrict__ tag, const double* __restrict__ xy, BcParams bc,
+                               const double* __restrict__ tdev, double dt, double* __restrict__ A,
+                               double* __restrict__ dinv, double* __restrict__ b, double* __restrict__ x0) {
+    const double tn = *tdev + dt;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nf; i += gridDim.x * blockDim.x) {
+        const int rb = rowptr[i], re = rowptr[i + 1];
+        if (tag[i] & CGP_VEL_DIR) {
+            for (int q = rb; q < re; ++q) A[q] = col[q] == i ? 1.0 : 0.0;
+            dinv[i] = 1.0;
+            double u, v;
+            dirichlet_value(bc, xy[2 * i], xy[2 * i + 1], tn, u, v);
+            reinterpret_cast<double2*>(b)[i] = make_double2(u, v);
+            reinterpret_cast<double2*>(x0)[i] = make_double2(u, v);
+            continue;
+        }
+        double bx = 0.0, by = 0.0;
+        for (int q = rb; q < re; ++q) {
+            A[q] = S[q];
+            const int j = col[q];
+            const double2 hj = reinterpret_cast<const double2*>(h)[j];
+            const double pj = P[j];
+            bx += dt * CxT[q] * pj + M[q] * hj.x;
+            by += dt * CyT[q] * pj + M[q] * hj.y;
+        }
+        const double2 wi = reinterpret_cast<const double2*>(w)[i];
+        int diag_slot = 0;
+        for (int m = vt_ptr[i]; m < vt_ptr[i + 1]; ++m) {
+            const int t = vt_list[m];
+            const int packed = vtslot[m];
+            const double* gt = geo + 7 * (int64_t)t;
+            const int a0 = tri[3 * t], a1 = tri[3 * t + 1], a2 = tri[3 * t + 2];
+            const double2 w0 = reinterpret_cast<const double2*>(w)[a0];
+            const double2 w1 = reinterpret_cast<const double2*>(w)[a1];
+            const double2 w2 = reinterpret_cast<const double2*>(w)[a2];
+            const double c = gt[0] / 12.0;
+            const double cx = c * (w0.x + w1.x + w2.x + wi.x), cy = c * (w0.y + w1.y + w2.y + wi.y);
+            const int li = packed & 3;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                const int slot = (packed >> (8 * (k + 1))) & 255;
+                A[rb + slot] += dt * (cx * gt[1 + 2 * k] + cy * gt[2 + 2 * k]);
+                if (k == li) diag_slot = slot;
+            }
+        }
+        dinv[i] = 1.0 / A[rb + diag_slot];
+        reinterpret_cast<double2*>(b)[i] = make_double2(bx, by);
+        reinterpret_cast<double2*>(x0)[i] = wi;
+    }
+}
+
+// Eqs. 22-23: r_i = -3/(2 dt) (Cx_c u~ + Cy_c v~)_i at coarse vertex i (the injected
+// U~ is the first N_c entries of the fine U~); r = 0 where phi = 0; mean for the projection.
+template <int LANES_>
+__global__ void __launch_bounds__(kBlock) k_coarse_rhs(CsrView Ac, const double* __restrict__ Cxc,
+                                                      const double* __restrict__ Cyc, const double* __restrict__ Ut,
+                                                      const uint8_t* __restrict__ tag, double dt,
+                                                      double* __restrict__ rc, KrylovState* st, int pure_neumann,
+                                                      double* partials, unsigned int* ticket) {
+    RowGroups<LANES_> rg;
+    double acc[1] = {0.0};
+    CGP_ROW_LOOP(rg, Ac.n, i) {
+        double s = 0.0;
+        const bool live = i < Ac.n;
+        if (live) {
+            for (int j = Ac.rowptr[i] + rg.sub; j < Ac.rowptr[i + 1]; j += LANES_) {
+                const double2 u = reinterpret_cast<const double2*>(Ut)[Ac.col[j]];
+                s += Cxc[j] * u.x + Cyc[j] * u.y;
+            }
+        }
+        s = group_sum<LANES_>(s);
+        if (live && rg.sub == 0) {
+            double r = (tag[i] & CGP_PHI_ZERO) ? 0.0 : -1.5 / dt * s;
+            rc[i] = r;
+            acc[0] += r;
+        }
+    }
+    double tot[1];
+    if (grid_sum<1>(acc, partials, ticket, tot) && threadIdx.x == 0) st->mean = pure_neumann ? tot[0] / Ac.n : 0.0;
+}
+
+// mean fix of a pure-Neumann solution: mu = sum m_i phi_i / sum m_i
+__global__ void __launch_bounds__(kBlock) k_phi_mean(int n, const double* __restrict__ m, const double* __restrict__ phi,
+                                                    double* __restrict__ out, double* partials, unsigned int* ticket) {
+    double acc[2] = {0.0, 0.0};
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        acc[0] += m[i] * phi[i];
+        acc[1] += m[i];
+    }
+    double tot[2];
+    if (grid_sum<2>(acc, partials, ticket, tot) && threadIdx.x == 0) *out = tot[0] / tot[1];
+}
+
+// plain mean of a given right-hand side (stand-alone Poisson solves)
+__global__ void __launch_bounds__(kBlock) k_rhs_mean(int n, const double* __restrict__ r, KrylovState* st,
+                                                    int pure_neumann, double* partials, unsigned int* ticket) {
+    double acc[1] = {0.0};
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) acc[0] += r[i];
+    double tot[1];
+    if (grid_sum<1>(acc, partials, ticket, tot) && threadIdx.x == 0) st->mean = pure_neumann ? tot[0] / n : 0.0;
+}
+
+__global__ void k_sub_scalar(int n, double* __restrict__ x, const double* __restrict__ mu) {
+    const double m = *mu;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) x[i] -= m;
+}
+
+// Eq. 24, one level: phi[nv_c + e] = (phi[a_e] + phi[b_e]) / 2; coincident vertices keep their value
+__global__ void k_prolong(int n_new, int nv_c, const int32_t* __restrict__ parents, double* __restrict__ phi) {
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n_new; e += gridDim.x * blockDim.x) {
+        const int2 pr = reinterpret_cast<const int2*>(parents)[e];
+        phi[nv_c + e] = 0.5 * (phi[pr.x] + phi[pr.y]);
+    }
+}
+
+// Eq. 25 right-hand side: g = -2/3 dt (Cx phi, Cy phi), 0 on Dirichlet rows.  If lumped,
+// delta = g / m directly (and no solve follows).
+template <int LANES_>
+__global__ void __launch_bounds__(kBlock) k_corr_rhs(CsrView A, const double* __restrict__ Cx,
+                                                    const double* __restrict__ Cy, const double* __restrict__ phi,
+                                                    const uint8_t* __restrict__ tag, double dt,
+                                                    double* __restrict__ g, const double* __restrict__ mlump,
+                                                    double* __restrict__ delta) {
+    RowGroups<LANES_> rg;
+    CGP_ROW_LOOP(rg, A.n, i) {
+        double sx = 0.0, sy = 0.0;
+        const bool live = i < A.n;
+        if (live) {
+            for (int j = A.rowptr[i] + rg.sub; j < A.rowptr[i + 1]; j += LANES_) {
+                const double pj = phi[A.col[j]];
+                sx += Cx[j] * pj;
+                sy += Cy[j] * pj;
+            }
+        }
+        sx = group_sum<LANES_>(sx);
+        sy = group_sum<LANES_>(sy);
+        if (live && rg.sub == 0) {
+            const double c = -2.0 / 3.0 * dt;
+            double2 gv = (tag[i] & CGP_VEL_DIR) ? make_double2(0.0, 0.0) : make_double2(c * sx, c * sy);
+            reinterpret_cast<double2*>(g)[i] = gv;
+            if (mlump) reinterpret_cast<double2*>(delta)[i] = make_double2(gv.x / mlump[i], gv.y / mlump[i]);
+        }
+    }
+}
+
+// D U~ = Cx u~ + Cy v~ (rotational update, Eq. 26); lumped: q = div / m directly
+template <int LANES_>
+__global__ void __launch_bounds__(kBlock) k_div(CsrView A, const double* __restrict__ Cx, const double* __restrict__ Cy,
+                                               const double* __restrict__ Ut, double* __restrict__ div,
+                                               const double* __restrict__ mlump, double* __restrict__ q) {
+    RowGroups<LANES_> rg;
+    CGP_ROW_LOOP(rg, A.n, i) {
+        double s = 0.0;
+        const bool live = i < A.n;
+        if (live) {
+            for (int j = A.rowptr[i] + rg.sub; j < A.rowptr[i + 1]; j += LANES_) {
+                const double2 u = reinterpret_cast<const double2*>(Ut)[A.col[j]];
+                s += Cx[j] * u.x + Cy[j] * u.y;
+            }
+        }
+        s = group_sum<LANES_>(s);
+        if (live && rg.sub == 0) {
+            div[i] = s;
+            if (mlump) q[i] = s / mlump[i];
+        }
+    }
+}
+
+// end of step: U^{n-1} <- U^n, U^{n+1} = U~ + delta (Eq. 25), P^{n+1} = P^n + phi_f - chi/Re q (Eq. 26)
+__global__ void k_finish(int nf, double* __restrict__ U, double* __restrict__ Uprev, const double* __restrict__ Ut,
+                         const double* __restrict__ delta, double* __restrict__ P, const double* __restrict__ phi,
+                         const double* __restrict__ q, int chi, double inv_re, double* __restrict__ tdev, double dt,
+                         DeviceStats* stats, const KrylovState* ks) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nf; i += gridDim.x * blockDim.x) {
+        const double2 u = reinterpret_cast<const double2*>(U)[i];
+        const double2 ut = reinterpret_cast<const double2*>(Ut)[i];
+        const double2 d = reinterpret_cast<const double2*>(delta)[i];
+        reinterpret_cast<double2*>(Uprev)[i] = u;
+        reinterpret_cast<double2*>(U)[i] = make_double2(ut.x + d.x, ut.y + d.y);
+        double p = P[i] + phi[i];
+        if (chi) p -= inv_re * q[i];
+        P[i] = p;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        *tdev = *tdev + dt;
+        stats->steps += 1;
+        for (int k = 0; k < KS_COUNT; ++k) {
+            stats->last_it[k] = ks[k].iter;
+            stats->sum_it[k] += ks[k].iter;
+            double r = 0.0;
+            for (int c = 0; c < 2; ++c)
+                if (ks[k].bb[c] > 0.0) r = fmax(r, sqrt(ks[k].rr[c] / ks[k].bb[c]));
+            stats->res[k] = r;
+            if (!stats->status && ks[k].status) stats->status = ks[k].status;
+        }
+    }
+}
+
+// scalar setup of a Krylov solve (tolerance, cap) before its init kernel
+__global__ void k_ks_setup(KrylovState* st, double tol2, int maxit) {
+    st->tol2 = tol2;
+    st->maxit = maxit;
+    st->iter = 0;
+    st->done = 0;
+    st->status = 0;
+}
+
+// ---------------------------------------------------------------- loop control
+struct Ctx {
+    Solver* s;
+    cudaStream_t st;
+    bool capture;
+};
+
+static inline int grid_rows(const Solver& s, int n, int lanes) {
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int64_t need = ((int64_t)n * lanes + kBlock - 1) / kBlock;
+    int64_t cap = (int64_t)sms * 8;
+    int g = (int)(need < cap ? need : cap);
+    (void)s;
+    return g < 1 ? 1 : g;
+}
+
+// Runs `init` once, then `body` until the KrylovState says done.  Eager: host polls the
+// done flag after every `chunk` trips.  Capture: a WHILE conditional node whose body is
+// captured on the side stream; the kernels set the condition themselves.
+template <class Init, class Body>
+static int krylov_loop(Ctx& c, KrylovState* ks, int max_trips, Init init, Body body) {
+    Solver& s = *c.s;
+    if (!c.capture) {
+        CGP_TRY(init(c.st, 0ull));
+        const int chunk = 4;
+        for (int trip = 0; trip < max_trips; trip += chunk) {
+            for (int k = 0; k < chunk; ++k) CGP_TRY(body(c.st, 0ull));
+            CGP_CUDA(cudaMemcpyAsync(s.h_flag, &ks->done, sizeof(int), cudaMemcpyDeviceToHost, c.st));
+            CGP_CUDA(cudaStreamSynchronize(c.st));
+            if (*s.h_flag) break;
+        }
+        return CGP_OK;
+    }
+    cudaStreamCaptureStatus cs;
+    cudaGraph_t g = nullptr;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t ndeps = 0;
+    CGP_CUDA(cudaStreamGetCaptureInfo(c.st, &cs, nullptr, &g, &deps, nullptr, &ndeps));
+    cudaGraphConditionalHandle handle;
+    CGP_CUDA(cudaGraphConditionalHandleCreate(&handle, g, 1, cudaGraphCondAssignDefault));
+    CGP_TRY(init(c.st, (unsigned long long)handle));
+    CGP_CUDA(cudaStreamGetCaptureInfo(c.st, &cs, nullptr, &g, &deps, nullptr, &ndeps));
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = handle;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t node;
+    CGP_CUDA(cudaGraphAddNode(&node, g, deps, nullptr, ndeps, &cp));
+    cudaGraph_t bodyg = cp.conditional.phGraph_out[0];
+    CGP_CUDA(cudaStreamUpdateCaptureDependencies(c.st, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+    CGP_CUDA(cudaStreamBeginCaptureToGraph(s.side, bodyg, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+    int rc = body(s.side, (unsigned long long)handle);
+    cudaGraph_t outg = nullptr;
+    cudaError_t e = cudaStreamEndCapture(s.side, &outg);
+    if (rc != CGP_OK) return rc;
+    if (e != cudaSuccess) {
+        set_error("loop body capture failed: %s", cudaGetErrorString(e));
+        return CGP_ECUDA;
+    }
+    return CGP_OK;
+}
+
+// PCG on (pattern A, values val, Jacobi dinv): b, x; NC components.  Body = two iterations
+// (the search direction alternates between two buffers).
+template <int NC>
+static int pcg(Ctx& c, CsrView A, const double* val, const double* dinv, double* b, double* x, KrylovState* ks,
+               double tol, int maxit, bool zero_x, bool project) {
+    Solver& s = *c.s;
+    const int gs = grid_rows(s, A.n, kLanes), gv = grid_rows(s, A.n, 1);
+    auto init = [&, gs](cudaStream_t st, unsigned long long h) -> int {
+        k_ks_setup<<<1, 1, 0, st>>>(ks, tol * tol, maxit);
+        k_pcg_init<NC, kLanes><<<gs, kBlock, 0, st>>>(A, val, dinv, b, x, s.kr, s.kz, s.kp0, ks, s.partials,
+                                                      s.tickets, zero_x, project, h);
+        CGP_LAUNCH_CHECK();
+        return CGP_OK;
+    };
+    auto body = [&, gs, gv](cudaStream_t st, unsigned long long h) -> int {
+        k_pcg_spmv<NC, kLanes><<<gs, kBlock, 0, st>>>(A, val, s.kz, s.kp0, s.kp1, s.kq, ks, s.partials, s.tickets);
+        k_pcg_update<NC><<<gv, kBlock, 0, st>>>(A.n, dinv, x, s.kr, s.kz, s.kp1, s.kq, ks, s.partials, s.tickets, h);
+        k_pcg_spmv<NC, kLanes><<<gs, kBlock, 0, st>>>(A, val, s.kz, s.kp1, s.kp0, s.kq, ks, s.partials, s.tickets);
+        k_pcg_update<NC><<<gv, kBlock, 0, st>>>(A.n, dinv, x, s.kr, s.kz, s.kp0, s.kq, ks, s.partials, s.tickets, h);
+        CGP_LAUNCH_CHECK();
+        return CGP_OK;
+    };
+    return krylov_loop(c, ks, (maxit + 1) / 2 + 1, init, body);
+}
+
+static int bicgstab(Ctx& c, CsrView A, const double* val, const double* dinv, const double* b, KrylovState* ks,
+                    double tol, int maxit) {
+    Solver& s = *c.s;
+    const int gs = grid_rows(s, A.n, kLanes), gv = grid_rows(s, A.n, 1);
+    BicgVecs V = s.bv;
+    auto init = [&, gs, V](cudaStream_t st, unsigned long long h) -> int {
+        k_ks_setup<<<1, 1, 0, st>>>(ks, tol * tol, maxit);
+        k_bicg_init<kLanes><<<gs, kBlock, 0, st>>>(A, val, b, V, ks, s.partials, s.tickets, h);
+        CGP_LAUNCH_CHECK();
+        return CGP_OK;
+    };
+    auto body = [&, gs, gv, V](cudaStream_t st, unsigned long long h) -> int {
+        k_bicg_p<<<gv, kBlock, 0, st>>>(A.n, dinv, V, ks);
+        k_bicg_v<kLanes><<<gs, kBlock, 0, st>>>(A, val, V, ks, s.partials, s.tickets);
+        k_bicg_s<<<gv, kBlock, 0, st>>>(A.n, dinv, V, ks);
+        k_bicg_t<kLanes><<<gs, kBlock, 0, st>>>(A, val, V, ks, s.partials, s.tickets);
+        k_bicg_x<<<gv, kBlock, 0, st>>>(A.n, V, ks, s.partials, s.tickets, h);
+        CGP_LAUNCH_CHECK();
+        return CGP_OK;
+    };
+    return krylov_loop(c, ks, maxit + 1, init, body);
+}
+
+// ---------------------------------------------------------------- pieces of a step
+static int coarse_solve(Ctx& c) {
+    Solver& s = *c.s;
+    const Level& C = s.mesh->lev[s.lc];
+    CsrView Ac{C.nv, C.rowptr, C.col};
+    const bool zero_x = s.prm.guess == CGP_GUESS_ZERO;
+    CGP_TRY(pcg<1>(c, Ac, s.Kc0, s.dinvKc, s.rc, s.phi, &s.ks[KS_POIS], s.prm.tol_poisson, s.prm.max_it_poisson,
+                   zero_x, s.pure_neumann));
+    if (s.pure_neumann) {
+        k_phi_mean<<<grid_rows(s, C.nv, 1), kBlock, 0, c.st>>>(C.nv, s.mlumpC, s.phi, s.scal, s.partials, s.tickets);
+        k_sub_scalar<<<grid_rows(s, C.nv, 1), kBlock, 0, c.st>>>(C.nv, s.phi, s.scal);
+        CGP_LAUNCH_CHECK();
+    }
+    return CGP_OK;
+}
+
+static int prolong_all(Ctx& c) {
+    Solver& s = *c.s;
+    for (int l = s.lc; l < s.lf; ++l) {
+        const Level& Lc = s.mesh->lev[l];
+        const Level& Lf = s.mesh->lev[l + 1];
+        const int n_new = Lf.nv - Lc.nv;
+        k_prolong<<<grid_rows(s, n_new, 1), kBlock, 0, c.st>>>(n_new, Lc.nv, Lf.parents, s.phi);
+    }
+    CGP_LAUNCH_CHECK();
+    return CGP_OK;
+}
+
+static int step_body(Ctx& c) {
+    Solver& s = *c.s;
+    const cgp_params& p = s.prm;
+    const Level& F = s.mesh->lev[s.lf];
+    const Level& C = s.mesh->lev[s.lc];
+    const BcParams bc = bc_from(p);
+    CsrView Af{F.nv, F.rowptr, F.col}, Ac{C.nv, C.rowptr, C.col};
+    const int gv = grid_rows(s, F.nv, 1), gs = grid_rows(s, F.nv, kLanes);
+    // Eq. 21: momentum
+    k_mom_prep<<<gv, kBlock, 0, c.st>>>(F.nv, s.U, s.Uprev, F.xy, bc, s.tdev, p.dt, s.w, s.h);
+    k_mom_assemble<<<gv, kBlock, 0, c.st>>>(F.nv, F.rowptr, F.col, F.vt_ptr, F.vt_list, F.tri, s.geo, s.vtslot, s.S,
+                                            s.M, s.CxT, s.CyT, s.P, s.w, s.h, F.tag, F.xy, bc, s.tdev, p.dt, s.A,
+                                            s.dinvA, s.b, s.Ut);
+    CGP_LAUNCH_CHECK();
+    CGP_TRY(bicgstab(c, Af, s.A, s.dinvA, s.b, &s.ks[KS_MOM], p.tol_mom, p.max_it_mom));
+    // Eqs. 22-23: injection, coarse divergence, coarse Poisson solve
+    k_coarse_rhs<kLanes><<<grid_rows(s, C.nv, kLanes), kBlock, 0, c.st>>>(
+        Ac, s.Cxc, s.Cyc, s.Ut, C.tag, p.dt, s.rc, &s.ks[KS_POIS], s.pure_neumann, s.partials, s.tickets);
+    CGP_LAUNCH_CHECK();
+    CGP_TRY(coarse_solve(c));
+    // Eq. 24: prolongation
+    CGP_TRY(prolong_all(c));
+    // Eq. 25: velocity correction
+    const bool lumped = p.mass_mode == CGP_MASS_LUMPED;
+    k_corr_rhs<kLanes><<<gs, kBlock, 0, c.st>>>(Af, s.Cx, s.Cy, s.phi, F.tag, p.dt, s.g, lumped ? s.mlumpF : nullptr,
+                                                s.delta);
+    CGP_LAUNCH_CHECK();
+    if (!lumped)
+        CGP_TRY(pcg<2>(c, Af, s.M0, s.dinvM0, s.g, s.delta, &s.ks[KS_CORR], p.tol_mass, p.max_it_mass, true, false));
+    // Eq. 26: pressure
+    if (p.chi) {
+        k_div<kLanes><<<gs, kBlock, 0, c.st>>>(Af, s.Cx, s.Cy, s.Ut, s.div, lumped ? s.mlumpF : nullptr, s.qrot);
+        CGP_LAUNCH_CHECK();
+        if (!lumped)
+            CGP_TRY(pcg<1>(c, Af, s.M, s.dinvM, s.div, s.qrot, &s.ks[KS_MASS], p.tol_mass, p.max_it_mass, true, false));
+    }
+    k_finish<<<gv, kBlock, 0, c.st>>>(F.nv, s.U, s.Uprev, s.Ut, s.delta, s.P, s.phi, s.qrot, p.chi, 1.0 / p.Re,
+                                      s.tdev, p.dt, s.stats, s.ks);
+    CGP_LAUNCH_CHECK();
+    return CGP_OK;
+}
+
+int init_state(Solver* s, cudaStream_t st) {
+    const Level& F = s->mesh->lev[s->lf];
+    k_init_state<<<blocks_for(F.nv), kBlock, 0, st>>>(F.nv, F.xy, F.tag, bc_from(s->prm), s->prm.dt, s->U, s->Uprev,
+                                                      s->P, s->tdev);
+    CGP_LAUNCH_CHECK();
+    return CGP_OK;
+}
+
+static int build_graph(Solver& s) {
+    cudaStream_t cap = nullptr;
+    CGP_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+    Ctx c{&s, cap, true};
+    cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) {
+        cudaStreamDestroy(cap);
+        set_error("begin capture failed: %s", cudaGetErrorString(e));
+        return CGP_ECUDA;
+    }
+    int rc = step_body(c);
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(cap, &g);
+    cudaStreamDestroy(cap);
+    if (rc != CGP_OK) {
+        if (g) cudaGraphDestroy(g);
+        return rc;
+    }
+    if (e != cudaSuccess) {
+        set_error("end capture failed: %s", cudaGetErrorString(e));
+        return CGP_ECUDA;
+    }
+    e = cudaGraphInstantiate(&s.step_exec, g, 0);
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(g);
+        set_error("graph instantiation failed: %s", cudaGetErrorString(e));
+        return CGP_ECUDA;
+    }
+    s.step_graph = g;
+    return CGP_OK;
+}
+
+int enqueue_step(Solver* s, cudaStream_t st, bool capture) {
+    Ctx c{s, st, capture};
+    return step_body(c);
+}
+
+static double* vec_ptr(Solver& s, int which, size_t* n) {
+    switch (which) {
+        case CGP_VEC_U: *n = 2 * (size_t)s.nf; return s.U;
+        case CGP_VEC_UPREV: *n = 2 * (size_t)s.nf; return s.Uprev;
+        case CGP_VEC_P: *n = s.nf; return s.P;
+        case CGP_VEC_UTILDE: *n = 2 * (size_t)s.nf; return s.Ut;
+        case CGP_VEC_RHS_C: *n = s.nc; return s.rc;
+        case CGP_VEC_PHI_C: *n = s.nc; return s.phi;
+        case CGP_VEC_PHI_F: *n = s.nf; return s.phi;
+        default: return nullptr;
+    }
+}
+
+static int copy_out(void* dst, const void* src, size_t bytes, int where, cudaStream_t st) {
+    CGP_CUDA(cudaMemcpyAsync(dst, src, bytes, where == CGP_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, st));
+    return CGP_OK;
+}
+
+static int copy_in(void* dst, const void* src, size_t bytes, int where, cudaStream_t st) {
+    CGP_CUDA(cudaMemcpyAsync(dst, src, bytes, where == CGP_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, st));
+    return CGP_OK;
+}
+
+}  // namespace cgp
+
+using namespace cgp;
+
+extern "C" int cgp_step(cgp_solver* h, int32_t n_steps, cgp_stream_t stream) {
+    clear_error();
+    if (!h || n_steps < 0) {
+        set_error("cgp_step: bad arguments");
+        return CGP_EINVAL;
+    }
+    Solver& s = h->s;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (s.prm.use_graph) {
+        if (!s.step_exec) CGP_TRY(build_graph(s));
+        for (int i = 0; i < n_steps; ++i) CGP_CUDA(cudaGraphLaunch(s.step_exec, st));
+        return CGP_OK;
+    }
+    for (int i = 0; i < n_steps; ++i) CGP_TRY(enqueue_step(&s, st, false));
+    return CGP_OK;
+}
+
+extern "C" int cgp_get_fields(cgp_solver* h, double* U, double* P, double* t, cgp_stats* stats, int32_t where,
+                              cgp_stream_t stream) {
+    clear_error();
+    if (!h) {
+        set_error("null solver");
+        return CGP_EINVAL;
+    }
+    Solver& s = h->s;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (U) CGP_TRY(copy_out(U, s.U, sizeof(double) * 2 * s.nf, where, st));
+    if (P) CGP_TRY(copy_out(P, s.P, sizeof(double) * s.nf, where, st));
+    DeviceStats ds;
+    double th = 0.0;
+    CGP_CUDA(cudaMemcpyAsync(&ds, s.stats, sizeof(ds), cudaMemcpyDeviceToHost, st));
+    CGP_CUDA(cudaMemcpyAsync(&th, s.tdev, sizeof(double), cudaMemcpyDeviceToHost, st));
+    CGP_CUDA(cudaStreamSynchronize(st));
+    if (t) *t = th;
+    if (stats) {
+        stats->steps = ds.steps;
+        stats->t = th;
+        stats->it_mom = ds.last_it[KS_MOM];
+        stats->it_poisson = ds.last_it[KS_POIS];
+        stats->it_corr = ds.last_it[KS_CORR];
+        stats->it_mass = ds.last_it[KS_MASS];
+        stats->sum_it_mom = ds.sum_it[KS_MOM];
+        stats->sum_it_poisson = ds.sum_it[KS_POIS];
+        stats->sum_it_corr = ds.sum_it[KS_CORR];
+        stats->sum_it_mass = ds.sum_it[KS_MASS];
+        stats->res_mom = ds.res[KS_MOM];
+        stats->res_poisson = ds.res[KS_POIS];
+        stats->status = ds.status;
+    }
+    return ds.status;
+}
+
+extern "C" int cgp_set_fields(cgp_solver* h, const double* U, const double* Uprev, const double* P, double t,
+                              int32_t where, cgp_stream_t stream) {
+    clear_error();
+    if (!h || !U || !P) {
+        set_error("cgp_set_fields: null argument");
+        return CGP_EINVAL;
+    }
+    Solver& s = h->s;
+    cudaStream_t st = (cudaStream_t)stream;
+    CGP_TRY(copy_in(s.U, U, sizeof(double) * 2 * s.nf, where, st));
+    CGP_TRY(copy_in(s.Uprev, Uprev ? Uprev : U, sizeof(double) * 2 * s.nf, where, st));
+    CGP_TRY(copy_in(s.P, P, sizeof(double) * s.nf, where, st));
+    CGP_CUDA(cudaMemcpyAsync(s.tdev, &t, sizeof(double), cudaMemcpyHostToDevice, st));
+    CGP_CUDA(cudaMemsetAsync(s.stats, 0, sizeof(DeviceStats), st));
+    CGP_CUDA(cudaStreamSynchronize(st));
+    return CGP_OK;
+}
+
+extern "C" int cgp_get_vector(cgp_solver* h, int32_t which, double* out, int32_t where, cgp_stream_t stream) {
+    clear_error();
+    if (!h || !out) {
+        set_error("cgp_get_vector: null argument");
+        return CGP_EINVAL;
+    }
+    size_t n = 0;
+    double* src = vec_ptr(h->s, which, &n);
+    if (!src) {
+        set_error("unknown vector %d", which);
+        return CGP_EINVAL;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    CGP_TRY(copy_out(out, src, n * sizeof(double), where, st));
+    if (where == CGP_HOST) CGP_CUDA(cudaStreamSynchronize(st));
+    return CGP_OK;
+}
+
+extern "C" int cgp_set_vector(cgp_solver* h, int32_t which, const double* in, int32_t where, cgp_stream_t stream) {
+    clear_error();
+    if (!h || !in || (which != CGP_VEC_U && which != CGP_VEC_UPREV && which != CGP_VEC_P && which != CGP_VEC_PHI_C)) {
+        set_error("cgp_set_vector: bad arguments");
+        return CGP_EINVAL;
+    }
+    size_t n = 0;
+    double* dst = vec_ptr(h->s, which, &n);
+    cudaStream_t st = (cudaStream_t)stream;
+    CGP_TRY(copy_in(dst, in, n * sizeof(double), where, st));
+    if (where == CGP_HOST) CGP_CUDA(cudaStreamSynchronize(st));
+    return CGP_OK;
+}
+
+extern "C" int cgp_poisson_solve(cgp_solver* h, const double* rhs, double* phi, int32_t* iters, int32_t where,
+                                 cgp_stream_t stream) {
+    clear_error();
+    if (!h || !rhs || !phi) {
+        set_error("cgp_poisson_solve: null argument");
+        return CGP_EINVAL;
+    }
+    Solver& s = h->s;
+    cudaStream_t st = (cudaStream_t)stream;
+    CGP_TRY(copy_in(s.rc, rhs, sizeof(double) * s.nc, where, st));
+    CGP_TRY(copy_in(s.phi, phi, sizeof(double) * s.nc, where, st));
+    KrylovState* ks = &s.ks[KS_POIS];
+    // range projection of a pure-Neumann problem uses the plain mean of the given rhs
+    k_rhs_mean<<<grid_rows(s, s.nc, 1), kBlock, 0, st>>>(s.nc, s.rc, ks, s.pure_neumann, s.partials, s.tickets);
+    CGP_LAUNCH_CHECK();
+    Ctx c{&s, st, false};
+    CGP_TRY(coarse_solve(c));
+    CGP_TRY(copy_out(phi, s.phi, sizeof(double) * s.nc, where, st));
+    int it = 0, status = 0;
+    CGP_CUDA(cudaMemcpyAsync(&it, &ks->iter, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CGP_CUDA(cudaMemcpyAsync(&status, &ks->status, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CGP_CUDA(cudaStreamSynchronize(st));
+    if (iters) *iters = it;
+    return status;
+}
+
+extern "C" int cgp_prolong(cgp_solver* h, const double* phi_c, double* phi_f, int32_t where, cgp_stream_t stream) {
+    clear_error();
+    if (!h || !phi_c || !phi_f) {
+        set_error("cgp_prolong: null argument");
+        return CGP_EINVAL;
+    }
+    Solver& s = h->s;
+    cudaStream_t st = (cudaStream_t)stream;
+    CGP_TRY(copy_in(s.phi, phi_c, sizeof(double) * s.nc, where, st));
+    Ctx c{&s, st, false};
+    CGP_TRY(prolong_all(c));
+    CGP_TRY(copy_out(phi_f, s.phi, sizeof(double) * s.nf, where, st));
+    if (where == CGP_HOST) CGP_CUDA(cudaStreamSynchronize(st));
+    return CGP_OK;
+}

@@ -1,0 +1,187 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle."""
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+from workloads import square_mesh, crisscross_mesh, channel_cylinder_mesh, VEL_DIR, PHI_ZERO, WORKLOADS
+from oracle.mesh import build_hierarchy
+from oracle.cgp import CGPOracle
+from oracle import fem, flows
+
+pytestmark = pytest.mark.gpu
+
+TIGHT = dict(tol_mom=1e-13, tol_poisson=1e-13, tol_mass=1e-14, max_it_poisson=50000)
+
+
+def rel(a, b):
+    return np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(np.asarray(b)), 1e-300)
+
+
+@pytest.fixture(scope="module")
+def cg(lib):
+    from paper_1812_00185_gb300 import binding
+    return binding
+
+
+def _channel_small():
+    return channel_cylinder_mesh(seed=4, h=0.05)
+
+
+@pytest.mark.parametrize("mk,levels", [(lambda: square_mesh(8), 3), (lambda: crisscross_mesh(5), 2),
+                                       (_channel_small, 2)])
+def test_mesh_hierarchy_bit_exact(cg, mk, levels):
+    base = mk()
+    ref = build_hierarchy(base.xy, base.tri, base.tag, levels)
+    m = cg.Mesh(base.xy, base.tri, base.tag, levels)
+    for l in range(levels + 1):
+        g = m.level(l)
+        r = ref[l]
+        assert np.array_equal(g["xy"], r.xy), l
+        assert np.array_equal(g["tri"], r.tri), l
+        assert np.array_equal(g["tag"], r.tag), l
+        assert np.array_equal(g["rowptr"], r.rowptr), l
+        assert np.array_equal(g["col"], r.col), l
+        if l > 0:
+            assert np.array_equal(g["parents"], r.parents), l
+    m.close()
+
+
+def _csr(lev, vals):
+    n = lev["rowptr"].shape[0] - 1
+    return sp.csr_matrix((vals, lev["col"], lev["rowptr"]), shape=(n, n))
+
+
+def test_static_operators_match(cg):
+    base = _channel_small()
+    m = cg.Mesh(base.xy, base.tri, base.tag, 2)
+    s = cg.Solver(m, cg.make_params(20.0, 0.01, k=1, bc_kind=cg.CGP_BC_CHANNEL, bc_param=(0.3, 0.41)))
+    o = CGPOracle(base, 2, 1, 20.0, 0.01, 1, flows.BC_CHANNEL, bc_param=(0.3, 0.41, 0, 0))
+    F, C = m.level(2), m.level(1)
+    for which, name, lev, ops in [(cg.CGP_MAT_M, "M", F, o.ops_f), (cg.CGP_MAT_K, "K", F, o.ops_f),
+                                  (cg.CGP_MAT_CX, "Cx", F, o.ops_f), (cg.CGP_MAT_CY, "Cy", F, o.ops_f),
+                                  (cg.CGP_MAT_KC, "K", C, o.ops_c), (cg.CGP_MAT_CXC, "Cx", C, o.ops_c),
+                                  (cg.CGP_MAT_CYC, "Cy", C, o.ops_c)]:
+        G = _csr(lev, s.matrix(which))
+        R = ops[name]
+        assert abs(G - R).max() <= 1e-13 * abs(R).max(), name
+    s.close(); m.close()
+
+
+def test_prolongation_bit_exact(cg):
+    base = square_mesh(4)
+    m = cg.Mesh(base.xy, base.tri, base.tag, 3)
+    s = cg.Solver(m, cg.make_params(100.0, 0.01, k=3))
+    levels = build_hierarchy(base.xy, base.tri, base.tag, 3)
+    phic = np.random.default_rng(0).standard_normal(levels[0].n_vert)
+    assert np.array_equal(cg.cgp_prolong(s.handle, phic), fem.prolong(phic, levels, 0, 3))
+    s.close(); m.close()
+
+
+@pytest.mark.parametrize("kind", ["neumann", "dirichlet"])
+def test_coarse_poisson_solve(cg, kind):
+    if kind == "neumann":
+        base, bc, bp = square_mesh(16), flows.BC_CAVITY, (1.0, 0, 0, 0)
+    else:
+        base, bc, bp = _channel_small(), flows.BC_CHANNEL, (0.3, 0.41, 0, 0)
+    m = cg.Mesh(base.xy, base.tri, base.tag, 2)
+    s = cg.Solver(m, cg.make_params(100.0, 0.01, k=1, bc_kind=bc, bc_param=bp, guess=cg.CGP_GUESS_ZERO, **TIGHT))
+    o = CGPOracle(base, 2, 1, 100.0, 0.01, 0, bc, bc_param=bp)
+    r = np.random.default_rng(1).standard_normal(o.coarse.n_vert)
+    r[o.phi0_mask] = 0.0
+    phi, it, rc = cg.cgp_poisson_solve(s.handle, r)
+    rr = r - r.mean() if o.pure_neumann else r
+    ref = o.poisson(rr)
+    assert rc == 0 and 0 < it < 5000
+    assert rel(phi, ref) < 1e-9
+    s.close(); m.close()
+
+
+def _pair(cg, base, n_levels, k, Re, dt, chi, bc, bp=(1.0, 0, 0, 0), use_graph=1, mass_mode=0, **kw):
+    m = cg.Mesh(base.xy, base.tri, base.tag, n_levels)
+    prm = cg.make_params(Re, dt, chi=chi, k=k, bc_kind=bc, bc_param=bp, use_graph=use_graph,
+                         mass_mode=mass_mode, **{**TIGHT, **kw})
+    s = cg.Solver(m, prm)
+    o = CGPOracle(base, n_levels, k, Re, dt, chi, bc, bc_param=bp,
+                  mass_mode="lumped" if mass_mode else "consistent")
+    return m, s, o
+
+
+def test_one_step_intermediates(cg):
+    m, s, o = _pair(cg, square_mesh(16), 2, 1, 100.0, 0.01, 1, flows.BC_CAVITY)
+    s.step(1)
+    out = o.step()
+    assert rel(s.vector(cg.CGP_VEC_UTILDE), out["Ut"]) < 1e-10
+    assert rel(s.vector(cg.CGP_VEC_RHS_C), out["rc"]) < 1e-10
+    assert rel(s.vector(cg.CGP_VEC_PHI_C), out["phic"]) < 1e-9
+    assert rel(s.vector(cg.CGP_VEC_PHI_F), out["phif"]) < 1e-9
+    U, P, t, st, rc = s.fields()
+    assert rc == 0 and t == o.t
+    assert rel(U, out["U"]) < 1e-10 and rel(P, out["P"]) < 1e-9
+    s.close(); m.close()
+
+
+def test_cavity64_k1_full_run(cg):
+    w = WORKLOADS["cavity64_k1"]
+    base = w.base_mesh()
+    m, s, o = _pair(cg, base, w.n_levels, w.k, w.Re, w.dt, w.chi, w.bc, tol_mom=w.tol_mom,
+                    tol_poisson=w.tol_poisson, tol_mass=1e-12)
+    s.step(w.steps)
+    o.run(w.steps)
+    U, P, t, st, rc = s.fields()
+    assert rc == 0 and st["steps"] == w.steps
+    assert rel(U, o.U) < 1e-6 and rel(P, o.P) < 1e-6, (rel(U, o.U), rel(P, o.P))
+    s.close(); m.close()
+
+
+@pytest.mark.parametrize("chi,mass", [(0, 0), (1, 0), (1, 1)])
+def test_channel_and_forms(cg, chi, mass):
+    m, s, o = _pair(cg, _channel_small(), 2, 1, 20.0, 0.005, chi, flows.BC_CHANNEL, bp=(0.3, 0.41, 0, 0),
+                    mass_mode=mass)
+    s.step(4)
+    o.run(4)
+    U, P, t, st, rc = s.fields()
+    assert rc == 0
+    assert rel(U, o.U) < 1e-8 and rel(P, o.P) < 1e-8, (rel(U, o.U), rel(P, o.P))
+    s.close(); m.close()
+
+
+def test_periodic_taylor_green(cg):
+    m, s, o = _pair(cg, square_mesh(8), 2, 2, 100.0, 0.002, 1, flows.BC_TG_PERIODIC)
+    s.step(5)
+    o.run(5)
+    U, P, t, st, rc = s.fields()
+    assert rc == 0 and rel(U, o.U) < 1e-8 and rel(P, o.P) < 1e-8
+    s.close(); m.close()
+
+
+def test_graph_replay_equals_eager_launches(cg):
+    res = []
+    for g in (0, 1):
+        m, s, _ = _pair(cg, square_mesh(8), 2, 1, 100.0, 0.01, 1, flows.BC_CAVITY, use_graph=g)
+        s.step(3)
+        U, P, t, st, rc = s.fields()
+        res.append((U, P, st))
+        s.close(); m.close()
+    assert np.array_equal(res[0][0], res[1][0]) and np.array_equal(res[0][1], res[1][1])
+    assert res[0][2]["sum_it_mom"] == res[1][2]["sum_it_mom"]
+
+
+def test_checkpoint_resume_is_bitwise(cg):
+    # 4 steps in one go == 2 steps, state saved, a fresh solver restored, 2 more steps
+    m, s, _ = _pair(cg, square_mesh(8), 2, 1, 100.0, 0.01, 1, flows.BC_CAVITY)
+    s.step(4)
+    U4, P4, t4, _, _ = s.fields()
+    m2, s2, _ = _pair(cg, square_mesh(8), 2, 1, 100.0, 0.01, 1, flows.BC_CAVITY)
+    s2.step(2)
+    U2, P2, t2, _, _ = s2.fields()
+    ck = (U2, s2.vector(cg.CGP_VEC_UPREV), P2, t2, s2.vector(cg.CGP_VEC_PHI_C))
+    m3, s3, _ = _pair(cg, square_mesh(8), 2, 1, 100.0, 0.01, 1, flows.BC_CAVITY)
+    s3.set_fields(ck[0], ck[1], ck[2], ck[3])
+    s3.set_vector(cg.CGP_VEC_PHI_C, ck[4])
+    s3.step(2)
+    U, P, t, _, _ = s3.fields()
+    assert t == t4
+    assert np.array_equal(U, U4) and np.array_equal(P, P4)
+    for x in (s, s2, s3, m, m2, m3):
+        x.close()
