@@ -1,0 +1,374 @@
+"""Benchmark of the coarse-grid incremental pressure-projection (CGP) time step.
+
+Workload (N = 1 GPU): the channel-with-cylinder problem, a seeded ~16k-triangle
+Delaunay base mesh refined three times (~1.05M velocity triangles, ~0.53M vertices),
+pressure increment two levels coarser, rotational form, Re = 20 on the cylinder
+diameter (nu = 1e-3), dt = 0.002, solver tolerances 1e-8.  One "step" is one CGP
+time step: momentum solve, injection, coarse Poisson solve, prolongation, velocity
+correction, pressure update (all inside the library's CUDA kernels, replayed as a
+CUDA graph).
+
+Printed: one JSON line (rank 0).  ``value`` = time steps per second of the headline
+form; ``e2e`` = the same through the C ABI with host buffers copied in and out every
+step; ``roofline`` = the step's dominant kernel against the measured HBM copy
+bandwidth; ``pcg_hbm`` = GB/s of the PCG iteration on a large synthetic Poisson
+problem; ``cpu_baseline`` = the FP64 CPU oracle on a bounded sample.
+
+``--impl reference`` times the FP64 CPU oracle itself on the same workload.
+Under torchrun (N > 1) every rank runs an independent replica (the method has no
+data-parallel exchange): value = steps of all ranks / max time over ranks.
+"""
+
+import argparse
+import json
+import os
+import resource
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "CGP time steps/s at ~1M tris + PCG HBM GB/s; learned+FP32 vs plain FP64"
+L2_BYTES = 129 * 1024 * 1024
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while the timed region runs."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.Q, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def workload_problem(name):
+    from workloads import WORKLOADS
+    w = WORKLOADS[name]
+    return w, w.base_mesh()
+
+
+def make_params(cg, w, form):
+    mixed = form in ("mixed", "mixed_learned")
+    return cg.make_params(w.Re, w.dt, chi=w.chi, k=w.k, tol_mom=w.tol_mom, tol_poisson=w.tol_poisson,
+                          tol_mass=1e-10, max_it_mom=1000, max_it_poisson=20000, max_it_mass=1000,
+                          precision=cg.CGP_MIXED if mixed else cg.CGP_FP64,
+                          guess=cg.CGP_GUESS_PREV, bc_kind=w.bc, bc_param=w.bc_param, use_graph=1)
+
+
+# algorithmic bytes per launch of each kernel kind (int32 indices, FP64 values);
+# n rows, z = CSR entries of the level the kernel works on, t = triangles
+def kernel_bytes(name, n, z, t=0):
+    table = {
+        "pois_spmv": 12 * z + 4 * n + 32 * n, "pois_update": 64 * n,
+        "mass_spmv": 12 * z + 4 * n + 32 * n, "mass_update": 64 * n,
+        "corr_spmv": 12 * z + 4 * n + 64 * n, "corr_update": 120 * n,
+        "bicg_v": 12 * z + 4 * n + 48 * n, "bicg_t": 12 * z + 4 * n + 48 * n,
+        "bicg_p": 88 * n, "bicg_s": 72 * n, "bicg_x": 128 * n,
+        "mom_assemble": 44 * z + 4 * n + 16 * n + 8 * n + 8 * n + 32 * n + 4 * n + 24 * t + 56 * t + 12 * t
+                        + 16 * n + n,
+        "mom_prep": 64 * n, "finish": 112 * n, "corr_rhs": 20 * z + 4 * n + 8 * n + n + 16 * n,
+        "div": 20 * z + 4 * n + 16 * n + 8 * n,
+    }
+    return table.get(name)
+
+
+def level_of(name):
+    return "coarse" if name.startswith("pois") or name in ("coarse_rhs", "phi_mean", "phi_sub") else "fine"
+
+
+def run_gpu(args, rank, world):
+    import torch
+    from paper_1812_00185_gb300 import binding as cg
+
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream()
+    w, base = workload_problem(args.workload)
+    t0 = time.time()
+    mesh = cg.Mesh(base.xy, base.tri, base.tag, w.n_levels)
+    torch.cuda.synchronize()
+    t_mesh = time.time() - t0
+    nv_f, nt_f, nnz_f = mesh.info(w.n_levels)
+    nv_c, nt_c, nnz_c = mesh.info(w.n_levels - w.k)
+
+    def run_form(form, steps, warmup, timed=True):
+        t0 = time.time()
+        s = cg.Solver(mesh, make_params(cg, w, form))
+        torch.cuda.synchronize()
+        t_asm = time.time() - t0
+        s.step(warmup)
+        _, _, _, st0, _ = s.fields()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        with ClockSampler(dev) as clk:
+            ev0.record(stream)
+            s.step(steps)
+            ev1.record(stream)
+            torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        ms = ev0.elapsed_time(ev1)
+        U, P, t, st1, rc = s.fields()
+        its = {k: (st1["sum_it_" + k] - st0["sum_it_" + k]) / steps for k in ("mom", "poisson", "corr", "mass")}
+        return s, {"ms": ms, "ms_per_step": ms / steps, "steps_per_s": 1000.0 * steps / ms, "iters": its,
+                   "launches": st1["launches"] - st0["launches"], "status": rc,
+                   "res_poisson": st1["res_poisson"], "res_mom": st1["res_mom"], "assemble_s": t_asm,
+                   "clocks": clk.summary()}
+
+    head_form = args.form
+    s, head = run_form(head_form, args.steps, args.warmup)
+    ws_bytes = s.workspace.numel()
+    # the plain FP64 form, for the comparison the metric names
+    forms = {head_form: {k: head[k] for k in ("steps_per_s", "ms_per_step", "iters", "status")}}
+    if head_form != "fp64" and not args.quick:
+        s2, plain = run_form("fp64", args.steps, args.warmup)
+        forms["fp64"] = {k: plain[k] for k in ("steps_per_s", "ms_per_step", "iters", "status")}
+        s2.close()
+
+    # end to end through the C ABI: pinned host state in, one step, state out, every step
+    Uh = torch.empty((nv_f, 2), dtype=torch.float64, pin_memory=True)
+    Uph = torch.empty((nv_f, 2), dtype=torch.float64, pin_memory=True)
+    Ph = torch.empty(nv_f, dtype=torch.float64, pin_memory=True)
+    U, P, tcur, _, _ = s.fields()
+    Uh.numpy()[:] = U
+    Uph.numpy()[:] = s.vector(cg.CGP_VEC_UPREV)
+    Ph.numpy()[:] = P
+    e2e_steps = max(1, min(args.steps, 20))
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for _ in range(e2e_steps):
+        cg.cgp_set_fields(s.handle, Uh.numpy(), Uph.numpy(), Ph.numpy(), tcur, where=cg.CGP_HOST)
+        cg.cgp_step(s.handle, 1)
+        Uph.copy_(Uh)
+        _, _, tcur, _, _ = cg.cgp_get_fields(s.handle, U=Uh.numpy(), P=Ph.numpy(), where=cg.CGP_HOST)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = ev0.elapsed_time(ev1) / e2e_steps
+    e2e = {"value": 1000.0 / e2e_ms * world, "unit": "steps/s", "h2d_bytes_per_step": 8 * 5 * nv_f,
+           "d2h_bytes_per_step": 8 * 3 * nv_f}
+
+    # per-kernel device times of one profiled step (events around every launch)
+    prof = cg.cgp_profile_step(s.handle)
+    peak, peak_kind = _peaks()
+    kern = {}
+    for name, (cnt, tot) in prof.items():
+        n, z, t = (nv_c, nnz_c, nt_c) if level_of(name) == "coarse" else (nv_f, nnz_f, nt_f)
+        b = kernel_bytes(name, n, z, t)
+        avg = tot / cnt
+        kern[name] = {"launches": cnt, "total_ms": round(tot, 4), "avg_us": round(1000 * avg, 2),
+                      "GBps": round(b / (avg * 1e-3) / 1e9, 1) if b else None}
+    dom = max(kern, key=lambda k: kern[k]["total_ms"] if kern[k]["GBps"] is not None else -1)
+    n, z, t = (nv_c, nnz_c, nt_c) if level_of(dom) == "coarse" else (nv_f, nnz_f, nt_f)
+    traffic = None
+    tr_path = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tr_path):
+        try:
+            traffic = json.load(open(tr_path)).get(args.workload, {}).get(dom)
+        except Exception:
+            traffic = None
+    roof = {"kernel": dom, "bound": "hbm", "achieved": kern[dom]["GBps"], "peak": peak, "unit": "GB/s",
+            "frac": round(kern[dom]["GBps"] / peak, 4), "traffic": traffic,
+            "bytes_per_launch": kernel_bytes(dom, n, z, t), "avg_launch_us": kern[dom]["avg_us"],
+            "peak_source": peak_kind}
+
+    # PCG iteration bandwidth on a synthetic Poisson problem far larger than L2
+    pcg = None
+    if not args.quick and rank == 0:
+        pcg = pcg_bandwidth(cg, torch, args.pcg_n, peak)
+
+    s.close()
+    mesh.close()
+    out = {
+        "metric": METRIC, "value": round(head["steps_per_s"] * world, 3), "unit": "steps/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(head["ms_per_step"], 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if head_form == "fp64" else "f32+f64", "data": "synthetic",
+        "config": {"workload": args.workload, "form": head_form, "fine_triangles": nt_f, "fine_vertices": nv_f,
+                   "coarse_vertices": nv_c, "k": w.k, "chi": w.chi, "Re": w.Re, "dt": w.dt,
+                   "tol": w.tol_poisson, "parallelism": "replicas" if world > 1 else "single",
+                   "l2": "working set %.2f GB > 129 MB L2 (no flush)" % (1e-9 * ws_bytes)},
+        "e2e": e2e, "gpu_launches": int(head["launches"]), "clocks": head["clocks"], "roofline": roof,
+        "forms": forms, "kernels": kern, "setup_s": {"mesh": round(t_mesh, 3), "assemble": round(head["assemble_s"], 3)},
+        "pcg_hbm": pcg,
+    }
+    return out, (w, base)
+
+
+def pcg_bandwidth(cg, torch, n_side, peak):
+    """GB/s of the coarse-Poisson PCG iteration on an n_side^2 x 2 structured mesh (k = 0)."""
+    from workloads import square_mesh, PHI_ZERO
+    lv = 0
+    nb = n_side
+    while nb > 256:
+        nb //= 2
+        lv += 1
+    base = square_mesh(nb, boundary_flags=PHI_ZERO)
+    mesh = cg.Mesh(base.xy, base.tri, base.tag, lv)
+    prm = cg.make_params(1.0, 1.0, k=0, tol_poisson=1e-30, max_it_poisson=200, guess=cg.CGP_GUESS_ZERO,
+                         bc_kind=cg.CGP_BC_CAVITY)
+    s = cg.Solver(mesh, prm)
+    nf, nc, zf, zc = cg.cgp_solver_info(s.handle)
+    rhs = np.random.default_rng(0).standard_normal(nc)
+    cg.cgp_poisson_solve(s.handle, rhs)          # warm-up
+    prof = None
+    t0 = time.time()
+    phi, it, rc = cg.cgp_poisson_solve(s.handle, rhs)
+    wall = time.time() - t0
+    # per-kernel times of the same solve come from a profiled step of this solver
+    prof = cg.cgp_profile_step(s.handle)
+    sp, up = prof.get("pois_spmv"), prof.get("pois_update")
+    out = {"n": nc, "nnz": zc, "iters": it, "wall_ms_per_iter": round(1000 * wall / max(it, 1), 4)}
+    if sp and up:
+        b_iter = kernel_bytes("pois_spmv", nc, zc) + kernel_bytes("pois_update", nc, zc)
+        t_iter = (sp[1] / sp[0] + up[1] / up[0]) * 1e-3
+        out.update({"bytes_per_iter": b_iter, "us_per_iter": round(1e6 * t_iter, 2),
+                    "GBps": round(b_iter / t_iter / 1e9, 1), "frac": round(b_iter / t_iter / 1e9 / peak, 4),
+                    "spmv_GBps": round(kernel_bytes("pois_spmv", nc, zc) / (sp[1] / sp[0] * 1e-3) / 1e9, 1),
+                    "update_GBps": round(kernel_bytes("pois_update", nc, zc) / (up[1] / up[0] * 1e-3) / 1e9, 1)})
+    s.close()
+    mesh.close()
+    return out
+
+
+def cpu_oracle_rate(w, base, budget_s):
+    """Steps/s of the FP64 oracle (setup excluded), bounded to about budget_s seconds."""
+    from oracle.cgp import CGPOracle
+    t0 = time.time()
+    o = CGPOracle(base, w.n_levels, w.k, w.Re, w.dt, w.chi, w.bc, bc_param=w.bc_param)
+    setup = time.time() - t0
+    r0 = resource.getrusage(resource.RUSAGE_SELF)
+    t0 = time.time()
+    n = 0
+    while True:
+        o.step()
+        n += 1
+        if time.time() - t0 > budget_s or n >= 50:
+            break
+    wall = time.time() - t0
+    r1 = resource.getrusage(resource.RUSAGE_SELF)
+    cpu = (r1.ru_utime - r0.ru_utime) + (r1.ru_stime - r0.ru_stime)
+    return {"value": round(n / wall, 5), "unit": "steps/s", "cores": max(1, int(round(cpu / wall))),
+            "kind": "oracle", "sample": "%d oracle time steps of %s (%d fine vertices) after %.1f s of setup"
+                                        % (n, w.name, o.fine.n_vert, setup)}, n, wall
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--workload", default="channel1m_k2")
+    ap.add_argument("--form", default="fp64", choices=["fp64", "mixed", "mixed_learned"])
+    ap.add_argument("--pcg-n", type=int, default=2048)
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--quick", action="store_true", help="skip the secondary measurements")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "gpu":
+        args.warmup = 3
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+
+    if args.impl == "reference":
+        if rank != 0:
+            return 0
+        w, base = workload_problem(args.workload)
+        res, n, wall = cpu_oracle_rate(w, base, min(120.0, 20.0 * max(1, args.steps) / 10.0))
+        print(json.dumps({
+            "metric": METRIC, "value": res["value"], "unit": "steps/s", "n_gpus": args.gpus, "steps": n,
+            "warmup": 0, "ms_per_step": round(1000 * wall / n, 3), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": args.workload, "form": "fp64 oracle (sparse direct solves)"},
+            "cpu_baseline": res,
+            "e2e": {"value": res["value"], "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        }))
+        return 0
+
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        dist.init_process_group("nccl")
+    out, (w, base) = run_gpu(args, rank, world)
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([out["ms_per_step"]], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        out["ms_per_step"] = round(float(t.item()), 4)
+        out["value"] = round(1000.0 * world / out["ms_per_step"], 3)
+    if rank == 0:
+        if world == 1 and not args.quick:
+            out["cpu_baseline"], _, _ = cpu_oracle_rate(w, base, args.cpu_budget)
+        print(json.dumps(out))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -100,6 +100,7 @@ typedef struct {
     int64_t sum_it_mom, sum_it_poisson, sum_it_corr, sum_it_mass;
     double res_mom, res_poisson;                           /* last relative residuals (max over components) */
     int32_t status;            /* first non-zero CGP_E* code seen by any solve, else 0 */
+    int64_t launches;          /* kernel launches of graph-replayed steps (Krylov loop trips included) */
 } cgp_stats;
 
 /* Library message for the last failing call of this thread ("" if none). */
@@ -173,6 +174,22 @@ int cgp_poisson_solve(cgp_solver* s, const double* rhs, double* phi, int32_t* it
                       int32_t where, cgp_stream_t stream);
 /* Eq. 24 alone: phi_f (N_f) = prolongation of phi_c (N_c) over the k levels. */
 int cgp_prolong(cgp_solver* s, const double* phi_c, double* phi_f, int32_t where, cgp_stream_t stream);
+
+/* Per-kernel timing of ONE step (the state advances as in cgp_step).  The step runs
+ * with eager launches, each bracketed by two CUDA events on `stream`; launches of loop
+ * kernels made after their solve had converged are not counted.  counts[id] and
+ * total_ms[id] (arrays of n_ids >= CGP_PROF_COUNT) receive, per kernel kind, the
+ * number of launches and their summed device time.  Synchronises. */
+enum {
+    CGP_PROF_MOM_PREP = 0, CGP_PROF_MOM_ASSEMBLE, CGP_PROF_MOM_SETUP, CGP_PROF_MOM_INIT,
+    CGP_PROF_BICG_P, CGP_PROF_BICG_V, CGP_PROF_BICG_S, CGP_PROF_BICG_T, CGP_PROF_BICG_X,
+    CGP_PROF_COARSE_RHS, CGP_PROF_POIS_SETUP, CGP_PROF_POIS_INIT, CGP_PROF_POIS_SPMV, CGP_PROF_POIS_UPDATE,
+    CGP_PROF_PHI_MEAN, CGP_PROF_PHI_SUB, CGP_PROF_PROLONG,
+    CGP_PROF_CORR_RHS, CGP_PROF_CORR_SETUP, CGP_PROF_CORR_INIT, CGP_PROF_CORR_SPMV, CGP_PROF_CORR_UPDATE,
+    CGP_PROF_DIV, CGP_PROF_MASS_SETUP, CGP_PROF_MASS_INIT, CGP_PROF_MASS_SPMV, CGP_PROF_MASS_UPDATE,
+    CGP_PROF_FINISH, CGP_PROF_COUNT
+};
+int cgp_profile_step(cgp_solver* s, cgp_stream_t stream, int32_t n_ids, int32_t* counts, double* total_ms);
 
 void cgp_solver_destroy(cgp_solver* s);
 

@@ -54,7 +54,7 @@ class Stats(ctypes.Structure):
     _fields_ = [("steps", c_int64), ("t", c_double), ("it_mom", c_int32), ("it_poisson", c_int32),
                 ("it_corr", c_int32), ("it_mass", c_int32), ("sum_it_mom", c_int64),
                 ("sum_it_poisson", c_int64), ("sum_it_corr", c_int64), ("sum_it_mass", c_int64),
-                ("res_mom", c_double), ("res_poisson", c_double), ("status", c_int32)]
+                ("res_mom", c_double), ("res_poisson", c_double), ("status", c_int32), ("launches", c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -80,8 +80,14 @@ _SIGS = {
                                   POINTER(c_int64)]),
     "cgp_poisson_solve": (c_int32, [c_void_p, c_void_p, c_void_p, POINTER(c_int32), c_int32, c_void_p]),
     "cgp_prolong": (c_int32, [c_void_p, c_void_p, c_void_p, c_int32, c_void_p]),
+    "cgp_profile_step": (c_int32, [c_void_p, c_void_p, c_int32, c_void_p, c_void_p]),
     "cgp_solver_destroy": (None, [c_void_p]),
 }
+
+PROF_NAMES = ["mom_prep", "mom_assemble", "mom_setup", "mom_init", "bicg_p", "bicg_v", "bicg_s", "bicg_t",
+              "bicg_x", "coarse_rhs", "pois_setup", "pois_init", "pois_spmv", "pois_update", "phi_mean",
+              "phi_sub", "prolong", "corr_rhs", "corr_setup", "corr_init", "corr_spmv", "corr_update", "div",
+              "mass_setup", "mass_init", "mass_spmv", "mass_update", "finish"]
 
 _LIB = None
 
@@ -268,6 +274,15 @@ def cgp_prolong(solver, phi_c, stream=None):
     out = np.empty(nf)
     _check(load().cgp_prolong(solver, _ptr(phi_c), _ptr(out), CGP_HOST, _stream(stream)))
     return out
+
+
+def cgp_profile_step(solver, stream=None):
+    """Advance one step with per-launch event timing: {kernel: (launches, total ms)}."""
+    n = len(PROF_NAMES)
+    counts = np.zeros(n, np.int32)
+    ms = np.zeros(n)
+    _check(load().cgp_profile_step(solver, _stream(stream), n, _ptr(counts), _ptr(ms)))
+    return {PROF_NAMES[i]: (int(counts[i]), float(ms[i])) for i in range(n) if counts[i]}
 
 
 def cgp_solver_destroy(solver):

@@ -24,6 +24,7 @@ enum { KS_MOM = 0, KS_POIS = 1, KS_CORR = 2, KS_MASS = 3, KS_COUNT = 4 };
 
 struct DeviceStats {
     int64_t steps;
+    int64_t launches;             // kernels launched by graph-replayed steps (loop trips included)
     int64_t sum_it[KS_COUNT];
     int32_t last_it[KS_COUNT];
     int32_t status;

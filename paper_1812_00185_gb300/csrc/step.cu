@@ -233,7 +233,7 @@ __global__ void __launch_bounds__(kBlock) k_div(CsrView A, const double* __restr
 __global__ void k_finish(int nf, double* __restrict__ U, double* __restrict__ Uprev, const double* __restrict__ Ut,
                          const double* __restrict__ delta, double* __restrict__ P, const double* __restrict__ phi,
                          const double* __restrict__ q, int chi, double inv_re, double* __restrict__ tdev, double dt,
-                         DeviceStats* stats, const KrylovState* ks) {
+                         DeviceStats* stats, const KrylovState* ks, int fixed_launches) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nf; i += gridDim.x * blockDim.x) {
         const double2 u = reinterpret_cast<const double2*>(U)[i];
         const double2 ut = reinterpret_cast<const double2*>(Ut)[i];
@@ -247,6 +247,11 @@ __global__ void k_finish(int nf, double* __restrict__ U, double* __restrict__ Up
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         *tdev = *tdev + dt;
         stats->steps += 1;
+        // launches of a graph replay: the fixed kernels, 5 per BiCGStab iteration and 4 per
+        // trip of a PCG loop body (two iterations per trip)
+        int64_t l = fixed_launches + 5 * (int64_t)ks[KS_MOM].iter;
+        for (int k = KS_POIS; k < KS_COUNT; ++k) l += 4 * (int64_t)((ks[k].iter + 1) / 2);
+        stats->launches += l;
         for (int k = 0; k < KS_COUNT; ++k) {
             stats->last_it[k] = ks[k].iter;
             stats->sum_it[k] += ks[k].iter;
@@ -269,11 +274,44 @@ __global__ void k_ks_setup(KrylovState* st, double tol2, int maxit) {
 }
 
 // ---------------------------------------------------------------- loop control
+// Optional per-launch timing: every kernel launch of an eager step is bracketed by
+// two CUDA events on the launching stream (cgp_profile_step).
+struct Prof {
+    int n = 0, cap = 0;
+    cudaEvent_t* ev = nullptr;   // 2 per launch
+    int* id = nullptr;
+};
+
 struct Ctx {
     Solver* s;
     cudaStream_t st;
     bool capture;
+    Prof* prof = nullptr;
 };
+
+static inline int prof_begin(Ctx& c, int id) {
+    if (!c.prof || c.prof->n >= c.prof->cap) return -1;
+    const int k = c.prof->n++;
+    c.prof->id[k] = id;
+    cudaEventRecord(c.prof->ev[2 * k], c.st);
+    return k;
+}
+
+static inline void prof_end(Ctx& c, int k) {
+    if (k >= 0) cudaEventRecord(c.prof->ev[2 * k + 1], c.st);
+}
+
+#define PL(c, pid, ...)                  \
+    do {                                 \
+        const int k_ = prof_begin(c, pid); \
+        __VA_ARGS__;                     \
+        prof_end(c, k_);                 \
+    } while (0)
+
+// bounded busy wait that keeps the stream ahead of the host while profiling
+__global__ void k_spin(int iters) {
+    for (int i = 0; i < iters; ++i) __nanosleep(1000);
+}
 
 static inline int grid_rows(const Solver& s, int n, int lanes) {
     int dev = 0, sms = 148;
@@ -293,9 +331,11 @@ template <class Init, class Body>
 static int krylov_loop(Ctx& c, KrylovState* ks, int max_trips, Init init, Body body) {
     Solver& s = *c.s;
     if (!c.capture) {
+        if (c.prof) k_spin<<<1, 32, 0, c.st>>>(40);
         CGP_TRY(init(c.st, 0ull));
         const int chunk = 4;
         for (int trip = 0; trip < max_trips; trip += chunk) {
+            if (c.prof) k_spin<<<1, 32, 0, c.st>>>(40);
             for (int k = 0; k < chunk; ++k) CGP_TRY(body(c.st, 0ull));
             CGP_CUDA(cudaMemcpyAsync(s.h_flag, &ks->done, sizeof(int), cudaMemcpyDeviceToHost, c.st));
             CGP_CUDA(cudaStreamSynchronize(c.st));
@@ -337,21 +377,25 @@ static int krylov_loop(Ctx& c, KrylovState* ks, int max_trips, Init init, Body b
 // (the search direction alternates between two buffers).
 template <int NC>
 static int pcg(Ctx& c, CsrView A, const double* val, const double* dinv, double* b, double* x, KrylovState* ks,
-               double tol, int maxit, bool zero_x, bool project) {
+               double tol, int maxit, bool zero_x, bool project, int pid) {
     Solver& s = *c.s;
     const int gs = grid_rows(s, A.n, kLanes), gv = grid_rows(s, A.n, 1);
     auto init = [&, gs](cudaStream_t st, unsigned long long h) -> int {
-        k_ks_setup<<<1, 1, 0, st>>>(ks, tol * tol, maxit);
-        k_pcg_init<NC, kLanes><<<gs, kBlock, 0, st>>>(A, val, dinv, b, x, s.kr, s.kz, s.kp0, ks, s.partials,
-                                                      s.tickets, zero_x, project, h);
+        PL(c, pid, k_ks_setup<<<1, 1, 0, st>>>(ks, tol * tol, maxit));
+        PL(c, pid + 1, k_pcg_init<NC, kLanes><<<gs, kBlock, 0, st>>>(A, val, dinv, b, x, s.kr, s.kz, s.kp0, ks,
+                                                                     s.partials, s.tickets, zero_x, project, h));
         CGP_LAUNCH_CHECK();
         return CGP_OK;
     };
     auto body = [&, gs, gv](cudaStream_t st, unsigned long long h) -> int {
-        k_pcg_spmv<NC, kLanes><<<gs, kBlock, 0, st>>>(A, val, s.kz, s.kp0, s.kp1, s.kq, ks, s.partials, s.tickets);
-        k_pcg_update<NC><<<gv, kBlock, 0, st>>>(A.n, dinv, x, s.kr, s.kz, s.kp1, s.kq, ks, s.partials, s.tickets, h);
-        k_pcg_spmv<NC, kLanes><<<gs, kBlock, 0, st>>>(A, val, s.kz, s.kp1, s.kp0, s.kq, ks, s.partials, s.tickets);
-        k_pcg_update<NC><<<gv, kBlock, 0, st>>>(A.n, dinv, x, s.kr, s.kz, s.kp0, s.kq, ks, s.partials, s.tickets, h);
+        PL(c, pid + 2, k_pcg_spmv<NC, kLanes><<<gs, kBlock, 0, st>>>(A, val, s.kz, s.kp0, s.kp1, s.kq, ks, s.partials,
+                                                                     s.tickets));
+        PL(c, pid + 3, k_pcg_update<NC><<<gv, kBlock, 0, st>>>(A.n, dinv, x, s.kr, s.kz, s.kp1, s.kq, ks, s.partials,
+                                                               s.tickets, h));
+        PL(c, pid + 2, k_pcg_spmv<NC, kLanes><<<gs, kBlock, 0, st>>>(A, val, s.kz, s.kp1, s.kp0, s.kq, ks, s.partials,
+                                                                     s.tickets));
+        PL(c, pid + 3, k_pcg_update<NC><<<gv, kBlock, 0, st>>>(A.n, dinv, x, s.kr, s.kz, s.kp0, s.kq, ks, s.partials,
+                                                               s.tickets, h));
         CGP_LAUNCH_CHECK();
         return CGP_OK;
     };
@@ -364,17 +408,17 @@ static int bicgstab(Ctx& c, CsrView A, const double* val, const double* dinv, co
     const int gs = grid_rows(s, A.n, kLanes), gv = grid_rows(s, A.n, 1);
     BicgVecs V = s.bv;
     auto init = [&, gs, V](cudaStream_t st, unsigned long long h) -> int {
-        k_ks_setup<<<1, 1, 0, st>>>(ks, tol * tol, maxit);
-        k_bicg_init<kLanes><<<gs, kBlock, 0, st>>>(A, val, b, V, ks, s.partials, s.tickets, h);
+        PL(c, CGP_PROF_MOM_SETUP, k_ks_setup<<<1, 1, 0, st>>>(ks, tol * tol, maxit));
+        PL(c, CGP_PROF_MOM_INIT, k_bicg_init<kLanes><<<gs, kBlock, 0, st>>>(A, val, b, V, ks, s.partials, s.tickets, h));
         CGP_LAUNCH_CHECK();
         return CGP_OK;
     };
     auto body = [&, gs, gv, V](cudaStream_t st, unsigned long long h) -> int {
-        k_bicg_p<<<gv, kBlock, 0, st>>>(A.n, dinv, V, ks);
-        k_bicg_v<kLanes><<<gs, kBlock, 0, st>>>(A, val, V, ks, s.partials, s.tickets);
-        k_bicg_s<<<gv, kBlock, 0, st>>>(A.n, dinv, V, ks);
-        k_bicg_t<kLanes><<<gs, kBlock, 0, st>>>(A, val, V, ks, s.partials, s.tickets);
-        k_bicg_x<<<gv, kBlock, 0, st>>>(A.n, V, ks, s.partials, s.tickets, h);
+        PL(c, CGP_PROF_BICG_P, k_bicg_p<<<gv, kBlock, 0, st>>>(A.n, dinv, V, ks));
+        PL(c, CGP_PROF_BICG_V, k_bicg_v<kLanes><<<gs, kBlock, 0, st>>>(A, val, V, ks, s.partials, s.tickets));
+        PL(c, CGP_PROF_BICG_S, k_bicg_s<<<gv, kBlock, 0, st>>>(A.n, dinv, V, ks));
+        PL(c, CGP_PROF_BICG_T, k_bicg_t<kLanes><<<gs, kBlock, 0, st>>>(A, val, V, ks, s.partials, s.tickets));
+        PL(c, CGP_PROF_BICG_X, k_bicg_x<<<gv, kBlock, 0, st>>>(A.n, V, ks, s.partials, s.tickets, h));
         CGP_LAUNCH_CHECK();
         return CGP_OK;
     };
@@ -388,10 +432,11 @@ static int coarse_solve(Ctx& c) {
     CsrView Ac{C.nv, C.rowptr, C.col};
     const bool zero_x = s.prm.guess == CGP_GUESS_ZERO;
     CGP_TRY(pcg<1>(c, Ac, s.Kc0, s.dinvKc, s.rc, s.phi, &s.ks[KS_POIS], s.prm.tol_poisson, s.prm.max_it_poisson,
-                   zero_x, s.pure_neumann));
+                   zero_x, s.pure_neumann, CGP_PROF_POIS_SETUP));
     if (s.pure_neumann) {
-        k_phi_mean<<<grid_rows(s, C.nv, 1), kBlock, 0, c.st>>>(C.nv, s.mlumpC, s.phi, s.scal, s.partials, s.tickets);
-        k_sub_scalar<<<grid_rows(s, C.nv, 1), kBlock, 0, c.st>>>(C.nv, s.phi, s.scal);
+        PL(c, CGP_PROF_PHI_MEAN, k_phi_mean<<<grid_rows(s, C.nv, 1), kBlock, 0, c.st>>>(C.nv, s.mlumpC, s.phi, s.scal,
+                                                                                        s.partials, s.tickets));
+        PL(c, CGP_PROF_PHI_SUB, k_sub_scalar<<<grid_rows(s, C.nv, 1), kBlock, 0, c.st>>>(C.nv, s.phi, s.scal));
         CGP_LAUNCH_CHECK();
     }
     return CGP_OK;
@@ -403,7 +448,7 @@ static int prolong_all(Ctx& c) {
         const Level& Lc = s.mesh->lev[l];
         const Level& Lf = s.mesh->lev[l + 1];
         const int n_new = Lf.nv - Lc.nv;
-        k_prolong<<<grid_rows(s, n_new, 1), kBlock, 0, c.st>>>(n_new, Lc.nv, Lf.parents, s.phi);
+        PL(c, CGP_PROF_PROLONG, k_prolong<<<grid_rows(s, n_new, 1), kBlock, 0, c.st>>>(n_new, Lc.nv, Lf.parents, s.phi));
     }
     CGP_LAUNCH_CHECK();
     return CGP_OK;
@@ -418,35 +463,44 @@ static int step_body(Ctx& c) {
     CsrView Af{F.nv, F.rowptr, F.col}, Ac{C.nv, C.rowptr, C.col};
     const int gv = grid_rows(s, F.nv, 1), gs = grid_rows(s, F.nv, kLanes);
     // Eq. 21: momentum
-    k_mom_prep<<<gv, kBlock, 0, c.st>>>(F.nv, s.U, s.Uprev, F.xy, bc, s.tdev, p.dt, s.w, s.h);
-    k_mom_assemble<<<gv, kBlock, 0, c.st>>>(F.nv, F.rowptr, F.col, F.vt_ptr, F.vt_list, F.tri, s.geo, s.vtslot, s.S,
-                                            s.M, s.CxT, s.CyT, s.P, s.w, s.h, F.tag, F.xy, bc, s.tdev, p.dt, s.A,
-                                            s.dinvA, s.b, s.Ut);
+    PL(c, CGP_PROF_MOM_PREP, k_mom_prep<<<gv, kBlock, 0, c.st>>>(F.nv, s.U, s.Uprev, F.xy, bc, s.tdev, p.dt, s.w, s.h));
+    PL(c, CGP_PROF_MOM_ASSEMBLE,
+       k_mom_assemble<<<gv, kBlock, 0, c.st>>>(F.nv, F.rowptr, F.col, F.vt_ptr, F.vt_list, F.tri, s.geo, s.vtslot, s.S,
+                                               s.M, s.CxT, s.CyT, s.P, s.w, s.h, F.tag, F.xy, bc, s.tdev, p.dt, s.A,
+                                               s.dinvA, s.b, s.Ut));
     CGP_LAUNCH_CHECK();
     CGP_TRY(bicgstab(c, Af, s.A, s.dinvA, s.b, &s.ks[KS_MOM], p.tol_mom, p.max_it_mom));
     // Eqs. 22-23: injection, coarse divergence, coarse Poisson solve
-    k_coarse_rhs<kLanes><<<grid_rows(s, C.nv, kLanes), kBlock, 0, c.st>>>(
-        Ac, s.Cxc, s.Cyc, s.Ut, C.tag, p.dt, s.rc, &s.ks[KS_POIS], s.pure_neumann, s.partials, s.tickets);
+    PL(c, CGP_PROF_COARSE_RHS,
+       k_coarse_rhs<kLanes><<<grid_rows(s, C.nv, kLanes), kBlock, 0, c.st>>>(
+           Ac, s.Cxc, s.Cyc, s.Ut, C.tag, p.dt, s.rc, &s.ks[KS_POIS], s.pure_neumann, s.partials, s.tickets));
     CGP_LAUNCH_CHECK();
     CGP_TRY(coarse_solve(c));
     // Eq. 24: prolongation
     CGP_TRY(prolong_all(c));
     // Eq. 25: velocity correction
     const bool lumped = p.mass_mode == CGP_MASS_LUMPED;
-    k_corr_rhs<kLanes><<<gs, kBlock, 0, c.st>>>(Af, s.Cx, s.Cy, s.phi, F.tag, p.dt, s.g, lumped ? s.mlumpF : nullptr,
-                                                s.delta);
+    PL(c, CGP_PROF_CORR_RHS,
+       k_corr_rhs<kLanes><<<gs, kBlock, 0, c.st>>>(Af, s.Cx, s.Cy, s.phi, F.tag, p.dt, s.g,
+                                                   lumped ? s.mlumpF : nullptr, s.delta));
     CGP_LAUNCH_CHECK();
     if (!lumped)
-        CGP_TRY(pcg<2>(c, Af, s.M0, s.dinvM0, s.g, s.delta, &s.ks[KS_CORR], p.tol_mass, p.max_it_mass, true, false));
+        CGP_TRY(pcg<2>(c, Af, s.M0, s.dinvM0, s.g, s.delta, &s.ks[KS_CORR], p.tol_mass, p.max_it_mass, true, false,
+                       CGP_PROF_CORR_SETUP));
     // Eq. 26: pressure
     if (p.chi) {
-        k_div<kLanes><<<gs, kBlock, 0, c.st>>>(Af, s.Cx, s.Cy, s.Ut, s.div, lumped ? s.mlumpF : nullptr, s.qrot);
+        PL(c, CGP_PROF_DIV,
+           k_div<kLanes><<<gs, kBlock, 0, c.st>>>(Af, s.Cx, s.Cy, s.Ut, s.div, lumped ? s.mlumpF : nullptr, s.qrot));
         CGP_LAUNCH_CHECK();
         if (!lumped)
-            CGP_TRY(pcg<1>(c, Af, s.M, s.dinvM, s.div, s.qrot, &s.ks[KS_MASS], p.tol_mass, p.max_it_mass, true, false));
+            CGP_TRY(pcg<1>(c, Af, s.M, s.dinvM, s.div, s.qrot, &s.ks[KS_MASS], p.tol_mass, p.max_it_mass, true, false,
+                           CGP_PROF_MASS_SETUP));
     }
-    k_finish<<<gv, kBlock, 0, c.st>>>(F.nv, s.U, s.Uprev, s.Ut, s.delta, s.P, s.phi, s.qrot, p.chi, 1.0 / p.Re,
-                                      s.tdev, p.dt, s.stats, s.ks);
+    const int fixed = 4 + 1 + 2 + (s.pure_neumann ? 2 : 0) + (s.lf - s.lc) + 1 + (lumped ? 0 : 2) +
+                      (p.chi ? 1 + (lumped ? 0 : 2) : 0) + 1;
+    PL(c, CGP_PROF_FINISH,
+       k_finish<<<gv, kBlock, 0, c.st>>>(F.nv, s.U, s.Uprev, s.Ut, s.delta, s.P, s.phi, s.qrot, p.chi, 1.0 / p.Re,
+                                         s.tdev, p.dt, s.stats, s.ks, fixed));
     CGP_LAUNCH_CHECK();
     return CGP_OK;
 }
@@ -559,6 +613,7 @@ extern "C" int cgp_get_fields(cgp_solver* h, double* U, double* P, double* t, cg
     if (t) *t = th;
     if (stats) {
         stats->steps = ds.steps;
+        stats->launches = ds.launches;
         stats->t = th;
         stats->it_mom = ds.last_it[KS_MOM];
         stats->it_poisson = ds.last_it[KS_POIS];
@@ -609,6 +664,59 @@ extern "C" int cgp_get_vector(cgp_solver* h, int32_t which, double* out, int32_t
     CGP_TRY(copy_out(out, src, n * sizeof(double), where, st));
     if (where == CGP_HOST) CGP_CUDA(cudaStreamSynchronize(st));
     return CGP_OK;
+}
+
+extern "C" int cgp_profile_step(cgp_solver* h, cgp_stream_t stream, int32_t n_ids, int32_t* counts,
+                                double* total_ms) {
+    clear_error();
+    if (!h || !counts || !total_ms || n_ids < CGP_PROF_COUNT) {
+        set_error("cgp_profile_step: bad arguments");
+        return CGP_EINVAL;
+    }
+    Solver& s = h->s;
+    cudaStream_t st = (cudaStream_t)stream;
+    Prof pr;
+    pr.cap = 4096;
+    std::vector<cudaEvent_t> ev(2 * pr.cap);
+    std::vector<int> ids(pr.cap);
+    for (auto& e : ev) CGP_CUDA(cudaEventCreate(&e));
+    pr.ev = ev.data();
+    pr.id = ids.data();
+    Ctx c{&s, st, false, &pr};
+    int rc = step_body(c);
+    KrylovState ks[KS_COUNT];
+    if (rc == CGP_OK) {
+        CGP_CUDA(cudaMemcpyAsync(ks, s.ks, sizeof(ks), cudaMemcpyDeviceToHost, st));
+        CGP_CUDA(cudaStreamSynchronize(st));
+        for (int i = 0; i < n_ids; ++i) {
+            counts[i] = 0;
+            total_ms[i] = 0.0;
+        }
+        // launches of loop kernels after their solve finished returned at once: keep the
+        // first `iter` launches of each loop kernel (they run in order)
+        auto solve_of = [](int id) {
+            if (id >= CGP_PROF_BICG_P && id <= CGP_PROF_BICG_X) return (int)KS_MOM;
+            if (id == CGP_PROF_POIS_SPMV || id == CGP_PROF_POIS_UPDATE) return (int)KS_POIS;
+            if (id == CGP_PROF_CORR_SPMV || id == CGP_PROF_CORR_UPDATE) return (int)KS_CORR;
+            if (id == CGP_PROF_MASS_SPMV || id == CGP_PROF_MASS_UPDATE) return (int)KS_MASS;
+            return -1;
+        };
+        for (int k = 0; k < pr.n; ++k) {
+            const int id = pr.id[k];
+            const int sv = solve_of(id);
+            if (sv >= 0 && counts[id] >= ks[sv].iter) continue;
+            float ms = 0.f;
+            CGP_CUDA(cudaEventElapsedTime(&ms, ev[2 * k], ev[2 * k + 1]));
+            counts[id] += 1;
+            total_ms[id] += ms;
+        }
+        if (pr.n >= pr.cap) {
+            set_error("profile truncated after %d launches", pr.cap);
+            rc = CGP_ENOMEM;
+        }
+    }
+    for (auto& e : ev) cudaEventDestroy(e);
+    return rc;
 }
 
 extern "C" int cgp_set_vector(cgp_solver* h, int32_t which, const double* in, int32_t where, cgp_stream_t stream) {
