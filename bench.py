@@ -107,12 +107,47 @@ def workload_problem(name):
     return w, w.base_mesh()
 
 
-def make_params(cg, w, form):
+def make_params(cg, w, form, use_graph=1):
     mixed = form in ("mixed", "mixed_learned")
+    learned = form in ("learned", "mixed_learned")
     return cg.make_params(w.Re, w.dt, chi=w.chi, k=w.k, tol_mom=w.tol_mom, tol_poisson=w.tol_poisson,
                           tol_mass=1e-10, max_it_mom=1000, max_it_poisson=20000, max_it_mass=1000,
                           precision=cg.CGP_MIXED if mixed else cg.CGP_FP64,
-                          guess=cg.CGP_GUESS_PREV, bc_kind=w.bc, bc_param=w.bc_param, use_graph=1)
+                          guess=cg.CGP_GUESS_LEARNED if learned else cg.CGP_GUESS_PREV, bc_kind=w.bc,
+                          bc_param=w.bc_param, use_graph=use_graph)
+
+
+def train_guess(cg, w, args):
+    """Train the learned-guess network on a held-out seed of the same workload (the timed
+    run uses seed w.base_n).  Returns (FP32 parameter vector, info dict)."""
+    import torch
+    from paper_1812_00185_gb300.learned import PairStore, train, init_params
+    from workloads import channel_cylinder_mesh, square_mesh
+    t0 = time.time()
+    if w.base == "channel":
+        base = channel_cylinder_mesh(seed=w.base_n + 1, h=w.extra.get("h", 0.0084))
+    else:
+        base = w.base_mesh()
+    mesh = cg.Mesh(base.xy, base.tri, base.tag, w.n_levels)
+    rec = cg.Solver(mesh, make_params(cg, w, "fp64"))
+    store = PairStore(rec.nc, args.train_pairs)
+    store.record(rec, args.train_pairs)
+    rec.close()
+    torch.cuda.synchronize()
+    t_rec = time.time() - t0
+    net = cg.cgp_mlp_create(mesh.handle, w.n_levels - w.k, 8)
+    cg.cgp_mlp_set_params(net, init_params(0))
+    t1 = time.time()
+    hist = train(net, store, args.train_iters, batch=8, lr=2e-3, log_every=max(1, args.train_iters // 4))
+    torch.cuda.synchronize()
+    t_train = time.time() - t1
+    p = cg.cgp_mlp_get_params(net)
+    cg.cgp_mlp_destroy(net)
+    del store
+    mesh.close()
+    return p, {"pairs": args.train_pairs, "iters": args.train_iters, "record_s": round(t_rec, 2),
+               "train_s": round(t_train, 2), "loss": [(int(i), round(float(l), 5)) for i, l in hist],
+               "train_mesh_seed": w.base_n + 1}
 
 
 # algorithmic bytes per launch of each kernel kind (int32 indices, FP64 values);
@@ -151,9 +186,17 @@ def run_gpu(args, rank, world):
     nv_f, nt_f, nnz_f = mesh.info(w.n_levels)
     nv_c, nt_c, nnz_c = mesh.info(w.n_levels - w.k)
 
+    learned = {}
+    if args.form in ("learned", "mixed_learned"):
+        learned["params"], learned["info"] = train_guess(cg, w, args)
+        learned["net"] = cg.cgp_mlp_create(mesh.handle, w.n_levels - w.k, 1)
+        cg.cgp_mlp_set_params(learned["net"], learned["params"])
+
     def run_form(form, steps, warmup, timed=True):
         t0 = time.time()
-        s = cg.Solver(mesh, make_params(cg, w, form))
+        s = cg.Solver(mesh, make_params(cg, w, form, args.graph))
+        if form in ("learned", "mixed_learned"):
+            cg.cgp_guess_set(s.handle, learned["net"])
         torch.cuda.synchronize()
         t_asm = time.time() - t0
         s.step(warmup)
@@ -173,6 +216,7 @@ def run_gpu(args, rank, world):
         U, P, t, st1, rc = s.fields()
         its = {k: (st1["sum_it_" + k] - st0["sum_it_" + k]) / steps for k in ("mom", "poisson", "corr", "mass")}
         return s, {"ms": ms, "ms_per_step": ms / steps, "steps_per_s": 1000.0 * steps / ms, "iters": its,
+                   "guess_used": st1["guess_used"] - st0["guess_used"],
                    "launches": st1["launches"] - st0["launches"], "status": rc,
                    "res_poisson": st1["res_poisson"], "res_mom": st1["res_mom"], "assemble_s": t_asm,
                    "clocks": clk.summary()}
@@ -181,11 +225,14 @@ def run_gpu(args, rank, world):
     s, head = run_form(head_form, args.steps, args.warmup)
     ws_bytes = s.workspace.numel()
     # the plain FP64 form, for the comparison the metric names
-    forms = {head_form: {k: head[k] for k in ("steps_per_s", "ms_per_step", "iters", "status")}}
-    if head_form != "fp64" and not args.quick:
-        s2, plain = run_form("fp64", args.steps, args.warmup)
-        forms["fp64"] = {k: plain[k] for k in ("steps_per_s", "ms_per_step", "iters", "status")}
-        s2.close()
+    keys = ("steps_per_s", "ms_per_step", "iters", "status", "guess_used", "res_poisson")
+    forms = {head_form: {k: head[k] for k in keys}}
+    if not args.quick:
+        for other in ("fp64", "mixed"):
+            if other != head_form:
+                s2, res = run_form(other, args.steps, args.warmup)
+                forms[other] = {k: res[k] for k in keys}
+                s2.close()
 
     # end to end through the C ABI: pinned host state in, one step, state out, every step
     Uh = torch.empty((nv_f, 2), dtype=torch.float64, pin_memory=True)
@@ -245,7 +292,7 @@ def run_gpu(args, rank, world):
         "metric": METRIC, "value": round(head["steps_per_s"] * world, 3), "unit": "steps/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(head["ms_per_step"], 4),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64" if head_form == "fp64" else "f32+f64", "data": "synthetic",
+        "dtype": "f32+f64" if "mixed" in head_form else "f64", "data": "synthetic",
         "config": {"workload": args.workload, "form": head_form, "fine_triangles": nt_f, "fine_vertices": nv_f,
                    "coarse_vertices": nv_c, "k": w.k, "chi": w.chi, "Re": w.Re, "dt": w.dt,
                    "tol": w.tol_poisson, "parallelism": "replicas" if world > 1 else "single",
@@ -254,6 +301,9 @@ def run_gpu(args, rank, world):
         "forms": forms, "kernels": kern, "setup_s": {"mesh": round(t_mesh, 3), "assemble": round(head["assemble_s"], 3)},
         "pcg_hbm": pcg,
     }
+    if learned:
+        out["learned"] = learned["info"]
+        cg.cgp_mlp_destroy(learned["net"])
     return out, (w, base)
 
 
@@ -322,10 +372,14 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--workload", default="channel1m_k2")
-    ap.add_argument("--form", default="fp64", choices=["fp64", "mixed", "mixed_learned"])
+    ap.add_argument("--form", default="mixed_learned", choices=["fp64", "mixed", "learned", "mixed_learned"])
+    ap.add_argument("--train-pairs", type=int, default=150)
+    ap.add_argument("--train-iters", type=int, default=400)
     ap.add_argument("--pcg-n", type=int, default=2048)
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--quick", action="store_true", help="skip the secondary measurements")
+    ap.add_argument("--graph", type=int, default=1, choices=[0, 1],
+                    help="1: replay steps as CUDA graphs; 0: eager launches (what ncu can profile)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "gpu":
         args.warmup = 3

@@ -58,7 +58,10 @@ enum {
     CGP_BC_TG_PERIODIC = 3   /* Taylor-Green with amplitude cos(2 pi t) and the body force that makes it exact */
 };
 enum { CGP_FP64 = 0, CGP_MIXED = 1 };                   /* precision of the coarse Poisson solve */
-enum { CGP_GUESS_ZERO = 0, CGP_GUESS_PREV = 1 };          /* initial guess of the coarse Poisson solve */
+/* initial guess of the coarse Poisson solve: zero, the previous step's increment, or the
+ * learned network's prediction (falls back to the previous increment whenever that one has
+ * the smaller FP64 residual, and until cgp_guess_set provides weights) */
+enum { CGP_GUESS_ZERO = 0, CGP_GUESS_PREV = 1, CGP_GUESS_LEARNED = 2 };
 enum { CGP_MASS_CONSISTENT = 0, CGP_MASS_LUMPED = 1 };    /* mass matrix of Eqs. 25-26 (lumped = Eq. 27) */
 enum { CGP_HOST = 0, CGP_DEVICE = 1 };
 
@@ -90,7 +93,17 @@ typedef struct {
     int32_t bc_kind;           /* CGP_BC_* */
     double bc_param[4];
     int32_t use_graph;         /* 1: replay each step as a CUDA graph with device-side loop control */
+    double tol_inner;          /* CGP_MIXED: residual reduction asked of each FP32 inner solve (0 = 1e-4) */
+    int32_t coarse_mode;       /* coarse Poisson solver: CGP_COARSE_AUTO | _GRID | _CLUSTER */
+    int32_t cluster_size;      /* CTAs of the cluster solver (0 = largest that fits, else 2..16) */
 } cgp_params;
+
+/* Coarse Poisson solver kinds.  KERNELS: two kernel launches per PCG iteration (graph
+ * WHILE loop).  PERSISTENT: the whole solve in one cooperative launch over the GPU with a
+ * bounded software grid barrier.  CLUSTER: the whole solve in one launch of one
+ * thread-block cluster, reductions through distributed shared memory.  AUTO = PERSISTENT.
+ * CGP_MIXED needs PERSISTENT or CLUSTER. */
+enum { CGP_COARSE_AUTO = 0, CGP_COARSE_KERNELS = 1, CGP_COARSE_CLUSTER = 2, CGP_COARSE_PERSISTENT = 3 };
 
 /* Per-run statistics. */
 typedef struct {
@@ -101,6 +114,7 @@ typedef struct {
     double res_mom, res_poisson;                           /* last relative residuals (max over components) */
     int32_t status;            /* first non-zero CGP_E* code seen by any solve, else 0 */
     int64_t launches;          /* kernel launches of graph-replayed steps (Krylov loop trips included) */
+    int64_t guess_used;        /* steps whose coarse solve started from the learned prediction */
 } cgp_stats;
 
 /* Library message for the last failing call of this thread ("" if none). */
@@ -187,11 +201,40 @@ enum {
     CGP_PROF_PHI_MEAN, CGP_PROF_PHI_SUB, CGP_PROF_PROLONG,
     CGP_PROF_CORR_RHS, CGP_PROF_CORR_SETUP, CGP_PROF_CORR_INIT, CGP_PROF_CORR_SPMV, CGP_PROF_CORR_UPDATE,
     CGP_PROF_DIV, CGP_PROF_MASS_SETUP, CGP_PROF_MASS_INIT, CGP_PROF_MASS_SPMV, CGP_PROF_MASS_UPDATE,
-    CGP_PROF_FINISH, CGP_PROF_COUNT
+    CGP_PROF_FINISH, CGP_PROF_POIS_CLUSTER, CGP_PROF_MLP, CGP_PROF_COUNT
 };
 int cgp_profile_step(cgp_solver* s, cgp_stream_t stream, int32_t n_ids, int32_t* counts, double* total_ms);
 
 void cgp_solver_destroy(cgp_solver* s);
+
+/* ---- learned initial guess (not in the paper) ----
+ * A per-vertex MLP on one mesh level with 1-ring mean aggregation: inputs per vertex
+ * (r/rms(r), q/rms(q), x, y) with r the coarse right-hand side of Eq. 23 and q the previous
+ * step's Phi_c; layers a_l = W_l [h; mean over neighbours of h] + b_l, widths 4-64-64-1,
+ * ReLU between layers; prediction Phi0 = q + rms(q) a_3.  Weights are bfloat16 in the
+ * forward pass (FP32 arithmetic) with FP32 master weights and Adam.  Parameter vector
+ * layout: W1[64][8], b1[64], W2[64][128], b2[64], W3[1][128], b3[1] (row-major, FP32).
+ * The network owns device memory allocated by cgp_mlp_create. */
+typedef struct cgp_mlp cgp_mlp;
+int cgp_mlp_param_count(void);
+/* Network for `level` of `mesh` (the mesh must outlive it) with room for max_batch samples;
+ * all parameters start at zero (then the prediction is q itself). */
+int cgp_mlp_create(const cgp_mesh* mesh, int32_t level, int32_t max_batch, cgp_mlp** out);
+int cgp_mlp_set_params(cgp_mlp* m, const float* params, int32_t where, cgp_stream_t stream);  /* resets Adam */
+int cgp_mlp_get_params(cgp_mlp* m, float* params, int32_t where, cgp_stream_t stream);
+/* pred = Phi0 for `batch` samples; r, q, pred: device arrays of batch * N doubles. Asynchronous. */
+int cgp_mlp_forward(cgp_mlp* m, const double* r, const double* q, int32_t batch, double* pred, cgp_stream_t stream);
+/* loss = mean (a_3 - clip((target - q)/rms(q), -10, 10))^2 and its gradient w.r.t. the parameters (host
+ * array of cgp_mlp_param_count floats); r, q, target on the device.  Synchronises. */
+int cgp_mlp_grad(cgp_mlp* m, const double* r, const double* q, const double* target, int32_t batch, float* grad,
+                 float* loss, cgp_stream_t stream);
+/* one Adam step (beta1 0.9, beta2 0.999, eps 1e-8) on a batch; loss (host, may be NULL: no sync) */
+int cgp_mlp_train_step(cgp_mlp* m, const double* r, const double* q, const double* target, int32_t batch, float lr,
+                       float* loss, cgp_stream_t stream);
+/* Copy the network's weights into a solver assembled with guess = CGP_GUESS_LEARNED whose
+ * pressure-increment level is the network's level.  Synchronises. */
+int cgp_guess_set(cgp_solver* s, const cgp_mlp* m, cgp_stream_t stream);
+void cgp_mlp_destroy(cgp_mlp* m);
 
 #ifdef __cplusplus
 }

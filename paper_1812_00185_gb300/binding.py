@@ -19,8 +19,9 @@ CGP_OK, CGP_EINVAL, CGP_ENOTCONV, CGP_EBREAKDOWN, CGP_ENONFINITE, CGP_ETIMEOUT, 
 CGP_VEL_DIR, CGP_PHI_ZERO = 1, 2
 CGP_BC_CAVITY, CGP_BC_CHANNEL, CGP_BC_TG, CGP_BC_TG_PERIODIC = 0, 1, 2, 3
 CGP_FP64, CGP_MIXED = 0, 1
-CGP_GUESS_ZERO, CGP_GUESS_PREV = 0, 1
+CGP_GUESS_ZERO, CGP_GUESS_PREV, CGP_GUESS_LEARNED = 0, 1, 2
 CGP_MASS_CONSISTENT, CGP_MASS_LUMPED = 0, 1
+CGP_COARSE_AUTO, CGP_COARSE_KERNELS, CGP_COARSE_CLUSTER, CGP_COARSE_PERSISTENT = 0, 1, 2, 3
 CGP_HOST, CGP_DEVICE = 0, 1
 (CGP_VEC_U, CGP_VEC_UPREV, CGP_VEC_P, CGP_VEC_UTILDE, CGP_VEC_RHS_C, CGP_VEC_PHI_C,
  CGP_VEC_PHI_F) = range(7)
@@ -47,14 +48,16 @@ class Params(ctypes.Structure):
                 ("tol_mom", c_double), ("tol_poisson", c_double), ("tol_mass", c_double),
                 ("max_it_mom", c_int32), ("max_it_poisson", c_int32), ("max_it_mass", c_int32),
                 ("precision", c_int32), ("guess", c_int32), ("mass_mode", c_int32), ("bc_kind", c_int32),
-                ("bc_param", c_double * 4), ("use_graph", c_int32)]
+                ("bc_param", c_double * 4), ("use_graph", c_int32), ("tol_inner", c_double),
+                ("coarse_mode", c_int32), ("cluster_size", c_int32)]
 
 
 class Stats(ctypes.Structure):
     _fields_ = [("steps", c_int64), ("t", c_double), ("it_mom", c_int32), ("it_poisson", c_int32),
                 ("it_corr", c_int32), ("it_mass", c_int32), ("sum_it_mom", c_int64),
                 ("sum_it_poisson", c_int64), ("sum_it_corr", c_int64), ("sum_it_mass", c_int64),
-                ("res_mom", c_double), ("res_poisson", c_double), ("status", c_int32), ("launches", c_int64)]
+                ("res_mom", c_double), ("res_poisson", c_double), ("status", c_int32), ("launches", c_int64),
+                ("guess_used", c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -82,12 +85,23 @@ _SIGS = {
     "cgp_prolong": (c_int32, [c_void_p, c_void_p, c_void_p, c_int32, c_void_p]),
     "cgp_profile_step": (c_int32, [c_void_p, c_void_p, c_int32, c_void_p, c_void_p]),
     "cgp_solver_destroy": (None, [c_void_p]),
+    "cgp_mlp_param_count": (c_int32, []),
+    "cgp_mlp_create": (c_int32, [c_void_p, c_int32, c_int32, POINTER(c_void_p)]),
+    "cgp_mlp_set_params": (c_int32, [c_void_p, c_void_p, c_int32, c_void_p]),
+    "cgp_mlp_get_params": (c_int32, [c_void_p, c_void_p, c_int32, c_void_p]),
+    "cgp_mlp_forward": (c_int32, [c_void_p, c_void_p, c_void_p, c_int32, c_void_p, c_void_p]),
+    "cgp_mlp_grad": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_int32, c_void_p, POINTER(ctypes.c_float),
+                               c_void_p]),
+    "cgp_mlp_train_step": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_int32, ctypes.c_float,
+                                     POINTER(ctypes.c_float), c_void_p]),
+    "cgp_guess_set": (c_int32, [c_void_p, c_void_p, c_void_p]),
+    "cgp_mlp_destroy": (None, [c_void_p]),
 }
 
 PROF_NAMES = ["mom_prep", "mom_assemble", "mom_setup", "mom_init", "bicg_p", "bicg_v", "bicg_s", "bicg_t",
               "bicg_x", "coarse_rhs", "pois_setup", "pois_init", "pois_spmv", "pois_update", "phi_mean",
               "phi_sub", "prolong", "corr_rhs", "corr_setup", "corr_init", "corr_spmv", "corr_update", "div",
-              "mass_setup", "mass_init", "mass_spmv", "mass_update", "finish"]
+              "mass_setup", "mass_init", "mass_spmv", "mass_update", "finish", "pois_onelaunch", "mlp_forward"]
 
 _LIB = None
 
@@ -179,7 +193,7 @@ def cgp_mesh_destroy(mesh):
 def make_params(Re, dt, chi=0, k=1, tol_mom=1e-10, tol_poisson=1e-10, tol_mass=1e-12, max_it_mom=500,
                 max_it_poisson=20000, max_it_mass=500, precision=CGP_FP64, guess=CGP_GUESS_PREV,
                 mass_mode=CGP_MASS_CONSISTENT, bc_kind=CGP_BC_CAVITY, bc_param=(1.0, 0.0, 0.0, 0.0),
-                use_graph=1):
+                use_graph=1, tol_inner=0.0, coarse_mode=0, cluster_size=0):
     p = Params()
     p.Re, p.dt, p.chi, p.k = Re, dt, chi, k
     p.tol_mom, p.tol_poisson, p.tol_mass = tol_mom, tol_poisson, tol_mass
@@ -188,6 +202,7 @@ def make_params(Re, dt, chi=0, k=1, tol_mom=1e-10, tol_poisson=1e-10, tol_mass=1
     for i in range(4):
         p.bc_param[i] = bc_param[i] if i < len(bc_param) else 0.0
     p.use_graph = use_graph
+    p.tol_inner, p.coarse_mode, p.cluster_size = tol_inner, coarse_mode, cluster_size
     return p
 
 
@@ -246,6 +261,11 @@ def cgp_get_vector(solver, which, stream=None):
     return out.reshape(-1, 2) if n == 2 * nf and which in (CGP_VEC_U, CGP_VEC_UPREV, CGP_VEC_UTILDE) else out
 
 
+def cgp_get_vector_device(solver, which, out, stream=None):
+    """Device-to-device copy of a solver vector into a torch tensor (no synchronisation)."""
+    _check(load().cgp_get_vector(solver, which, _ptr(out), CGP_DEVICE, _stream(stream)))
+
+
 def cgp_set_vector(solver, which, data, stream=None):
     data = np.ascontiguousarray(data, dtype=np.float64)
     _check(load().cgp_set_vector(solver, which, _ptr(data), CGP_HOST, _stream(stream)))
@@ -287,6 +307,57 @@ def cgp_profile_step(solver, stream=None):
 
 def cgp_solver_destroy(solver):
     load().cgp_solver_destroy(solver)
+
+
+# ---------------------------------------------------------------- learned guess
+def cgp_mlp_param_count():
+    return int(load().cgp_mlp_param_count())
+
+
+def cgp_mlp_create(mesh, level, max_batch):
+    out = c_void_p()
+    _check(load().cgp_mlp_create(mesh, int(level), int(max_batch), byref(out)))
+    return out
+
+
+def cgp_mlp_set_params(m, params, stream=None):
+    params = np.ascontiguousarray(params, dtype=np.float32)
+    assert params.size == cgp_mlp_param_count()
+    _check(load().cgp_mlp_set_params(m, _ptr(params), CGP_HOST, _stream(stream)))
+
+
+def cgp_mlp_get_params(m, stream=None):
+    out = np.empty(cgp_mlp_param_count(), np.float32)
+    _check(load().cgp_mlp_get_params(m, _ptr(out), CGP_HOST, _stream(stream)))
+    return out
+
+
+def cgp_mlp_forward(m, r, q, batch, pred, stream=None):
+    """r, q, pred: device tensors of batch * N doubles."""
+    _check(load().cgp_mlp_forward(m, _ptr(r), _ptr(q), int(batch), _ptr(pred), _stream(stream)))
+
+
+def cgp_mlp_grad(m, r, q, target, batch, stream=None):
+    g = np.empty(cgp_mlp_param_count(), np.float32)
+    loss = ctypes.c_float()
+    _check(load().cgp_mlp_grad(m, _ptr(r), _ptr(q), _ptr(target), int(batch), _ptr(g), byref(loss),
+                               _stream(stream)))
+    return float(loss.value), g
+
+
+def cgp_mlp_train_step(m, r, q, target, batch, lr, want_loss=True, stream=None):
+    loss = ctypes.c_float()
+    _check(load().cgp_mlp_train_step(m, _ptr(r), _ptr(q), _ptr(target), int(batch), float(lr),
+                                     byref(loss) if want_loss else None, _stream(stream)))
+    return float(loss.value) if want_loss else None
+
+
+def cgp_guess_set(solver, m, stream=None):
+    _check(load().cgp_guess_set(solver, m, _stream(stream)))
+
+
+def cgp_mlp_destroy(m):
+    load().cgp_mlp_destroy(m)
 
 
 # ---------------------------------------------------------------- convenience objects

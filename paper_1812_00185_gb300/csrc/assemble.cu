@@ -38,7 +38,7 @@ __device__ __forceinline__ int find_slot(const int32_t* __restrict__ col, int b,
 
 // Row i of M, K, Cx, Cy (and optionally Cx^T, Cy^T) plus the packed corner slots.
 __global__ void k_static_rows(int nv, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
-                              const int32_t* __restrict__ vt_ptr, const int32_t* __restrict__ vt_list,
+                              const int32_t* __restrict__ sell_ptr, const int32_t* __restrict__ vt_ptr, const int32_t* __restrict__ vt_list,
                               const int32_t* __restrict__ tri, const double* __restrict__ geo,
                               double* __restrict__ M, double* __restrict__ K, double* __restrict__ Cx,
                               double* __restrict__ Cy, double* __restrict__ CxT, double* __restrict__ CyT,
@@ -46,7 +46,8 @@ __global__ void k_static_rows(int nv, const int32_t* __restrict__ rowptr, const 
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nv) return;
     const int rb = rowptr[i], re = rowptr[i + 1];
-    for (int q = rb; q < re; ++q) {
+    for (int k = 0; k < re - rb; ++k) {
+        const int64_t q = sell_pos(sell_ptr, i, k);
         M[q] = 0.0;
         K[q] = 0.0;
         Cx[q] = 0.0;
@@ -66,7 +67,7 @@ __global__ void k_static_rows(int nv, const int32_t* __restrict__ rowptr, const 
         const double gix = gt[1 + 2 * li], giy = gt[2 + 2 * li];
         for (int k = 0; k < 3; ++k) {
             if (slots[k] < 0) continue;   // cannot happen for a consistent adjacency
-            const int q = rb + slots[k];
+            const int64_t q = sell_pos(sell_ptr, i, slots[k]);
             const double gkx = gt[1 + 2 * k], gky = gt[2 + 2 * k];
             M[q] += area / 12.0 * (k == li ? 2.0 : 1.0);
             K[q] += area * (gix * gkx + giy * gky);
@@ -80,7 +81,7 @@ __global__ void k_static_rows(int nv, const int32_t* __restrict__ rowptr, const 
 
 // out = A with the rows/columns of flagged vertices replaced by the identity; dinv = 1/out_ii
 __global__ void k_eliminate(int nv, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
-                            const double* __restrict__ A, const uint8_t* __restrict__ tag, int flag,
+                            const int32_t* __restrict__ sell_ptr, const double* __restrict__ A, const uint8_t* __restrict__ tag, int flag,
                             double* __restrict__ out, double* __restrict__ dinv) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nv) return;
@@ -88,10 +89,11 @@ __global__ void k_eliminate(int nv, const int32_t* __restrict__ rowptr, const in
     double d = 1.0;
     for (int q = rowptr[i]; q < rowptr[i + 1]; ++q) {
         const int j = col[q];
+        const int64_t e = sell_pos(sell_ptr, i, q - rowptr[i]);
         double a;
         if (fi || (tag[j] & flag)) a = (i == j) ? 1.0 : 0.0;
-        else a = A[q];
-        out[q] = a;
+        else a = A[e];
+        out[e] = a;
         if (j == i) d = a;
     }
     dinv[i] = 1.0 / d;
@@ -99,18 +101,32 @@ __global__ void k_eliminate(int nv, const int32_t* __restrict__ rowptr, const in
 
 // S = a M + c K; also dinvM = 1/M_ii and the lumped mass (row sums of M)
 __global__ void k_combine(int nv, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
-                          const double* __restrict__ M, const double* __restrict__ K, double a, double c,
+                          const int32_t* __restrict__ sell_ptr, const double* __restrict__ M, const double* __restrict__ K, double a, double c,
                           double* __restrict__ S, double* __restrict__ dinvM, double* __restrict__ mlump) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nv) return;
     double sum = 0.0, d = 1.0;
     for (int q = rowptr[i]; q < rowptr[i + 1]; ++q) {
-        if (S) S[q] = a * M[q] + c * K[q];
-        sum += M[q];
-        if (col[q] == i) d = M[q];
+        const int64_t e = sell_pos(sell_ptr, i, q - rowptr[i]);
+        if (S) S[e] = a * M[e] + c * K[e];
+        sum += M[e];
+        if (col[q] == i) d = M[e];
     }
     if (dinvM) dinvM[i] = 1.0 / d;
     if (mlump) mlump[i] = sum;
+}
+
+__global__ void k_to_float(int64_t n, const double* __restrict__ a, float* __restrict__ b) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        b[i] = (float)a[i];
+}
+
+// values of a SELL-stored operator in CSR order (for inspection)
+__global__ void k_sell_to_csr(int nv, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ sell_ptr,
+                              const double* __restrict__ v, double* __restrict__ out) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nv) return;
+    for (int q = rowptr[i]; q < rowptr[i + 1]; ++q) out[q] = v[sell_pos(sell_ptr, i, q - rowptr[i])];
 }
 
 static int layout(Solver& s, void* base, size_t* bytes) {
@@ -118,7 +134,7 @@ static int layout(Solver& s, void* base, size_t* bytes) {
     const Level& F = m->lev[s.lf];
     const Level& C = m->lev[s.lc];
     Carve cv(base);
-    const size_t nf = F.nv, nc = C.nv, nnzf = F.nnz, nnzc = C.nnz;
+    const size_t nf = F.nv, nc = C.nv, nnzf = F.nnz_sell, nnzc = C.nnz_sell;
     s.M = cv.take<double>(nnzf);
     s.K = cv.take<double>(nnzf);
     s.Cx = cv.take<double>(nnzf);
@@ -142,6 +158,17 @@ static int layout(Solver& s, void* base, size_t* bytes) {
     s.dinvKc = cv.take<double>(nc);
     s.mlumpC = cv.take<double>(nc);
     s.geoc = cv.take<double>((size_t)7 * C.nt);
+    s.Kc0f = cv.take<float>(nnzc);
+    s.dinvKcf = cv.take<float>(nc);
+    s.cw64 = cv.take<double>(8 * nc);
+    if (s.prm.guess == CGP_GUESS_LEARNED) {
+        s.phi_guess = cv.take<double>(nc);
+        s.mlp.carve(cv, (int)nc, 1);
+    }
+    s.cw32 = cv.take<float>(9 * nc);
+    s.csr_tmp = cv.take<double>(F.nnz > C.nnz ? F.nnz : C.nnz);
+    s.val_begin = s.M;
+    s.val_end = s.geo;
     double** vec2[] = {&s.U, &s.Uprev, &s.Ut, &s.w, &s.h, &s.b, &s.g, &s.delta,
                        &s.bv.r, &s.bv.rhat, &s.bv.p, &s.bv.v, &s.bv.y, &s.bv.s, &s.bv.z, &s.bv.t,
                        &s.kr, &s.kz, &s.kp0, &s.kp1, &s.kq};
@@ -154,6 +181,9 @@ static int layout(Solver& s, void* base, size_t* bytes) {
     s.qrot = cv.take<double>(nf);
     s.partials = cv.take<double>((size_t)s.max_grid * 8);
     s.tickets = cv.take<unsigned int>(64);
+    s.bar_count = cv.take<unsigned int>(2);
+    s.bar_err = (int*)(s.bar_count ? s.bar_count + 1 : nullptr);
+    s.coarse_partials = cv.take<double>((size_t)2 * s.max_grid * 4);
     s.ks = cv.take<KrylovState>(KS_COUNT);
     s.stats = cv.take<DeviceStats>(1);
     s.tdev = cv.take<double>(1);
@@ -170,8 +200,10 @@ static int check_params(const cgp_mesh* m, const cgp_params* p) {
     if (p->k < 0 || p->k > m->n_levels || !(p->Re > 0) || !(p->dt > 0) || (p->chi != 0 && p->chi != 1) ||
         !(p->tol_mom > 0) || !(p->tol_poisson > 0) || !(p->tol_mass > 0) || p->max_it_mom < 1 ||
         p->max_it_poisson < 1 || p->max_it_mass < 1 || p->bc_kind < 0 || p->bc_kind > CGP_BC_TG_PERIODIC ||
-        (p->precision != CGP_FP64 && p->precision != CGP_MIXED) || p->guess < 0 || p->guess > 1 ||
-        (p->mass_mode != CGP_MASS_CONSISTENT && p->mass_mode != CGP_MASS_LUMPED)) {
+        (p->precision != CGP_FP64 && p->precision != CGP_MIXED) || p->guess < 0 || p->guess > 2 ||
+        (p->mass_mode != CGP_MASS_CONSISTENT && p->mass_mode != CGP_MASS_LUMPED) || p->coarse_mode < 0 ||
+        p->coarse_mode > CGP_COARSE_PERSISTENT || p->cluster_size < 0 || p->cluster_size > 16 || p->tol_inner < 0 ||
+        p->tol_inner >= 1) {
         set_error("invalid cgp_params");
         return CGP_EINVAL;
     }
@@ -255,22 +287,35 @@ extern "C" int cgp_assemble(const cgp_mesh* mesh, const cgp_params* params, void
             if (t & CGP_PHI_ZERO) s.pure_neumann = false;
     }
     k_geometry<<<blocks_for(F.nt), kBlock, 0, st>>>(F.xy, F.tri, F.nt, s.geo);
-    k_static_rows<<<blocks_for(F.nv), kBlock, 0, st>>>(F.nv, F.rowptr, F.col, F.vt_ptr, F.vt_list, F.tri, s.geo,
+    // all SELL value arrays start at zero (padding entries stay zero)
+    if (cudaMemsetAsync(s.M, 0, (char*)s.geo - (char*)s.M, st) != cudaSuccess ||
+        cudaMemsetAsync(s.Mc, 0, (char*)s.geoc - (char*)s.Mc, st) != cudaSuccess) {
+        set_error("workspace initialisation failed");
+        return fail(CGP_ECUDA);
+    }
+    k_static_rows<<<blocks_for(F.nv), kBlock, 0, st>>>(F.nv, F.rowptr, F.col, F.sell_ptr, F.vt_ptr, F.vt_list, F.tri, s.geo,
                                                        s.M, s.K, s.Cx, s.Cy, s.CxT, s.CyT, s.vtslot);
     const double a = 1.5, c = params->dt / params->Re;
-    k_combine<<<blocks_for(F.nv), kBlock, 0, st>>>(F.nv, F.rowptr, F.col, s.M, s.K, a, c, s.S, s.dinvM, s.mlumpF);
-    k_eliminate<<<blocks_for(F.nv), kBlock, 0, st>>>(F.nv, F.rowptr, F.col, s.M, F.tag, CGP_VEL_DIR, s.M0,
-                                                     s.dinvM0);
+    k_combine<<<blocks_for(F.nv), kBlock, 0, st>>>(F.nv, F.rowptr, F.col, F.sell_ptr, s.M, s.K, a, c, s.S, s.dinvM,
+                                                   s.mlumpF);
+    k_eliminate<<<blocks_for(F.nv), kBlock, 0, st>>>(F.nv, F.rowptr, F.col, F.sell_ptr, s.M, F.tag, CGP_VEL_DIR,
+                                                     s.M0, s.dinvM0);
     k_geometry<<<blocks_for(C.nt), kBlock, 0, st>>>(C.xy, C.tri, C.nt, s.geoc);
-    k_static_rows<<<blocks_for(C.nv), kBlock, 0, st>>>(C.nv, C.rowptr, C.col, C.vt_ptr, C.vt_list, C.tri, s.geoc,
+    k_static_rows<<<blocks_for(C.nv), kBlock, 0, st>>>(C.nv, C.rowptr, C.col, C.sell_ptr, C.vt_ptr, C.vt_list, C.tri, s.geoc,
                                                        s.Mc, s.Kc, s.Cxc, s.Cyc, nullptr, nullptr, nullptr);
-    k_combine<<<blocks_for(C.nv), kBlock, 0, st>>>(C.nv, C.rowptr, C.col, s.Mc, s.Kc, 0.0, 0.0, nullptr, nullptr,
-                                                   s.mlumpC);
-    k_eliminate<<<blocks_for(C.nv), kBlock, 0, st>>>(C.nv, C.rowptr, C.col, s.Kc, C.tag, CGP_PHI_ZERO, s.Kc0,
-                                                     s.dinvKc);
+    k_combine<<<blocks_for(C.nv), kBlock, 0, st>>>(C.nv, C.rowptr, C.col, C.sell_ptr, s.Mc, s.Kc, 0.0, 0.0, nullptr,
+                                                   nullptr, s.mlumpC);
+    k_eliminate<<<blocks_for(C.nv), kBlock, 0, st>>>(C.nv, C.rowptr, C.col, C.sell_ptr, s.Kc, C.tag, CGP_PHI_ZERO,
+                                                     s.Kc0, s.dinvKc);
+    k_to_float<<<blocks_for(C.nnz_sell), kBlock, 0, st>>>(C.nnz_sell, s.Kc0, s.Kc0f);
+    k_to_float<<<blocks_for(C.nv), kBlock, 0, st>>>(C.nv, s.dinvKc, s.dinvKcf);
     if (cudaGetLastError() != cudaSuccess) {
         set_error("assembly launch failed");
         return fail(CGP_ECUDA);
+    }
+    {
+        int rc = choose_coarse_solver(s);
+        if (rc != CGP_OK) return fail(rc);
     }
     if (cudaMemsetAsync(s.tickets, 0, 64 * sizeof(unsigned int), st) != cudaSuccess ||
         cudaMemsetAsync(s.ks, 0, KS_COUNT * sizeof(KrylovState), st) != cudaSuccess ||
@@ -315,19 +360,24 @@ extern "C" int cgp_get_matrix(cgp_solver* h, int32_t which, double* vals, int32_
     }
     Solver& s = h->s;
     const double* src = nullptr;
-    size_t n = 0;
+    const bool coarse = which == CGP_MAT_KC || which == CGP_MAT_CXC || which == CGP_MAT_CYC;
     switch (which) {
-        case CGP_MAT_M: src = s.M; n = s.nnzf; break;
-        case CGP_MAT_K: src = s.K; n = s.nnzf; break;
-        case CGP_MAT_CX: src = s.Cx; n = s.nnzf; break;
-        case CGP_MAT_CY: src = s.Cy; n = s.nnzf; break;
-        case CGP_MAT_KC: src = s.Kc; n = s.nnzc; break;
-        case CGP_MAT_CXC: src = s.Cxc; n = s.nnzc; break;
-        case CGP_MAT_CYC: src = s.Cyc; n = s.nnzc; break;
-        case CGP_MAT_A: src = s.A; n = s.nnzf; break;
+        case CGP_MAT_M: src = s.M; break;
+        case CGP_MAT_K: src = s.K; break;
+        case CGP_MAT_CX: src = s.Cx; break;
+        case CGP_MAT_CY: src = s.Cy; break;
+        case CGP_MAT_KC: src = s.Kc; break;
+        case CGP_MAT_CXC: src = s.Cxc; break;
+        case CGP_MAT_CYC: src = s.Cyc; break;
+        case CGP_MAT_A: src = s.A; break;
         default: set_error("unknown matrix %d", which); return CGP_EINVAL;
     }
+    const Level& L = s.mesh->lev[coarse ? s.lc : s.lf];
+    const size_t n = L.nnz;
     cudaStream_t st = (cudaStream_t)stream;
+    k_sell_to_csr<<<blocks_for(L.nv), kBlock, 0, st>>>(L.nv, L.rowptr, L.sell_ptr, src, s.csr_tmp);
+    CGP_LAUNCH_CHECK();
+    src = s.csr_tmp;
     CGP_CUDA(cudaMemcpyAsync(vals, src, n * sizeof(double),
                              where == CGP_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, st));
     if (where == CGP_HOST) CGP_CUDA(cudaStreamSynchronize(st));

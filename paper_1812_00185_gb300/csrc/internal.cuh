@@ -53,7 +53,20 @@ struct Level {
     int32_t* parents = nullptr;  // 2*(nv - nv_prev): end points of the vertices added at this level
     int32_t* vt_ptr = nullptr;   // nv+1: triangles around each vertex
     int32_t* vt_list = nullptr;  // 3*nt, ascending per vertex
+    // sliced ELL (SELL-32) view of the same pattern: slice s = rows 32s..32s+31, stored
+    // column-major with the slice's longest row as width; entry (row i, k-th of its row)
+    // sits at sell_ptr[i/32] + 32 k + i%32.  Padding: column = first row of the slice, value 0.
+    int32_t nslices = 0;
+    int64_t nnz_sell = 0;
+    int32_t* sell_ptr = nullptr; // nslices+1
+    int32_t* sell_col = nullptr; // nnz_sell
 };
+
+constexpr int kSlice = 32;
+
+__host__ __device__ __forceinline__ int64_t sell_pos(const int32_t* sell_ptr, int row, int k) {
+    return (int64_t)sell_ptr[row >> 5] + 32 * k + (row & 31);
+}
 
 // Exclusive scan of n int32 counts into out[0..n] (out[n] = total), on `stream`.
 int exclusive_scan(const int32_t* in, int32_t* out, int64_t n, int32_t* tmp, cudaStream_t stream);

@@ -22,11 +22,20 @@ struct KrylovState {
     int pad[2];
 };
 
-struct CsrView {
-    int n;
-    const int32_t* __restrict__ rowptr;
+// SELL-32 pattern of a level (see Level): one warp works on one slice of 32 rows,
+// lane = row within the slice, so every load of the pattern and the values is coalesced.
+struct SellView {
+    int n, nslices;
+    const int32_t* __restrict__ ptr;
     const int32_t* __restrict__ col;
 };
+
+inline SellView sell_of(const Level& L) { return SellView{L.nv, L.nslices, L.sell_ptr, L.sell_col}; }
+
+// warp-uniform loop over the slices of A; inside: lane, row, base (first entry), w (width)
+#define CGP_SLICE_LOOP(A, sl)                                                                  \
+    for (int sl = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); sl < (A).nslices;        \
+         sl += (int)((gridDim.x * blockDim.x) >> 5))
 
 template <int NC>
 __device__ __forceinline__ void ldv(const double* __restrict__ p, int i, double (&o)[NC]) {
@@ -48,30 +57,39 @@ __device__ __forceinline__ void stv(double* __restrict__ p, int i, const double 
     }
 }
 
-// Rows are processed by groups of LANES consecutive lanes of a warp (LANES | 32).
-// All lanes of a warp run the same number of loop trips, so the shuffles are safe.
-template <int LANES>
-struct RowGroups {
-    int first, stride, sub;
-    __device__ RowGroups() {
-        const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
-        first = gtid / LANES;
-        stride = (gridDim.x * blockDim.x) / LANES;
-        sub = threadIdx.x & (LANES - 1);
-    }
-};
 
-template <int LANES>
-__device__ __forceinline__ double group_sum(double v) {
+// acc[c] += sum_k val(row, k) * g(col(row, k))[c] over the row of (slice sl, lane).
+// The pattern and value loads of up to 8 entries are issued together, then the 8
+// gathers, so a row costs about three dependent memory round trips (slice offset,
+// pattern/values, gathered vector) instead of two per entry.
+template <int NC, class T, class Gather>
+__device__ __forceinline__ void sell_accum(const SellView& A, const T* __restrict__ val, int sl, int lane, Gather&& g,
+                                           double (&acc)[NC]) {
+    const int base = __ldg(A.ptr + sl), w = (__ldg(A.ptr + sl + 1) - base) >> 5;
+    for (int k0 = 0; k0 < w; k0 += 8) {
+        int cj[8];
+        double av[8];
 #pragma unroll
-    for (int o = LANES / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
+        for (int u = 0; u < 8; ++u) {
+            cj[u] = 0;
+            av[u] = 0.0;
+            if (k0 + u < w) {
+                const int e = base + 32 * (k0 + u) + lane;
+                cj[u] = __ldg(A.col + e);
+                av[u] = (double)__ldg(val + e);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            if (k0 + u < w) {
+                double xv[NC];
+                g(cj[u], xv);
+#pragma unroll
+                for (int c = 0; c < NC; ++c) acc[c] += av[u] * xv[c];
+            }
+        }
+    }
 }
-
-// loop over row groups with a warp-uniform trip count
-#define CGP_ROW_LOOP(RG, n, row)                                                            \
-    for (int base_ = (RG).first - ((RG).first % (32 / LANES_)), row = (RG).first;           \
-         base_ < (n); base_ += (RG).stride, row += (RG).stride)
 
 __device__ __forceinline__ void set_loop_condition(unsigned long long handle, int keep_going) {
 #if defined(__CUDA_ARCH__)
@@ -84,35 +102,25 @@ __device__ __forceinline__ bool finite(double x) { return isfinite(x); }
 // ------------------------------------------------------------------ PCG
 // init: r = b - A x (x = 0 if zero_x), optional rhs projection b -= mean,
 // z = D^{-1} r, p = z; rz = <r,z>, rr = <r,r>, bb = <b,b>.
-template <int NC, int LANES_>
-__global__ void __launch_bounds__(kBlock) k_pcg_init(CsrView A, const double* __restrict__ val,
+template <int NC>
+__global__ void __launch_bounds__(kBlock) k_pcg_init(SellView A, const double* __restrict__ val,
                                                     const double* __restrict__ dinv, double* __restrict__ b,
                                                     double* __restrict__ x, double* __restrict__ r,
                                                     double* __restrict__ z, double* __restrict__ p,
                                                     KrylovState* st, double* partials, unsigned int* ticket,
                                                     int zero_x, int project, unsigned long long cond) {
-    RowGroups<LANES_> rg;
     const double mean = project ? st->mean : 0.0;
+    const int lane = threadIdx.x & 31;
     double acc[3 * NC];
 #pragma unroll
     for (int k = 0; k < 3 * NC; ++k) acc[k] = 0.0;
-    CGP_ROW_LOOP(rg, A.n, i) {
+    CGP_SLICE_LOOP(A, sl) {
+        const int i = sl * 32 + lane;
         double ax[NC];
 #pragma unroll
         for (int c = 0; c < NC; ++c) ax[c] = 0.0;
-        const bool live = i < A.n;
-        if (live && !zero_x) {
-            for (int j = A.rowptr[i] + rg.sub; j < A.rowptr[i + 1]; j += LANES_) {
-                double xv[NC];
-                ldv<NC>(x, A.col[j], xv);
-                const double a = val[j];
-#pragma unroll
-                for (int c = 0; c < NC; ++c) ax[c] += a * xv[c];
-            }
-        }
-#pragma unroll
-        for (int c = 0; c < NC; ++c) ax[c] = group_sum<LANES_>(ax[c]);
-        if (live && rg.sub == 0) {
+        if (!zero_x) sell_accum<NC>(A, val, sl, lane, [&](int j, double (&o)[NC]) { ldv<NC>(x, j, o); }, ax);
+        if (i < A.n) {
             double bv[NC], rv[NC], zv[NC];
             ldv<NC>(b, i, bv);
             const double d = dinv[i];
@@ -166,38 +174,34 @@ __global__ void __launch_bounds__(kBlock) k_pcg_init(CsrView A, const double* __
 }
 
 // q = A p_new with p_new = z + beta p_old computed on the fly; pq = <p_new, q>.
-template <int NC, int LANES_>
-__global__ void __launch_bounds__(kBlock) k_pcg_spmv(CsrView A, const double* __restrict__ val,
+template <int NC>
+__global__ void __launch_bounds__(kBlock) k_pcg_spmv(SellView A, const double* __restrict__ val,
                                                     const double* __restrict__ z, const double* __restrict__ pold,
                                                     double* __restrict__ pnew, double* __restrict__ q,
                                                     KrylovState* st, double* partials, unsigned int* ticket) {
     if (st->done) return;
-    RowGroups<LANES_> rg;
+    const int lane = threadIdx.x & 31;
     double beta[NC];
 #pragma unroll
     for (int c = 0; c < NC; ++c) beta[c] = st->beta[c];
     double acc[NC];
 #pragma unroll
     for (int c = 0; c < NC; ++c) acc[c] = 0.0;
-    CGP_ROW_LOOP(rg, A.n, i) {
+    CGP_SLICE_LOOP(A, sl) {
+        const int i = sl * 32 + lane;
         double ax[NC];
 #pragma unroll
         for (int c = 0; c < NC; ++c) ax[c] = 0.0;
-        const bool live = i < A.n;
-        if (live) {
-            for (int j = A.rowptr[i] + rg.sub; j < A.rowptr[i + 1]; j += LANES_) {
-                const int cj = A.col[j];
-                double zv[NC], pv[NC];
-                ldv<NC>(z, cj, zv);
-                ldv<NC>(pold, cj, pv);
-                const double a = val[j];
+        sell_accum<NC>(A, val, sl, lane,
+                       [&](int j, double (&o)[NC]) {
+                           double zv[NC], pv[NC];
+                           ldv<NC>(z, j, zv);
+                           ldv<NC>(pold, j, pv);
 #pragma unroll
-                for (int c = 0; c < NC; ++c) ax[c] += a * (zv[c] + beta[c] * pv[c]);
-            }
-        }
-#pragma unroll
-        for (int c = 0; c < NC; ++c) ax[c] = group_sum<LANES_>(ax[c]);
-        if (live && rg.sub == 0) {
+                           for (int c = 0; c < NC; ++c) o[c] = zv[c] + beta[c] * pv[c];
+                       },
+                       ax);
+        if (i < A.n) {
             double zv[NC], pv[NC];
             ldv<NC>(z, i, zv);
             ldv<NC>(pold, i, pv);
@@ -302,28 +306,24 @@ struct BicgVecs {
     double *x, *r, *rhat, *p, *v, *y, *s, *z, *t;   // 2 components interleaved
 };
 
-template <int LANES_>
-__global__ void __launch_bounds__(kBlock) k_bicg_init(CsrView A, const double* __restrict__ val,
+// two-component SELL SpMV of row (sl, lane): returns A u at that row
+static __device__ __forceinline__ void spmv2_row(const SellView& A, const double* __restrict__ val,
+                                          const double* __restrict__ u, int sl, int lane, double (&ax)[2]) {
+    ax[0] = ax[1] = 0.0;
+    sell_accum<2>(A, val, sl, lane, [&](int j, double (&o)[2]) { ldv<2>(u, j, o); }, ax);
+}
+
+static __global__ void __launch_bounds__(kBlock) k_bicg_init(SellView A, const double* __restrict__ val,
                                                      const double* __restrict__ b, BicgVecs V, KrylovState* st,
                                                      double* partials, unsigned int* ticket,
                                                      unsigned long long cond) {
-    RowGroups<LANES_> rg;
+    const int lane = threadIdx.x & 31;
     double acc[6] = {0, 0, 0, 0, 0, 0};
-    CGP_ROW_LOOP(rg, A.n, i) {
-        double ax[2] = {0.0, 0.0};
-        const bool live = i < A.n;
-        if (live) {
-            for (int j = A.rowptr[i] + rg.sub; j < A.rowptr[i + 1]; j += LANES_) {
-                double xv[2];
-                ldv<2>(V.x, A.col[j], xv);
-                const double a = val[j];
-                ax[0] += a * xv[0];
-                ax[1] += a * xv[1];
-            }
-        }
-        ax[0] = group_sum<LANES_>(ax[0]);
-        ax[1] = group_sum<LANES_>(ax[1]);
-        if (live && rg.sub == 0) {
+    CGP_SLICE_LOOP(A, sl) {
+        const int i = sl * 32 + lane;
+        double ax[2];
+        spmv2_row(A, val, V.x, sl, lane, ax);
+        if (i < A.n) {
             double bv[2], rv[2];
             ldv<2>(b, i, bv);
             const double zero[2] = {0.0, 0.0};
@@ -384,27 +384,16 @@ static __global__ void __launch_bounds__(kBlock) k_bicg_p(int n, const double* _
 }
 
 // v = A y; alpha = rho / <rhat, v>
-template <int LANES_>
-__global__ void __launch_bounds__(kBlock) k_bicg_v(CsrView A, const double* __restrict__ val, BicgVecs V,
+static __global__ void __launch_bounds__(kBlock) k_bicg_v(SellView A, const double* __restrict__ val, BicgVecs V,
                                                   KrylovState* st, double* partials, unsigned int* ticket) {
     if (st->done) return;
-    RowGroups<LANES_> rg;
+    const int lane = threadIdx.x & 31;
     double acc[2] = {0.0, 0.0};
-    CGP_ROW_LOOP(rg, A.n, i) {
-        double ax[2] = {0.0, 0.0};
-        const bool live = i < A.n;
-        if (live) {
-            for (int j = A.rowptr[i] + rg.sub; j < A.rowptr[i + 1]; j += LANES_) {
-                double yv[2];
-                ldv<2>(V.y, A.col[j], yv);
-                const double a = val[j];
-                ax[0] += a * yv[0];
-                ax[1] += a * yv[1];
-            }
-        }
-        ax[0] = group_sum<LANES_>(ax[0]);
-        ax[1] = group_sum<LANES_>(ax[1]);
-        if (live && rg.sub == 0) {
+    CGP_SLICE_LOOP(A, sl) {
+        const int i = sl * 32 + lane;
+        double ax[2];
+        spmv2_row(A, val, V.y, sl, lane, ax);
+        if (i < A.n) {
             double rh[2];
             ldv<2>(V.rhat, i, rh);
             acc[0] += rh[0] * ax[0];
@@ -448,27 +437,16 @@ static __global__ void __launch_bounds__(kBlock) k_bicg_s(int n, const double* _
 }
 
 // t = A z; omega = <t,s>/<t,t>
-template <int LANES_>
-__global__ void __launch_bounds__(kBlock) k_bicg_t(CsrView A, const double* __restrict__ val, BicgVecs V,
+static __global__ void __launch_bounds__(kBlock) k_bicg_t(SellView A, const double* __restrict__ val, BicgVecs V,
                                                   KrylovState* st, double* partials, unsigned int* ticket) {
     if (st->done) return;
-    RowGroups<LANES_> rg;
+    const int lane = threadIdx.x & 31;
     double acc[4] = {0.0, 0.0, 0.0, 0.0};
-    CGP_ROW_LOOP(rg, A.n, i) {
-        double ax[2] = {0.0, 0.0};
-        const bool live = i < A.n;
-        if (live) {
-            for (int j = A.rowptr[i] + rg.sub; j < A.rowptr[i + 1]; j += LANES_) {
-                double zv[2];
-                ldv<2>(V.z, A.col[j], zv);
-                const double a = val[j];
-                ax[0] += a * zv[0];
-                ax[1] += a * zv[1];
-            }
-        }
-        ax[0] = group_sum<LANES_>(ax[0]);
-        ax[1] = group_sum<LANES_>(ax[1]);
-        if (live && rg.sub == 0) {
+    CGP_SLICE_LOOP(A, sl) {
+        const int i = sl * 32 + lane;
+        double ax[2];
+        spmv2_row(A, val, V.z, sl, lane, ax);
+        if (i < A.n) {
             double sv[2];
             ldv<2>(V.s, i, sv);
             for (int c = 0; c < 2; ++c) {

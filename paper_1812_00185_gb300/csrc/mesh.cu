@@ -126,6 +126,26 @@ __global__ void k_upper_count(const int32_t* __restrict__ rowptr, const int32_t*
     cnt[v] = n;
 }
 
+// SELL-32: entries per slice = 32 * (longest row of the slice)
+__global__ void k_slice_size(const int32_t* __restrict__ rowptr, int nv, int nslices, int32_t* __restrict__ cnt) {
+    int sl = blockIdx.x * blockDim.x + threadIdx.x;
+    if (sl >= nslices) return;
+    int w = 0;
+    for (int r = 32 * sl; r < 32 * sl + 32 && r < nv; ++r) w = max(w, rowptr[r + 1] - rowptr[r]);
+    cnt[sl] = 32 * w;
+}
+
+__global__ void k_sell_fill(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col, int nv, int nslices,
+                            const int32_t* __restrict__ sell_ptr, int32_t* __restrict__ sell_col) {
+    int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= 32 * nslices) return;
+    const int sl = r >> 5;
+    const int w = (sell_ptr[sl + 1] - sell_ptr[sl]) / 32;
+    const int len = r < nv ? rowptr[r + 1] - rowptr[r] : 0;
+    for (int k = 0; k < w; ++k)
+        sell_col[sell_ptr[sl] + 32 * k + (r & 31)] = k < len ? col[rowptr[r] + k] : 32 * sl;
+}
+
 // Number of triangles shared by vertices a and b (both lists ascending).
 __device__ int common_triangles(int a, int b, const int32_t* __restrict__ vt_ptr, const int32_t* __restrict__ vt_list) {
     int i = vt_ptr[a], ie = vt_ptr[a + 1], j = vt_ptr[b], je = vt_ptr[b + 1], n = 0;
@@ -243,6 +263,18 @@ static int build_connectivity(cgp_mesh* m, Level& L, int32_t* cnt, int32_t* tmp,
     L.nnz = nnz;
     CGP_TRY(dalloc(m, &L.col, (size_t)nnz));
     k_adj_fill<<<blocks_for(L.nv), kBlock, 0, s>>>(L.tri, L.vt_ptr, L.vt_list, L.nv, L.rowptr, L.col);
+    // SELL-32 view
+    L.nslices = (L.nv + kSlice - 1) / kSlice;
+    CGP_TRY(dalloc(m, &L.sell_ptr, (size_t)L.nslices + 1));
+    k_slice_size<<<blocks_for(L.nslices), kBlock, 0, s>>>(L.rowptr, L.nv, L.nslices, cnt);
+    CGP_TRY(exclusive_scan(cnt, L.sell_ptr, L.nslices, tmp, s));
+    int32_t nsell = 0;
+    CGP_CUDA(cudaMemcpyAsync(&nsell, L.sell_ptr + L.nslices, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    CGP_CUDA(cudaStreamSynchronize(s));
+    L.nnz_sell = nsell;
+    CGP_TRY(dalloc(m, &L.sell_col, (size_t)nsell));
+    k_sell_fill<<<blocks_for((int64_t)L.nslices * kSlice), kBlock, 0, s>>>(L.rowptr, L.col, L.nv, L.nslices,
+                                                                          L.sell_ptr, L.sell_col);
     CGP_LAUNCH_CHECK();
     return CGP_OK;
 }

@@ -3,6 +3,7 @@
 #pragma once
 
 #include "krylov.cuh"
+#include "mlp.cuh"
 
 namespace cgp {
 
@@ -25,6 +26,7 @@ enum { KS_MOM = 0, KS_POIS = 1, KS_CORR = 2, KS_MASS = 3, KS_COUNT = 4 };
 struct DeviceStats {
     int64_t steps;
     int64_t launches;             // kernels launched by graph-replayed steps (loop trips included)
+    int64_t guess_used;           // steps that started the coarse solve from the learned prediction
     int64_t sum_it[KS_COUNT];
     int32_t last_it[KS_COUNT];
     int32_t status;
@@ -51,7 +53,21 @@ struct Solver {
     // coarse-level static operators
     double *Mc = nullptr, *Kc = nullptr, *Kc0 = nullptr, *Cxc = nullptr, *Cyc = nullptr;
     double *dinvKc = nullptr, *mlumpC = nullptr;
+    float *Kc0f = nullptr, *dinvKcf = nullptr;                   // FP32 copies (mixed precision)
+    MlpBuffers mlp;               // learned guess (CGP_GUESS_LEARNED): weights and batch-1 activations
+    bool guess_ready = false;     // weights set by cgp_guess_set
+    double* phi_guess = nullptr;  // n_c: the network's prediction of Phi_c
+    double* cw64 = nullptr;       // coarse one-launch solver work: 8 FP64 vectors of n_c
+    float* cw32 = nullptr;        // and 9 FP32 vectors of n_c
+    int coarse_kind = 0;          // CGP_COARSE_KERNELS / _CLUSTER / _PERSISTENT (AUTO resolved)
+    int cluster_size = 0;         // CTAs of the one-cluster solver
+    int coarse_grid = 0;          // CTAs of the persistent (cooperative) solver
+    unsigned int* bar_count = nullptr;   // grid barrier counter, followed by the error word
+    int* bar_err = nullptr;
+    double* coarse_partials = nullptr;   // 2 x max_grid x 4
     double* geoc = nullptr;
+    double* csr_tmp = nullptr;    // CSR-ordered copy of one operator (cgp_get_matrix)
+    double *val_begin = nullptr, *val_end = nullptr;
     int32_t* vtslotc = nullptr;
     // per-step
     double *A = nullptr, *dinvA = nullptr;
@@ -75,6 +91,7 @@ struct Solver {
 
 // helpers implemented in step.cu / assemble.cu
 int enqueue_step(Solver* s, cudaStream_t st, bool capture);
+int choose_coarse_solver(Solver& s);
 int init_state(Solver* s, cudaStream_t st);
 
 }  // namespace cgp

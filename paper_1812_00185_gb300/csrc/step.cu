@@ -3,12 +3,12 @@
 // Krylov loops are conditional WHILE nodes driven by the kernels themselves.
 #include <cstring>
 
+#include "coarse_pcg.cuh"
 #include "flows.cuh"
 #include "solver.cuh"
 
 namespace cgp {
 
-constexpr int kLanes = 8;   // lanes per CSR row in the SpMV kernels
 
 // ---------------------------------------------------------------- per-vertex kernels
 __global__ void k_init_state(int nf, const double* __restrict__ xy, const uint8_t* __restrict__ tag, BcParams bc,
@@ -56,7 +56,7 @@ __global__ void k_mom_prep(int nf, const double* __restrict__ U, const double* _
 //   b = dt (Cx^T P, Cy^T P) + M h     (pressure term in weak form, see the readings)
 // Dirichlet rows: identity row, b = u_D(t^{n+1}).  Also x0 = w (u_D on Dirichlet rows), dinv.
 __global__ void k_mom_assemble(int nf, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
-                               const int32_t* __restrict__ vt_ptr, const int32_t* __restrict__ vt_list,
+                               const int32_t* __restrict__ sell_ptr, const int32_t* __restrict__ vt_ptr, const int32_t* __restrict__ vt_list,
                                const int32_t* __restrict__ tri, const double* __restrict__ geo,
                                const int32_t* __restrict__ vtslot, const double* __restrict__ S,
                                const double* __restrict__ M, const double* __restrict__ CxT,
@@ -68,8 +68,9 @@ __global__ void k_mom_assemble(int nf, const int32_t* __restrict__ rowptr, const
     const double tn = *tdev + dt;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nf; i += gridDim.x * blockDim.x) {
         const int rb = rowptr[i], re = rowptr[i + 1];
+        const int64_t e0 = sell_pos(sell_ptr, i, 0);   // entry k of the row is at e0 + 32 k
         if (tag[i] & CGP_VEL_DIR) {
-            for (int q = rb; q < re; ++q) A[q] = col[q] == i ? 1.0 : 0.0;
+            for (int q = rb; q < re; ++q) A[e0 + 32 * (q - rb)] = col[q] == i ? 1.0 : 0.0;
             dinv[i] = 1.0;
             double u, v;
             dirichlet_value(bc, xy[2 * i], xy[2 * i + 1], tn, u, v);
@@ -79,12 +80,13 @@ __global__ void k_mom_assemble(int nf, const int32_t* __restrict__ rowptr, const
         }
         double bx = 0.0, by = 0.0;
         for (int q = rb; q < re; ++q) {
-            A[q] = S[q];
+            const int64_t e = e0 + 32 * (q - rb);
+            A[e] = S[e];
             const int j = col[q];
             const double2 hj = reinterpret_cast<const double2*>(h)[j];
             const double pj = P[j];
-            bx += dt * CxT[q] * pj + M[q] * hj.x;
-            by += dt * CyT[q] * pj + M[q] * hj.y;
+            bx += dt * CxT[e] * pj + M[e] * hj.x;
+            by += dt * CyT[e] * pj + M[e] * hj.y;
         }
         const double2 wi = reinterpret_cast<const double2*>(w)[i];
         int diag_slot = 0;
@@ -102,11 +104,11 @@ __global__ void k_mom_assemble(int nf, const int32_t* __restrict__ rowptr, const
 #pragma unroll
             for (int k = 0; k < 3; ++k) {
                 const int slot = (packed >> (8 * (k + 1))) & 255;
-                A[rb + slot] += dt * (cx * gt[1 + 2 * k] + cy * gt[2 + 2 * k]);
+                A[e0 + 32 * slot] += dt * (cx * gt[1 + 2 * k] + cy * gt[2 + 2 * k]);
                 if (k == li) diag_slot = slot;
             }
         }
-        dinv[i] = 1.0 / A[rb + diag_slot];
+        dinv[i] = 1.0 / A[e0 + 32 * diag_slot];
         reinterpret_cast<double2*>(b)[i] = make_double2(bx, by);
         reinterpret_cast<double2*>(x0)[i] = wi;
     }
@@ -114,25 +116,20 @@ __global__ void k_mom_assemble(int nf, const int32_t* __restrict__ rowptr, const
 
 // Eqs. 22-23: r_i = -3/(2 dt) (Cx_c u~ + Cy_c v~)_i at coarse vertex i (the injected
 // U~ is the first N_c entries of the fine U~); r = 0 where phi = 0; mean for the projection.
-template <int LANES_>
-__global__ void __launch_bounds__(kBlock) k_coarse_rhs(CsrView Ac, const double* __restrict__ Cxc,
+__global__ void __launch_bounds__(kBlock) k_coarse_rhs(SellView Ac, const double* __restrict__ Cxc,
                                                       const double* __restrict__ Cyc, const double* __restrict__ Ut,
                                                       const uint8_t* __restrict__ tag, double dt,
                                                       double* __restrict__ rc, KrylovState* st, int pure_neumann,
                                                       double* partials, unsigned int* ticket) {
-    RowGroups<LANES_> rg;
+    const int lane = threadIdx.x & 31;
     double acc[1] = {0.0};
-    CGP_ROW_LOOP(rg, Ac.n, i) {
-        double s = 0.0;
-        const bool live = i < Ac.n;
-        if (live) {
-            for (int j = Ac.rowptr[i] + rg.sub; j < Ac.rowptr[i + 1]; j += LANES_) {
-                const double2 u = reinterpret_cast<const double2*>(Ut)[Ac.col[j]];
-                s += Cxc[j] * u.x + Cyc[j] * u.y;
-            }
-        }
-        s = group_sum<LANES_>(s);
-        if (live && rg.sub == 0) {
+    CGP_SLICE_LOOP(Ac, sl) {
+        const int i = sl * 32 + lane;
+        double sx[1] = {0.0}, sy[1] = {0.0};
+        sell_accum<1>(Ac, Cxc, sl, lane, [&](int j, double (&o)[1]) { o[0] = Ut[2 * j]; }, sx);
+        sell_accum<1>(Ac, Cyc, sl, lane, [&](int j, double (&o)[1]) { o[0] = Ut[2 * j + 1]; }, sy);
+        const double s = sx[0] + sy[0];
+        if (i < Ac.n) {
             double r = (tag[i] & CGP_PHI_ZERO) ? 0.0 : -1.5 / dt * s;
             rc[i] = r;
             acc[0] += r;
@@ -178,26 +175,19 @@ __global__ void k_prolong(int n_new, int nv_c, const int32_t* __restrict__ paren
 
 // Eq. 25 right-hand side: g = -2/3 dt (Cx phi, Cy phi), 0 on Dirichlet rows.  If lumped,
 // delta = g / m directly (and no solve follows).
-template <int LANES_>
-__global__ void __launch_bounds__(kBlock) k_corr_rhs(CsrView A, const double* __restrict__ Cx,
+__global__ void __launch_bounds__(kBlock) k_corr_rhs(SellView A, const double* __restrict__ Cx,
                                                     const double* __restrict__ Cy, const double* __restrict__ phi,
                                                     const uint8_t* __restrict__ tag, double dt,
                                                     double* __restrict__ g, const double* __restrict__ mlump,
                                                     double* __restrict__ delta) {
-    RowGroups<LANES_> rg;
-    CGP_ROW_LOOP(rg, A.n, i) {
-        double sx = 0.0, sy = 0.0;
-        const bool live = i < A.n;
-        if (live) {
-            for (int j = A.rowptr[i] + rg.sub; j < A.rowptr[i + 1]; j += LANES_) {
-                const double pj = phi[A.col[j]];
-                sx += Cx[j] * pj;
-                sy += Cy[j] * pj;
-            }
-        }
-        sx = group_sum<LANES_>(sx);
-        sy = group_sum<LANES_>(sy);
-        if (live && rg.sub == 0) {
+    const int lane = threadIdx.x & 31;
+    CGP_SLICE_LOOP(A, sl) {
+        const int i = sl * 32 + lane;
+        double ax[1] = {0.0}, ay[1] = {0.0};
+        sell_accum<1>(A, Cx, sl, lane, [&](int j, double (&o)[1]) { o[0] = phi[j]; }, ax);
+        sell_accum<1>(A, Cy, sl, lane, [&](int j, double (&o)[1]) { o[0] = phi[j]; }, ay);
+        const double sx = ax[0], sy = ay[0];
+        if (i < A.n) {
             const double c = -2.0 / 3.0 * dt;
             double2 gv = (tag[i] & CGP_VEL_DIR) ? make_double2(0.0, 0.0) : make_double2(c * sx, c * sy);
             reinterpret_cast<double2*>(g)[i] = gv;
@@ -207,22 +197,17 @@ __global__ void __launch_bounds__(kBlock) k_corr_rhs(CsrView A, const double* __
 }
 
 // D U~ = Cx u~ + Cy v~ (rotational update, Eq. 26); lumped: q = div / m directly
-template <int LANES_>
-__global__ void __launch_bounds__(kBlock) k_div(CsrView A, const double* __restrict__ Cx, const double* __restrict__ Cy,
+__global__ void __launch_bounds__(kBlock) k_div(SellView A, const double* __restrict__ Cx, const double* __restrict__ Cy,
                                                const double* __restrict__ Ut, double* __restrict__ div,
                                                const double* __restrict__ mlump, double* __restrict__ q) {
-    RowGroups<LANES_> rg;
-    CGP_ROW_LOOP(rg, A.n, i) {
-        double s = 0.0;
-        const bool live = i < A.n;
-        if (live) {
-            for (int j = A.rowptr[i] + rg.sub; j < A.rowptr[i + 1]; j += LANES_) {
-                const double2 u = reinterpret_cast<const double2*>(Ut)[A.col[j]];
-                s += Cx[j] * u.x + Cy[j] * u.y;
-            }
-        }
-        s = group_sum<LANES_>(s);
-        if (live && rg.sub == 0) {
+    const int lane = threadIdx.x & 31;
+    CGP_SLICE_LOOP(A, sl) {
+        const int i = sl * 32 + lane;
+        double sx[1] = {0.0}, sy[1] = {0.0};
+        sell_accum<1>(A, Cx, sl, lane, [&](int j, double (&o)[1]) { o[0] = Ut[2 * j]; }, sx);
+        sell_accum<1>(A, Cy, sl, lane, [&](int j, double (&o)[1]) { o[0] = Ut[2 * j + 1]; }, sy);
+        const double s = sx[0] + sy[0];
+        if (i < A.n) {
             div[i] = s;
             if (mlump) q[i] = s / mlump[i];
         }
@@ -233,7 +218,7 @@ __global__ void __launch_bounds__(kBlock) k_div(CsrView A, const double* __restr
 __global__ void k_finish(int nf, double* __restrict__ U, double* __restrict__ Uprev, const double* __restrict__ Ut,
                          const double* __restrict__ delta, double* __restrict__ P, const double* __restrict__ phi,
                          const double* __restrict__ q, int chi, double inv_re, double* __restrict__ tdev, double dt,
-                         DeviceStats* stats, const KrylovState* ks, int fixed_launches) {
+                         DeviceStats* stats, const KrylovState* ks, int fixed_launches, int pois_loop) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nf; i += gridDim.x * blockDim.x) {
         const double2 u = reinterpret_cast<const double2*>(U)[i];
         const double2 ut = reinterpret_cast<const double2*>(Ut)[i];
@@ -250,8 +235,10 @@ __global__ void k_finish(int nf, double* __restrict__ U, double* __restrict__ Up
         // launches of a graph replay: the fixed kernels, 5 per BiCGStab iteration and 4 per
         // trip of a PCG loop body (two iterations per trip)
         int64_t l = fixed_launches + 5 * (int64_t)ks[KS_MOM].iter;
-        for (int k = KS_POIS; k < KS_COUNT; ++k) l += 4 * (int64_t)((ks[k].iter + 1) / 2);
+        for (int k = KS_POIS; k < KS_COUNT; ++k)
+            if (k != KS_POIS || pois_loop) l += 4 * (int64_t)((ks[k].iter + 1) / 2);
         stats->launches += l;
+        if (ks[KS_POIS].pad[1]) stats->guess_used += 1;
         for (int k = 0; k < KS_COUNT; ++k) {
             stats->last_it[k] = ks[k].iter;
             stats->sum_it[k] += ks[k].iter;
@@ -376,23 +363,23 @@ static int krylov_loop(Ctx& c, KrylovState* ks, int max_trips, Init init, Body b
 // PCG on (pattern A, values val, Jacobi dinv): b, x; NC components.  Body = two iterations
 // (the search direction alternates between two buffers).
 template <int NC>
-static int pcg(Ctx& c, CsrView A, const double* val, const double* dinv, double* b, double* x, KrylovState* ks,
+static int pcg(Ctx& c, SellView A, const double* val, const double* dinv, double* b, double* x, KrylovState* ks,
                double tol, int maxit, bool zero_x, bool project, int pid) {
     Solver& s = *c.s;
-    const int gs = grid_rows(s, A.n, kLanes), gv = grid_rows(s, A.n, 1);
+    const int gs = grid_rows(s, A.nslices * 32, 1), gv = grid_rows(s, A.n, 1);
     auto init = [&, gs](cudaStream_t st, unsigned long long h) -> int {
         PL(c, pid, k_ks_setup<<<1, 1, 0, st>>>(ks, tol * tol, maxit));
-        PL(c, pid + 1, k_pcg_init<NC, kLanes><<<gs, kBlock, 0, st>>>(A, val, dinv, b, x, s.kr, s.kz, s.kp0, ks,
+        PL(c, pid + 1, k_pcg_init<NC><<<gs, kBlock, 0, st>>>(A, val, dinv, b, x, s.kr, s.kz, s.kp0, ks,
                                                                      s.partials, s.tickets, zero_x, project, h));
         CGP_LAUNCH_CHECK();
         return CGP_OK;
     };
     auto body = [&, gs, gv](cudaStream_t st, unsigned long long h) -> int {
-        PL(c, pid + 2, k_pcg_spmv<NC, kLanes><<<gs, kBlock, 0, st>>>(A, val, s.kz, s.kp0, s.kp1, s.kq, ks, s.partials,
+        PL(c, pid + 2, k_pcg_spmv<NC><<<gs, kBlock, 0, st>>>(A, val, s.kz, s.kp0, s.kp1, s.kq, ks, s.partials,
                                                                      s.tickets));
         PL(c, pid + 3, k_pcg_update<NC><<<gv, kBlock, 0, st>>>(A.n, dinv, x, s.kr, s.kz, s.kp1, s.kq, ks, s.partials,
                                                                s.tickets, h));
-        PL(c, pid + 2, k_pcg_spmv<NC, kLanes><<<gs, kBlock, 0, st>>>(A, val, s.kz, s.kp1, s.kp0, s.kq, ks, s.partials,
+        PL(c, pid + 2, k_pcg_spmv<NC><<<gs, kBlock, 0, st>>>(A, val, s.kz, s.kp1, s.kp0, s.kq, ks, s.partials,
                                                                      s.tickets));
         PL(c, pid + 3, k_pcg_update<NC><<<gv, kBlock, 0, st>>>(A.n, dinv, x, s.kr, s.kz, s.kp0, s.kq, ks, s.partials,
                                                                s.tickets, h));
@@ -402,22 +389,22 @@ static int pcg(Ctx& c, CsrView A, const double* val, const double* dinv, double*
     return krylov_loop(c, ks, (maxit + 1) / 2 + 1, init, body);
 }
 
-static int bicgstab(Ctx& c, CsrView A, const double* val, const double* dinv, const double* b, KrylovState* ks,
+static int bicgstab(Ctx& c, SellView A, const double* val, const double* dinv, const double* b, KrylovState* ks,
                     double tol, int maxit) {
     Solver& s = *c.s;
-    const int gs = grid_rows(s, A.n, kLanes), gv = grid_rows(s, A.n, 1);
+    const int gs = grid_rows(s, A.nslices * 32, 1), gv = grid_rows(s, A.n, 1);
     BicgVecs V = s.bv;
     auto init = [&, gs, V](cudaStream_t st, unsigned long long h) -> int {
         PL(c, CGP_PROF_MOM_SETUP, k_ks_setup<<<1, 1, 0, st>>>(ks, tol * tol, maxit));
-        PL(c, CGP_PROF_MOM_INIT, k_bicg_init<kLanes><<<gs, kBlock, 0, st>>>(A, val, b, V, ks, s.partials, s.tickets, h));
+        PL(c, CGP_PROF_MOM_INIT, k_bicg_init<<<gs, kBlock, 0, st>>>(A, val, b, V, ks, s.partials, s.tickets, h));
         CGP_LAUNCH_CHECK();
         return CGP_OK;
     };
     auto body = [&, gs, gv, V](cudaStream_t st, unsigned long long h) -> int {
         PL(c, CGP_PROF_BICG_P, k_bicg_p<<<gv, kBlock, 0, st>>>(A.n, dinv, V, ks));
-        PL(c, CGP_PROF_BICG_V, k_bicg_v<kLanes><<<gs, kBlock, 0, st>>>(A, val, V, ks, s.partials, s.tickets));
+        PL(c, CGP_PROF_BICG_V, k_bicg_v<<<gs, kBlock, 0, st>>>(A, val, V, ks, s.partials, s.tickets));
         PL(c, CGP_PROF_BICG_S, k_bicg_s<<<gv, kBlock, 0, st>>>(A.n, dinv, V, ks));
-        PL(c, CGP_PROF_BICG_T, k_bicg_t<kLanes><<<gs, kBlock, 0, st>>>(A, val, V, ks, s.partials, s.tickets));
+        PL(c, CGP_PROF_BICG_T, k_bicg_t<<<gs, kBlock, 0, st>>>(A, val, V, ks, s.partials, s.tickets));
         PL(c, CGP_PROF_BICG_X, k_bicg_x<<<gv, kBlock, 0, st>>>(A.n, V, ks, s.partials, s.tickets, h));
         CGP_LAUNCH_CHECK();
         return CGP_OK;
@@ -425,12 +412,130 @@ static int bicgstab(Ctx& c, CsrView A, const double* val, const double* dinv, co
     return krylov_loop(c, ks, maxit + 1, init, body);
 }
 
+// ---------------------------------------------------------------- coarse solver choice
+static cudaLaunchConfig_t cluster_config(int csize, cudaStream_t st, cudaLaunchAttribute* attr) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(csize, 1, 1);
+    cfg.blockDim = dim3(kClusterThreads, 1, 1);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = csize;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cfg;
+}
+
+int choose_coarse_solver(Solver& s) {
+    const cgp_params& p = s.prm;
+    int mode = p.coarse_mode;
+    if (mode == CGP_COARSE_AUTO) mode = CGP_COARSE_PERSISTENT;
+    s.coarse_kind = mode;
+    s.cluster_size = 0;
+    s.coarse_grid = 0;
+    if (mode == CGP_COARSE_KERNELS) {
+        if (p.precision == CGP_MIXED || p.guess == CGP_GUESS_LEARNED) {
+            set_error("CGP_MIXED and CGP_GUESS_LEARNED need a one-launch coarse solver (persistent or cluster)");
+            return CGP_EINVAL;
+        }
+        return CGP_OK;
+    }
+    int dev = 0, sms = 0;
+    CGP_CUDA(cudaGetDevice(&dev));
+    CGP_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    if (mode == CGP_COARSE_PERSISTENT) {
+        int coop = 0, per_sm = 0;
+        CGP_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
+        CGP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pcg_grid, kGridThreads, 0));
+        if (!coop || per_sm < 1) {
+            set_error("cooperative launch unavailable for the persistent coarse solver");
+            return CGP_EINVAL;
+        }
+        const Level& C = s.mesh->lev[s.lc];
+        // one slice per warp is enough; never more CTAs than can be co-resident
+        const int need = (C.nslices + kGridThreads / 32 - 1) / (kGridThreads / 32);
+        const int cap = sms * (per_sm < 2 ? per_sm : 2);
+        s.coarse_grid = need < cap ? need : cap;
+        if (s.coarse_grid < 1) s.coarse_grid = 1;
+        return CGP_OK;
+    }
+    CGP_CUDA(cudaFuncSetAttribute(k_pcg_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+    const int cands[] = {16, 8, 4, 2};
+    for (int cs : cands) {
+        if (p.cluster_size && cs != p.cluster_size) continue;
+        cudaLaunchAttribute attr[1];
+        cudaLaunchConfig_t cfg = cluster_config(cs, nullptr, attr);
+        int n = 0;
+        if (cudaOccupancyMaxActiveClusters(&n, k_pcg_cluster, &cfg) == cudaSuccess && n > 0) {
+            s.cluster_size = cs;
+            break;
+        }
+        cudaGetLastError();
+    }
+    if (!s.cluster_size) {
+        set_error("no thread-block cluster of the requested size fits this device");
+        return CGP_EINVAL;
+    }
+    return CGP_OK;
+}
+
 // ---------------------------------------------------------------- pieces of a step
 static int coarse_solve(Ctx& c) {
     Solver& s = *c.s;
     const Level& C = s.mesh->lev[s.lc];
-    CsrView Ac{C.nv, C.rowptr, C.col};
+    SellView Ac = sell_of(C);
     const bool zero_x = s.prm.guess == CGP_GUESS_ZERO;
+    if (s.coarse_kind == CGP_COARSE_CLUSTER || s.coarse_kind == CGP_COARSE_PERSISTENT) {
+        CoarsePcgArgs a;
+        a.A = Ac;
+        a.val = s.Kc0;
+        a.valf = s.Kc0f;
+        a.dinv = s.dinvKc;
+        a.dinvf = s.dinvKcf;
+        a.b = s.rc;
+        a.x = s.phi;
+        a.x_alt = nullptr;
+        if (s.prm.guess == CGP_GUESS_LEARNED && s.guess_ready) {
+            // the network predicts Phi_c from the coarse rhs and the previous Phi_c
+            const Level& Cl = s.mesh->lev[s.lc];
+            PL(c, CGP_PROF_MLP, CGP_TRY(mlp_forward(s.mlp, Cl, s.rc, s.phi, 1, s.phi_guess, c.st)));
+            a.x_alt = s.phi_guess;
+        }
+        a.w64 = s.cw64;
+        a.w32 = s.cw32;
+        a.mlump = s.pure_neumann ? s.mlumpC : nullptr;
+        a.st = &s.ks[KS_POIS];
+        a.tol2 = s.prm.tol_poisson * s.prm.tol_poisson;
+        a.inner_tol = s.prm.tol_inner > 0 ? s.prm.tol_inner : 1e-4;
+        a.maxit = s.prm.max_it_poisson;
+        a.zero_x = zero_x;
+        a.project = s.pure_neumann;
+        a.mixed = s.prm.precision == CGP_MIXED;
+        a.max_outer = 50;
+        a.bar_count = s.bar_count;
+        a.bar_err = s.bar_err;
+        a.partials = s.coarse_partials;
+        if (s.coarse_kind == CGP_COARSE_CLUSTER) {
+            cudaLaunchAttribute attr[1];
+            cudaLaunchConfig_t cfg = cluster_config(s.cluster_size, c.st, attr);
+            PL(c, CGP_PROF_POIS_CLUSTER, CGP_CUDA(cudaLaunchKernelEx(&cfg, k_pcg_cluster, a)));
+            return CGP_OK;
+        }
+        CGP_CUDA(cudaMemsetAsync(s.bar_count, 0, 2 * sizeof(unsigned int), c.st));   // counter + error word
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(s.coarse_grid, 1, 1);
+        cfg.blockDim = dim3(kGridThreads, 1, 1);
+        cfg.stream = c.st;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeCooperative;
+        attr[0].val.cooperative = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        PL(c, CGP_PROF_POIS_CLUSTER, CGP_CUDA(cudaLaunchKernelEx(&cfg, k_pcg_grid, a)));
+        return CGP_OK;
+    }
     CGP_TRY(pcg<1>(c, Ac, s.Kc0, s.dinvKc, s.rc, s.phi, &s.ks[KS_POIS], s.prm.tol_poisson, s.prm.max_it_poisson,
                    zero_x, s.pure_neumann, CGP_PROF_POIS_SETUP));
     if (s.pure_neumann) {
@@ -460,19 +565,19 @@ static int step_body(Ctx& c) {
     const Level& F = s.mesh->lev[s.lf];
     const Level& C = s.mesh->lev[s.lc];
     const BcParams bc = bc_from(p);
-    CsrView Af{F.nv, F.rowptr, F.col}, Ac{C.nv, C.rowptr, C.col};
-    const int gv = grid_rows(s, F.nv, 1), gs = grid_rows(s, F.nv, kLanes);
+    SellView Af = sell_of(F), Ac = sell_of(C);
+    const int gv = grid_rows(s, F.nv, 1), gs = grid_rows(s, F.nslices * 32, 1);
     // Eq. 21: momentum
     PL(c, CGP_PROF_MOM_PREP, k_mom_prep<<<gv, kBlock, 0, c.st>>>(F.nv, s.U, s.Uprev, F.xy, bc, s.tdev, p.dt, s.w, s.h));
     PL(c, CGP_PROF_MOM_ASSEMBLE,
-       k_mom_assemble<<<gv, kBlock, 0, c.st>>>(F.nv, F.rowptr, F.col, F.vt_ptr, F.vt_list, F.tri, s.geo, s.vtslot, s.S,
+       k_mom_assemble<<<gv, kBlock, 0, c.st>>>(F.nv, F.rowptr, F.col, F.sell_ptr, F.vt_ptr, F.vt_list, F.tri, s.geo, s.vtslot, s.S,
                                                s.M, s.CxT, s.CyT, s.P, s.w, s.h, F.tag, F.xy, bc, s.tdev, p.dt, s.A,
                                                s.dinvA, s.b, s.Ut));
     CGP_LAUNCH_CHECK();
     CGP_TRY(bicgstab(c, Af, s.A, s.dinvA, s.b, &s.ks[KS_MOM], p.tol_mom, p.max_it_mom));
     // Eqs. 22-23: injection, coarse divergence, coarse Poisson solve
     PL(c, CGP_PROF_COARSE_RHS,
-       k_coarse_rhs<kLanes><<<grid_rows(s, C.nv, kLanes), kBlock, 0, c.st>>>(
+       k_coarse_rhs<<<grid_rows(s, C.nslices * 32, 1), kBlock, 0, c.st>>>(
            Ac, s.Cxc, s.Cyc, s.Ut, C.tag, p.dt, s.rc, &s.ks[KS_POIS], s.pure_neumann, s.partials, s.tickets));
     CGP_LAUNCH_CHECK();
     CGP_TRY(coarse_solve(c));
@@ -481,7 +586,7 @@ static int step_body(Ctx& c) {
     // Eq. 25: velocity correction
     const bool lumped = p.mass_mode == CGP_MASS_LUMPED;
     PL(c, CGP_PROF_CORR_RHS,
-       k_corr_rhs<kLanes><<<gs, kBlock, 0, c.st>>>(Af, s.Cx, s.Cy, s.phi, F.tag, p.dt, s.g,
+       k_corr_rhs<<<gs, kBlock, 0, c.st>>>(Af, s.Cx, s.Cy, s.phi, F.tag, p.dt, s.g,
                                                    lumped ? s.mlumpF : nullptr, s.delta));
     CGP_LAUNCH_CHECK();
     if (!lumped)
@@ -490,17 +595,19 @@ static int step_body(Ctx& c) {
     // Eq. 26: pressure
     if (p.chi) {
         PL(c, CGP_PROF_DIV,
-           k_div<kLanes><<<gs, kBlock, 0, c.st>>>(Af, s.Cx, s.Cy, s.Ut, s.div, lumped ? s.mlumpF : nullptr, s.qrot));
+           k_div<<<gs, kBlock, 0, c.st>>>(Af, s.Cx, s.Cy, s.Ut, s.div, lumped ? s.mlumpF : nullptr, s.qrot));
         CGP_LAUNCH_CHECK();
         if (!lumped)
             CGP_TRY(pcg<1>(c, Af, s.M, s.dinvM, s.div, s.qrot, &s.ks[KS_MASS], p.tol_mass, p.max_it_mass, true, false,
                            CGP_PROF_MASS_SETUP));
     }
-    const int fixed = 4 + 1 + 2 + (s.pure_neumann ? 2 : 0) + (s.lf - s.lc) + 1 + (lumped ? 0 : 2) +
-                      (p.chi ? 1 + (lumped ? 0 : 2) : 0) + 1;
+    const bool one_launch = s.coarse_kind != CGP_COARSE_KERNELS;
+    const int coarse_fixed = (one_launch ? 1 : 2 + (s.pure_neumann ? 2 : 0)) +
+                             ((p.guess == CGP_GUESS_LEARNED && s.guess_ready) ? 9 : 0);
+    const int fixed = 4 + 1 + coarse_fixed + (s.lf - s.lc) + 1 + (lumped ? 0 : 2) + (p.chi ? 1 + (lumped ? 0 : 2) : 0) + 1;
     PL(c, CGP_PROF_FINISH,
        k_finish<<<gv, kBlock, 0, c.st>>>(F.nv, s.U, s.Uprev, s.Ut, s.delta, s.P, s.phi, s.qrot, p.chi, 1.0 / p.Re,
-                                         s.tdev, p.dt, s.stats, s.ks, fixed));
+                                         s.tdev, p.dt, s.stats, s.ks, fixed, one_launch ? 0 : 1));
     CGP_LAUNCH_CHECK();
     return CGP_OK;
 }
@@ -614,6 +721,7 @@ extern "C" int cgp_get_fields(cgp_solver* h, double* U, double* P, double* t, cg
     if (stats) {
         stats->steps = ds.steps;
         stats->launches = ds.launches;
+        stats->guess_used = ds.guess_used;
         stats->t = th;
         stats->it_mom = ds.last_it[KS_MOM];
         stats->it_poisson = ds.last_it[KS_POIS];

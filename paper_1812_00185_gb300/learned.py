@@ -1,0 +1,68 @@
+"""Training driver of the learned initial guess (argument marshalling around the C ABI).
+
+Pairs are recorded from the library's own solver: before a step the previous coarse
+increment q = Phi_c^n is copied out, after it the coarse right-hand side r of Eq. 23 and
+the converged Phi_c^{n+1} (the target).  Training runs the library's CUDA forward,
+backward and Adam kernels (cgp_mlp_train_step); PyTorch only holds the device buffers.
+"""
+
+import numpy as np
+
+from . import binding as cg
+
+
+class PairStore:
+    """Device buffers of recorded (r, q, target) triples on one mesh level."""
+
+    def __init__(self, n, capacity):
+        import torch
+        self.n, self.cap, self.count = n, capacity, 0
+        self.r = torch.empty((capacity, n), dtype=torch.float64, device="cuda")
+        self.q = torch.empty_like(self.r)
+        self.t = torch.empty_like(self.r)
+
+    def record(self, solver, steps):
+        """Advance `steps` steps of `solver` (a binding.Solver), storing one triple per step."""
+        for _ in range(steps):
+            if self.count >= self.cap:
+                break
+            k = self.count
+            cg.cgp_get_vector_device(solver.handle, cg.CGP_VEC_PHI_C, self.q[k])
+            solver.step(1)
+            cg.cgp_get_vector_device(solver.handle, cg.CGP_VEC_RHS_C, self.r[k])
+            cg.cgp_get_vector_device(solver.handle, cg.CGP_VEC_PHI_C, self.t[k])
+            self.count += 1
+        return self.count
+
+
+def train(net, store, iters, batch=8, lr=1e-3, seed=0, log_every=0):
+    """Adam on random batches of the store; returns the loss history (every log_every, and last)."""
+    import torch
+    rng = np.random.default_rng(seed)
+    n = store.n
+    rb = torch.empty((batch, n), dtype=torch.float64, device="cuda")
+    qb, tb = torch.empty_like(rb), torch.empty_like(rb)
+    hist = []
+    for it in range(iters):
+        idx = torch.as_tensor(rng.integers(0, store.count, size=batch), device="cuda")
+        torch.index_select(store.r[:store.count], 0, idx, out=rb)
+        torch.index_select(store.q[:store.count], 0, idx, out=qb)
+        torch.index_select(store.t[:store.count], 0, idx, out=tb)
+        want = (log_every and it % log_every == 0) or it == iters - 1
+        loss = cg.cgp_mlp_train_step(net, rb, qb, tb, batch, lr, want_loss=want)
+        if want:
+            hist.append((it, loss))
+    return hist
+
+
+def init_params(seed=0):
+    """He-style initialisation of the parameter vector (last layer small so that the
+    initial prediction stays close to the previous increment)."""
+    rng = np.random.default_rng(seed)
+    p = np.zeros(cg.cgp_mlp_param_count(), np.float32)
+    o = 0
+    for fin, fout, scale in ((4, 64, 1.0), (64, 64, 1.0), (64, 1, 0.01)):
+        w = rng.standard_normal((fout, 2 * fin)) * np.sqrt(2.0 / (2 * fin)) * scale
+        p[o:o + w.size] = w.ravel()
+        o += w.size + fout          # biases stay zero
+    return p

@@ -1,0 +1,114 @@
+"""Learned initial guess: CUDA forward/backward against the FP64 oracle, training, and the
+guess inside the step (the PCG tolerance judges it, the previous increment is the fallback)."""
+
+import numpy as np
+import pytest
+
+from workloads import square_mesh, channel_cylinder_mesh
+from oracle import mlp as omlp
+from oracle.mesh import build_hierarchy
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def cg(lib):
+    from paper_1812_00185_gb300 import binding
+    return binding
+
+
+def _params_to_lists(p):
+    W, b, o = [], [], 0
+    for fin, fout in zip(omlp.WIDTHS[:-1], omlp.WIDTHS[1:]):
+        W.append(p[o:o + fout * 2 * fin].reshape(fout, 2 * fin).astype(np.float64))
+        o += fout * 2 * fin
+        b.append(p[o:o + fout].astype(np.float64))
+        o += fout
+    return W, b
+
+
+def _bf16(x):
+    # round-to-nearest-even to bfloat16, as __float2bfloat16_rn does
+    u = np.asarray(x, np.float32).view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32)
+
+
+def _grads_to_vector(gW, gb):
+    return np.concatenate([np.concatenate([w.ravel(), x]) for w, x in zip(gW, gb)])
+
+
+def test_forward_and_gradients_match_oracle(cg):
+    import torch
+    from paper_1812_00185_gb300.learned import init_params
+    base = square_mesh(6)
+    mesh = cg.Mesh(base.xy, base.tri, base.tag, 1)
+    lev = build_hierarchy(base.xy, base.tri, base.tag, 1)[1]
+    n = lev.n_vert
+    net = cg.cgp_mlp_create(mesh.handle, 1, 2)
+    p = init_params(3)
+    p[p.size - 129:p.size - 1] *= 100.0          # make the last layer matter
+    rng = np.random.default_rng(1)
+    p[512:576] = 0.1 * rng.standard_normal(64)   # non-zero biases
+    cg.cgp_mlp_set_params(net, p)
+    r = rng.standard_normal((2, n))
+    q = rng.standard_normal((2, n))
+    t = q + 0.2 * rng.standard_normal((2, n))
+    R, Q, T = (torch.tensor(a, device="cuda") for a in (r, q, t))
+    pred = torch.empty_like(R)
+    cg.cgp_mlp_forward(net, R, Q, 2, pred)
+    torch.cuda.synchronize()
+    # the oracle gets the weights the GPU uses: bfloat16-rounded W, FP32 biases
+    W, b = _params_to_lists(p)
+    W = [_bf16(w).astype(np.float64) for w in W]
+    for k in range(2):
+        ref, _ = omlp.forward(W, b, r[k], q[k], lev.xy, lev.rowptr, lev.col)
+        np.testing.assert_allclose(pred[k].cpu().numpy(), ref, rtol=2e-4, atol=2e-5 * np.abs(ref).max())
+    loss, g = cg.cgp_mlp_grad(net, R, Q, T, 2)
+    lref, gW, gb = omlp.loss_and_grads(W, b, [(r[k], q[k], t[k]) for k in range(2)], lev.xy, lev.rowptr, lev.col)
+    gref = _grads_to_vector(gW, gb)
+    assert abs(loss - lref) <= 1e-4 * lref
+    rel = np.linalg.norm(g - gref) / np.linalg.norm(gref)
+    assert rel < 1e-3, rel
+    cg.cgp_mlp_destroy(net)
+    mesh.close()
+
+
+def test_training_and_learned_guess_in_the_step(cg):
+    import torch
+    from paper_1812_00185_gb300.learned import PairStore, train, init_params
+    base = channel_cylinder_mesh(seed=7, h=0.03)
+    mesh = cg.Mesh(base.xy, base.tri, base.tag, 2)
+    common = dict(chi=1, k=1, bc_kind=cg.CGP_BC_CHANNEL, bc_param=(0.3, 0.41), tol_mom=1e-10, tol_poisson=1e-8,
+                  tol_mass=1e-10)
+    # record (r, q, target) triples from the plain solver
+    rec = cg.Solver(mesh, cg.make_params(1000.0, 0.002, **common))
+    store = PairStore(rec.nc, 80)
+    store.record(rec, 80)
+    rec.close()
+    net = cg.cgp_mlp_create(mesh.handle, 1, 8)
+    cg.cgp_mlp_set_params(net, init_params(0))
+    hist = train(net, store, 300, batch=8, lr=2e-3, log_every=50)
+    assert hist[-1][1] < hist[0][1], hist
+    # the same 40 steps with the previous-increment guess and with the learned guess
+    out = {}
+    for mode in (cg.CGP_GUESS_PREV, cg.CGP_GUESS_LEARNED):
+        s = cg.Solver(mesh, cg.make_params(1000.0, 0.002, guess=mode, **common))
+        if mode == cg.CGP_GUESS_LEARNED:
+            cg.cgp_guess_set(s.handle, net)
+        s.step(40)
+        U, P, t, st, rc = s.fields()
+        out[mode] = (U, P, st)
+        assert rc == 0
+        s.close()
+    Up, Pp, sp = out[cg.CGP_GUESS_PREV]
+    Ul, Pl, sl = out[cg.CGP_GUESS_LEARNED]
+    # both solves stop at the same relative residual: the fields agree to that level
+    assert np.linalg.norm(Ul - Up) / np.linalg.norm(Up) < 1e-6
+    assert np.linalg.norm(Pl - Pp) / np.linalg.norm(Pp) < 1e-5
+    print("coarse PCG iterations over 40 steps: previous-increment guess %d, learned guess %d (used in %d steps)"
+          % (sp["sum_it_poisson"], sl["sum_it_poisson"], sl["guess_used"]))
+    # the residual judge never lets the learned start be worse than the fallback by much
+    assert sl["sum_it_poisson"] <= 1.1 * sp["sum_it_poisson"]
+    cg.cgp_mlp_destroy(net)
+    mesh.close()
