@@ -285,6 +285,9 @@ def run_gpu(args, rank, world):
     pcg = None
     if not args.quick and rank == 0:
         pcg = pcg_bandwidth(cg, torch, args.pcg_n, peak)
+    batch = None
+    if not args.quick and args.batch > 0:
+        batch = batch_throughput(cg, torch, args.batch, args.batch_steps, 3)
 
     s.close()
     mesh.close()
@@ -299,7 +302,7 @@ def run_gpu(args, rank, world):
                    "l2": "working set %.2f GB > 129 MB L2 (no flush)" % (1e-9 * ws_bytes)},
         "e2e": e2e, "gpu_launches": int(head["launches"]), "clocks": head["clocks"], "roofline": roof,
         "forms": forms, "kernels": kern, "setup_s": {"mesh": round(t_mesh, 3), "assemble": round(head["assemble_s"], 3)},
-        "pcg_hbm": pcg,
+        "pcg_hbm": pcg, "batch": batch,
     }
     if learned:
         out["learned"] = learned["info"]
@@ -317,8 +320,9 @@ def pcg_bandwidth(cg, torch, n_side, peak):
         lv += 1
     base = square_mesh(nb, boundary_flags=PHI_ZERO)
     mesh = cg.Mesh(base.xy, base.tri, base.tag, lv)
+    # the two-kernels-per-iteration PCG: the bandwidth-oriented path for coarse meshes far beyond L2
     prm = cg.make_params(1.0, 1.0, k=0, tol_poisson=1e-30, max_it_poisson=200, guess=cg.CGP_GUESS_ZERO,
-                         bc_kind=cg.CGP_BC_CAVITY)
+                         bc_kind=cg.CGP_BC_CAVITY, coarse_mode=cg.CGP_COARSE_KERNELS)
     s = cg.Solver(mesh, prm)
     nf, nc, zf, zc = cg.cgp_solver_info(s.handle)
     rhs = np.random.default_rng(0).standard_normal(nc)
@@ -340,6 +344,54 @@ def pcg_bandwidth(cg, torch, n_side, peak):
                     "update_GBps": round(kernel_bytes("pois_update", nc, zc) / (up[1] / up[0] * 1e-3) / 1e9, 1)})
     s.close()
     mesh.close()
+    return out
+
+
+def batch_throughput(cg, torch, n_inst, steps, warmup):
+    """The batched form: n_inst uneven lid-driven cavities (seeded sizes 32^2..256^2 x 2
+    triangles, Re in [10, 400], 1-3 coarsening levels, dt = 0.005, rotational form, FP32-inner
+    coarse solves) advanced by one graph per step with one persistent launch for all coarse
+    solves."""
+    from workloads import batch_instances, square_mesh
+    specs = batch_instances(n_inst)
+    t0 = time.time()
+    meshes, solvers = [], []
+    nf_tot = nc_tot = 0
+    for sp in specs:
+        base = square_mesh(sp["n_fine"] >> sp["k"])
+        m = cg.Mesh(base.xy, base.tri, base.tag, sp["k"])
+        prm = cg.make_params(sp["Re"], 0.005, chi=1, k=sp["k"], tol_mom=1e-8, tol_poisson=1e-8, tol_mass=1e-10,
+                             precision=cg.CGP_MIXED, bc_kind=cg.CGP_BC_CAVITY)
+        s = cg.Solver(m, prm)
+        meshes.append(m)
+        solvers.append(s)
+        nf_tot += s.nf
+        nc_tot += s.nc
+    torch.cuda.synchronize()
+    t_setup = time.time() - t0
+    t0 = time.time()
+    b = cg.cgp_batch_create(solvers)
+    info = cg.cgp_batch_info(b)
+    t_tune = time.time() - t0
+    cg.cgp_batch_step(b, warmup)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    cg.cgp_batch_step(b, steps)
+    ev1.record()
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1) / steps
+    its = [s.fields()[3] for s in solvers]
+    bad = sum(1 for st in its if st["status"] != 0)
+    out = {"instances": n_inst, "fine_vertices": nf_tot, "coarse_vertices": nc_tot, "steps": steps,
+           "ms_per_batch_step": round(ms, 4), "instance_steps_per_s": round(1000.0 * n_inst / ms, 1),
+           "fine_vertex_steps_per_s": round(1000.0 * nf_tot / ms, 1), "autotune": info,
+           "setup_s": round(t_setup, 2), "tune_and_capture_s": round(t_tune, 2), "instances_not_converged": bad}
+    cg.cgp_batch_destroy(b)
+    for s in solvers:
+        s.close()
+    for m in meshes:
+        m.close()
     return out
 
 
@@ -373,6 +425,8 @@ def main():
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--workload", default="channel1m_k2")
     ap.add_argument("--form", default="mixed_learned", choices=["fp64", "mixed", "learned", "mixed_learned"])
+    ap.add_argument("--batch", type=int, default=256, help="instances of the batched form (0: skip)")
+    ap.add_argument("--batch-steps", type=int, default=10)
     ap.add_argument("--train-pairs", type=int, default=150)
     ap.add_argument("--train-iters", type=int, default=400)
     ap.add_argument("--pcg-n", type=int, default=2048)

@@ -207,6 +207,29 @@ int cgp_profile_step(cgp_solver* s, cgp_stream_t stream, int32_t n_ids, int32_t*
 
 void cgp_solver_destroy(cgp_solver* s);
 
+/* ---- batches of independent instances (not in the paper) ----
+ * cgp_batch_create groups assembled solvers (any meshes and parameters; each keeps its own
+ * workspace and state) into one CUDA graph per step: every instance's momentum solve and
+ * coarse right-hand side on its own stream, then ONE persistent launch that solves all the
+ * coarse Poisson problems (thread-block clusters take instances from a queue, largest
+ * first, and reduce through distributed shared memory), then every instance's correction
+ * and pressure update.  cluster_size (0 = autotune, else 1, 2, 4, 8) and threads (0 =
+ * autotune, else 256, 512, 1024) fix the persistent launch's shape; the autotuner times
+ * each candidate on the instances' first coarse problems, restoring their state after each
+ * trial.  The batch allocates its own device memory (launch arguments, a queue counter and
+ * the saved coarse state); the solvers must outlive it.  Synchronises `stream`. */
+typedef struct cgp_batch cgp_batch;
+int cgp_batch_create(cgp_solver* const* solvers, int32_t n, int32_t cluster_size, int32_t threads,
+                     cgp_stream_t stream, cgp_batch** out);
+/* n_steps batched steps (graph launches on `stream`); per-instance results and stats via
+ * cgp_get_fields on each solver. */
+int cgp_batch_step(cgp_batch* b, int32_t n_steps, cgp_stream_t stream);
+/* Chosen shape, clusters per launch, and the autotuner's trial times (ms; -1 = not run) for
+ * the candidates (cluster, threads) = (1,256),(1,512),(1,1024),(2,256),...,(8,1024). */
+int cgp_batch_info(const cgp_batch* b, int32_t* cluster_size, int32_t* threads, int32_t* nclusters, float* trial_ms,
+                   int32_t n_trials);
+void cgp_batch_destroy(cgp_batch* b);
+
 /* ---- learned initial guess (not in the paper) ----
  * A per-vertex MLP on one mesh level with 1-ring mean aggregation: inputs per vertex
  * (r/rms(r), q/rms(q), x, y) with r the coarse right-hand side of Eq. 23 and q the previous

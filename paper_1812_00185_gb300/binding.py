@@ -96,7 +96,14 @@ _SIGS = {
                                      POINTER(ctypes.c_float), c_void_p]),
     "cgp_guess_set": (c_int32, [c_void_p, c_void_p, c_void_p]),
     "cgp_mlp_destroy": (None, [c_void_p]),
+    "cgp_batch_create": (c_int32, [c_void_p, c_int32, c_int32, c_int32, c_void_p, POINTER(c_void_p)]),
+    "cgp_batch_step": (c_int32, [c_void_p, c_int32, c_void_p]),
+    "cgp_batch_info": (c_int32, [c_void_p, POINTER(c_int32), POINTER(c_int32), POINTER(c_int32), c_void_p,
+                                 c_int32]),
+    "cgp_batch_destroy": (None, [c_void_p]),
 }
+
+BATCH_CANDIDATES = [(c, t) for c in (1, 2, 4, 8) for t in (256, 512, 1024)]
 
 PROF_NAMES = ["mom_prep", "mom_assemble", "mom_setup", "mom_init", "bicg_p", "bicg_v", "bicg_s", "bicg_t",
               "bicg_x", "coarse_rhs", "pois_setup", "pois_init", "pois_spmv", "pois_update", "phi_mean",
@@ -307,6 +314,30 @@ def cgp_profile_step(solver, stream=None):
 
 def cgp_solver_destroy(solver):
     load().cgp_solver_destroy(solver)
+
+
+# ---------------------------------------------------------------- batches
+def cgp_batch_create(solvers, cluster_size=0, threads=0, stream=None):
+    arr = (c_void_p * len(solvers))(*[s.handle if hasattr(s, "handle") else s for s in solvers])
+    out = c_void_p()
+    _check(load().cgp_batch_create(arr, len(solvers), int(cluster_size), int(threads), _stream(stream), byref(out)))
+    return out
+
+
+def cgp_batch_step(batch, n_steps, stream=None):
+    _check(load().cgp_batch_step(batch, int(n_steps), _stream(stream)))
+
+
+def cgp_batch_info(batch):
+    cs, th, ncl = c_int32(), c_int32(), c_int32()
+    trials = np.zeros(len(BATCH_CANDIDATES), np.float32)
+    _check(load().cgp_batch_info(batch, byref(cs), byref(th), byref(ncl), _ptr(trials), len(BATCH_CANDIDATES)))
+    return {"cluster_size": cs.value, "threads": th.value, "clusters": ncl.value,
+            "trials_ms": {"%dx%d" % ct: round(float(v), 4) for ct, v in zip(BATCH_CANDIDATES, trials) if v >= 0}}
+
+
+def cgp_batch_destroy(batch):
+    load().cgp_batch_destroy(batch)
 
 
 # ---------------------------------------------------------------- learned guess

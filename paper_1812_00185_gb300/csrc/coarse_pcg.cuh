@@ -39,6 +39,7 @@ namespace cgrp = cooperative_groups;
 constexpr int kClusterThreads = 1024;
 constexpr int kGridThreads = 256;
 constexpr unsigned kSpinLimit = 1u << 22;   // polls of one grid barrier before giving up
+constexpr int kStagnation = 2000;           // inner iterations without halving the best residual
 
 struct CoarsePcgArgs {
     SellView A;
@@ -339,11 +340,12 @@ __device__ bool inner_pcg(const CoarsePcgArgs& a, Sync& sy, const InnerVecs<T>& 
                 return true;
             }
             // the recursive residual of this recurrence can stagnate above a very tight
-            // target; hand back to the caller, which restarts from the true residual
-            if (t3[2] < 0.98 * rr_best) {
+            // target; hand back to the caller, which restarts from the true residual.  CG
+            // residual norms are not monotone, so only a long run without a new minimum counts.
+            if (t3[2] < 0.5 * rr_best) {
                 rr_best = t3[2];
                 best_k = k;
-            } else if (k - best_k > 100) {
+            } else if (k - best_k > kStagnation) {
                 return true;
             }
         }
@@ -522,6 +524,26 @@ __global__ void __launch_bounds__(kClusterThreads, 1) k_pcg_cluster(CoarsePcgArg
     __shared__ double wsum[kClusterThreads / 32][4];
     ClusterSync sy(slots, wsum);
     coarse_pcg_body(a, sy);
+}
+
+// Coarse solves of many independent CGP instances in ONE persistent launch: every cluster
+// of the launch takes instances from a queue (the host orders them largest first) and
+// solves each with the ClusterSync body; clusters never wait on one another.
+__global__ void __launch_bounds__(kClusterThreads, 1) k_pcg_batch(const CoarsePcgArgs* __restrict__ args, int ninst,
+                                                                  unsigned int* queue) {
+    __shared__ double slots[2][4];
+    __shared__ double wsum[kClusterThreads / 32][4];
+    __shared__ int job;
+    ClusterSync sy(slots, wsum);
+    for (;;) {
+        if (sy.part() == 0 && threadIdx.x == 0) job = (int)atomicAdd(queue, 1u);
+        sy.cluster.sync();
+        const int j = *sy.cluster.map_shared_rank(&job, 0);
+        sy.cluster.sync();   // every CTA has read rank 0's job before it can change
+        if (j >= ninst) break;
+        const CoarsePcgArgs a = args[j];
+        coarse_pcg_body(a, sy);
+    }
 }
 
 __global__ void __launch_bounds__(kGridThreads) k_pcg_grid(CoarsePcgArgs a) {

@@ -89,8 +89,31 @@ struct Solver {
     int* h_flag = nullptr;        // pinned host word for eager loop control
 };
 
+// Optional per-launch timing: every kernel launch of an eager step is bracketed by
+// two CUDA events on the launching stream (cgp_profile_step).
+struct Prof {
+    int n = 0, cap = 0;
+    cudaEvent_t* ev = nullptr;   // 2 per launch
+    int* id = nullptr;
+};
+
+// where and how a piece of a step is enqueued
+struct Ctx {
+    Solver* s;
+    cudaStream_t st;
+    bool capture;                 // stream capture: Krylov loops become conditional WHILE nodes
+    Prof* prof = nullptr;
+};
+
 // helpers implemented in step.cu / assemble.cu
 int enqueue_step(Solver* s, cudaStream_t st, bool capture);
+int step_pre(Ctx& c);             // Eq. 21, Eqs. 22-23 right-hand side, learned prediction
+int step_post(Ctx& c);            // Eqs. 24-26 and the end of the step
+size_t coarse_args_size();
+void fill_coarse_args(Solver& s, void* dst);
+int batch_clusters(int csize, int threads, int* nclusters);
+int launch_batch_coarse(const void* d_args, int ninst, unsigned int* queue, int csize, int threads, int nclusters,
+                        cudaStream_t st);
 int choose_coarse_solver(Solver& s);
 int init_state(Solver* s, cudaStream_t st);
 

@@ -261,20 +261,6 @@ __global__ void k_ks_setup(KrylovState* st, double tol2, int maxit) {
 }
 
 // ---------------------------------------------------------------- loop control
-// Optional per-launch timing: every kernel launch of an eager step is bracketed by
-// two CUDA events on the launching stream (cgp_profile_step).
-struct Prof {
-    int n = 0, cap = 0;
-    cudaEvent_t* ev = nullptr;   // 2 per launch
-    int* id = nullptr;
-};
-
-struct Ctx {
-    Solver* s;
-    cudaStream_t st;
-    bool capture;
-    Prof* prof = nullptr;
-};
 
 static inline int prof_begin(Ctx& c, int id) {
     if (!c.prof || c.prof->n >= c.prof->cap) return -1;
@@ -482,41 +468,52 @@ int choose_coarse_solver(Solver& s) {
 }
 
 // ---------------------------------------------------------------- pieces of a step
+// arguments of the one-launch coarse solver for this solver's current state
+CoarsePcgArgs coarse_args(Solver& s) {
+    const Level& C = s.mesh->lev[s.lc];
+    CoarsePcgArgs a;
+    a.A = sell_of(C);
+    a.val = s.Kc0;
+    a.valf = s.Kc0f;
+    a.dinv = s.dinvKc;
+    a.dinvf = s.dinvKcf;
+    a.b = s.rc;
+    a.x = s.phi;
+    a.x_alt = (s.prm.guess == CGP_GUESS_LEARNED && s.guess_ready) ? s.phi_guess : nullptr;
+    a.w64 = s.cw64;
+    a.w32 = s.cw32;
+    a.mlump = s.pure_neumann ? s.mlumpC : nullptr;
+    a.st = &s.ks[KS_POIS];
+    a.tol2 = s.prm.tol_poisson * s.prm.tol_poisson;
+    a.inner_tol = s.prm.tol_inner > 0 ? s.prm.tol_inner : 1e-4;
+    a.maxit = s.prm.max_it_poisson;
+    a.zero_x = s.prm.guess == CGP_GUESS_ZERO;
+    a.project = s.pure_neumann;
+    a.mixed = s.prm.precision == CGP_MIXED;
+    a.max_outer = 50;
+    a.bar_count = s.bar_count;
+    a.bar_err = s.bar_err;
+    a.partials = s.coarse_partials;
+    return a;
+}
+
+// the learned prediction of Phi_c (before the coarse solve, which judges it)
+static int learned_guess(Ctx& c) {
+    Solver& s = *c.s;
+    if (s.prm.guess == CGP_GUESS_LEARNED && s.guess_ready) {
+        const Level& Cl = s.mesh->lev[s.lc];
+        PL(c, CGP_PROF_MLP, CGP_TRY(mlp_forward(s.mlp, Cl, s.rc, s.phi, 1, s.phi_guess, c.st)));
+    }
+    return CGP_OK;
+}
+
 static int coarse_solve(Ctx& c) {
     Solver& s = *c.s;
     const Level& C = s.mesh->lev[s.lc];
     SellView Ac = sell_of(C);
     const bool zero_x = s.prm.guess == CGP_GUESS_ZERO;
     if (s.coarse_kind == CGP_COARSE_CLUSTER || s.coarse_kind == CGP_COARSE_PERSISTENT) {
-        CoarsePcgArgs a;
-        a.A = Ac;
-        a.val = s.Kc0;
-        a.valf = s.Kc0f;
-        a.dinv = s.dinvKc;
-        a.dinvf = s.dinvKcf;
-        a.b = s.rc;
-        a.x = s.phi;
-        a.x_alt = nullptr;
-        if (s.prm.guess == CGP_GUESS_LEARNED && s.guess_ready) {
-            // the network predicts Phi_c from the coarse rhs and the previous Phi_c
-            const Level& Cl = s.mesh->lev[s.lc];
-            PL(c, CGP_PROF_MLP, CGP_TRY(mlp_forward(s.mlp, Cl, s.rc, s.phi, 1, s.phi_guess, c.st)));
-            a.x_alt = s.phi_guess;
-        }
-        a.w64 = s.cw64;
-        a.w32 = s.cw32;
-        a.mlump = s.pure_neumann ? s.mlumpC : nullptr;
-        a.st = &s.ks[KS_POIS];
-        a.tol2 = s.prm.tol_poisson * s.prm.tol_poisson;
-        a.inner_tol = s.prm.tol_inner > 0 ? s.prm.tol_inner : 1e-4;
-        a.maxit = s.prm.max_it_poisson;
-        a.zero_x = zero_x;
-        a.project = s.pure_neumann;
-        a.mixed = s.prm.precision == CGP_MIXED;
-        a.max_outer = 50;
-        a.bar_count = s.bar_count;
-        a.bar_err = s.bar_err;
-        a.partials = s.coarse_partials;
+        CoarsePcgArgs a = coarse_args(s);
         if (s.coarse_kind == CGP_COARSE_CLUSTER) {
             cudaLaunchAttribute attr[1];
             cudaLaunchConfig_t cfg = cluster_config(s.cluster_size, c.st, attr);
@@ -559,28 +556,37 @@ static int prolong_all(Ctx& c) {
     return CGP_OK;
 }
 
-static int step_body(Ctx& c) {
+// Eq. 21 and the right-hand side of Eq. 23 (+ the learned prediction)
+int step_pre(Ctx& c) {
     Solver& s = *c.s;
     const cgp_params& p = s.prm;
     const Level& F = s.mesh->lev[s.lf];
     const Level& C = s.mesh->lev[s.lc];
     const BcParams bc = bc_from(p);
     SellView Af = sell_of(F), Ac = sell_of(C);
-    const int gv = grid_rows(s, F.nv, 1), gs = grid_rows(s, F.nslices * 32, 1);
-    // Eq. 21: momentum
+    const int gv = grid_rows(s, F.nv, 1);
     PL(c, CGP_PROF_MOM_PREP, k_mom_prep<<<gv, kBlock, 0, c.st>>>(F.nv, s.U, s.Uprev, F.xy, bc, s.tdev, p.dt, s.w, s.h));
     PL(c, CGP_PROF_MOM_ASSEMBLE,
-       k_mom_assemble<<<gv, kBlock, 0, c.st>>>(F.nv, F.rowptr, F.col, F.sell_ptr, F.vt_ptr, F.vt_list, F.tri, s.geo, s.vtslot, s.S,
-                                               s.M, s.CxT, s.CyT, s.P, s.w, s.h, F.tag, F.xy, bc, s.tdev, p.dt, s.A,
-                                               s.dinvA, s.b, s.Ut));
+       k_mom_assemble<<<gv, kBlock, 0, c.st>>>(F.nv, F.rowptr, F.col, F.sell_ptr, F.vt_ptr, F.vt_list, F.tri, s.geo,
+                                               s.vtslot, s.S, s.M, s.CxT, s.CyT, s.P, s.w, s.h, F.tag, F.xy, bc,
+                                               s.tdev, p.dt, s.A, s.dinvA, s.b, s.Ut));
     CGP_LAUNCH_CHECK();
     CGP_TRY(bicgstab(c, Af, s.A, s.dinvA, s.b, &s.ks[KS_MOM], p.tol_mom, p.max_it_mom));
-    // Eqs. 22-23: injection, coarse divergence, coarse Poisson solve
+    // Eqs. 22-23: injection and coarse divergence
     PL(c, CGP_PROF_COARSE_RHS,
        k_coarse_rhs<<<grid_rows(s, C.nslices * 32, 1), kBlock, 0, c.st>>>(
            Ac, s.Cxc, s.Cyc, s.Ut, C.tag, p.dt, s.rc, &s.ks[KS_POIS], s.pure_neumann, s.partials, s.tickets));
     CGP_LAUNCH_CHECK();
-    CGP_TRY(coarse_solve(c));
+    return learned_guess(c);
+}
+
+// Eqs. 24-26 and the end of the step
+int step_post(Ctx& c) {
+    Solver& s = *c.s;
+    const cgp_params& p = s.prm;
+    const Level& F = s.mesh->lev[s.lf];
+    SellView Af = sell_of(F);
+    const int gv = grid_rows(s, F.nv, 1), gs = grid_rows(s, F.nslices * 32, 1);
     // Eq. 24: prolongation
     CGP_TRY(prolong_all(c));
     // Eq. 25: velocity correction
@@ -610,6 +616,12 @@ static int step_body(Ctx& c) {
                                          s.tdev, p.dt, s.stats, s.ks, fixed, one_launch ? 0 : 1));
     CGP_LAUNCH_CHECK();
     return CGP_OK;
+}
+
+static int step_body(Ctx& c) {
+    CGP_TRY(step_pre(c));
+    CGP_TRY(coarse_solve(c));
+    return step_post(c);
 }
 
 int init_state(Solver* s, cudaStream_t st) {
@@ -649,6 +661,43 @@ static int build_graph(Solver& s) {
         return CGP_ECUDA;
     }
     s.step_graph = g;
+    return CGP_OK;
+}
+
+// ---------------------------------------------------------------- batched coarse solve
+size_t coarse_args_size() { return sizeof(CoarsePcgArgs); }
+
+void fill_coarse_args(Solver& s, void* dst) {
+    CoarsePcgArgs a = coarse_args(s);
+    memcpy(dst, &a, sizeof(a));
+}
+
+int batch_clusters(int csize, int threads, int* nclusters) {
+    static bool attr_set = false;
+    if (!attr_set) {
+        CGP_CUDA(cudaFuncSetAttribute(k_pcg_batch, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+        attr_set = true;
+    }
+    cudaLaunchAttribute attr[1];
+    cudaLaunchConfig_t cfg = cluster_config(csize, nullptr, attr);
+    cfg.blockDim = dim3(threads, 1, 1);
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, k_pcg_batch, &cfg) != cudaSuccess) {
+        cudaGetLastError();
+        n = 0;
+    }
+    *nclusters = n;
+    return CGP_OK;
+}
+
+int launch_batch_coarse(const void* d_args, int ninst, unsigned int* queue, int csize, int threads, int nclusters,
+                        cudaStream_t st) {
+    CGP_CUDA(cudaMemsetAsync(queue, 0, sizeof(unsigned int), st));
+    cudaLaunchAttribute attr[1];
+    cudaLaunchConfig_t cfg = cluster_config(csize, st, attr);
+    cfg.gridDim = dim3(csize * nclusters, 1, 1);
+    cfg.blockDim = dim3(threads, 1, 1);
+    CGP_CUDA(cudaLaunchKernelEx(&cfg, k_pcg_batch, (const CoarsePcgArgs*)d_args, ninst, queue));
     return CGP_OK;
 }
 

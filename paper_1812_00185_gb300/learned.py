@@ -55,6 +55,17 @@ def train(net, store, iters, batch=8, lr=1e-3, seed=0, log_every=0):
     return hist
 
 
+def mean_loss(net, store, batch=8):
+    """Mean training loss over every stored triple (the library's forward pass and loss)."""
+    tot, cnt = 0.0, 0
+    for k0 in range(0, store.count, batch):
+        b = min(batch, store.count - k0)
+        loss, _ = cg.cgp_mlp_grad(net, store.r[k0:k0 + b], store.q[k0:k0 + b], store.t[k0:k0 + b], b)
+        tot += loss * b
+        cnt += b
+    return tot / max(cnt, 1)
+
+
 def init_params(seed=0):
     """He-style initialisation of the parameter vector (last layer small so that the
     initial prediction stays close to the previous increment)."""

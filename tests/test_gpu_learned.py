@@ -76,7 +76,7 @@ def test_forward_and_gradients_match_oracle(cg):
 
 def test_training_and_learned_guess_in_the_step(cg):
     import torch
-    from paper_1812_00185_gb300.learned import PairStore, train, init_params
+    from paper_1812_00185_gb300.learned import PairStore, train, init_params, mean_loss
     base = channel_cylinder_mesh(seed=7, h=0.03)
     mesh = cg.Mesh(base.xy, base.tri, base.tag, 2)
     common = dict(chi=1, k=1, bc_kind=cg.CGP_BC_CHANNEL, bc_param=(0.3, 0.41), tol_mom=1e-10, tol_poisson=1e-8,
@@ -88,8 +88,12 @@ def test_training_and_learned_guess_in_the_step(cg):
     rec.close()
     net = cg.cgp_mlp_create(mesh.handle, 1, 8)
     cg.cgp_mlp_set_params(net, init_params(0))
-    hist = train(net, store, 300, batch=8, lr=2e-3, log_every=50)
-    assert hist[-1][1] < hist[0][1], hist
+    before = mean_loss(net, store)
+    train(net, store, 300, batch=8, lr=1e-3)
+    after = mean_loss(net, store)
+    print("training loss over the 80 recorded steps: %.4g before, %.4g after 300 Adam steps" % (before, after))
+    # the fit improves; how much the prediction helps the solver is measured below
+    assert after < before, (before, after)
     # the same 40 steps with the previous-increment guess and with the learned guess
     out = {}
     for mode in (cg.CGP_GUESS_PREV, cg.CGP_GUESS_LEARNED):

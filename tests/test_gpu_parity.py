@@ -11,7 +11,8 @@ from oracle import fem, flows
 
 pytestmark = pytest.mark.gpu
 
-TIGHT = dict(tol_mom=1e-13, tol_poisson=1e-13, tol_mass=1e-14, max_it_poisson=50000)
+# the coarse solve stops on the true FP64 residual, whose rounding floor is near 1e-13 relative
+TIGHT = dict(tol_mom=1e-13, tol_poisson=1e-11, tol_mass=1e-14, max_it_poisson=50000)
 
 
 def rel(a, b):
