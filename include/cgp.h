@@ -93,7 +93,7 @@ typedef struct {
     int32_t bc_kind;           /* CGP_BC_* */
     double bc_param[4];
     int32_t use_graph;         /* 1: replay each step as a CUDA graph with device-side loop control */
-    double tol_inner;          /* CGP_MIXED: residual reduction asked of each FP32 inner solve (0 = 1e-4) */
+    double tol_inner;          /* CGP_MIXED: residual reduction asked of each FP32 inner solve (0 = 1e-3) */
     int32_t coarse_mode;       /* coarse Poisson solver: CGP_COARSE_AUTO | _GRID | _CLUSTER */
     int32_t cluster_size;      /* CTAs of the cluster solver (0 = largest that fits, else 2..16) */
 } cgp_params;
@@ -258,6 +258,29 @@ int cgp_mlp_train_step(cgp_mlp* m, const double* r, const double* q, const doubl
  * pressure-increment level is the network's level.  Synchronises. */
 int cgp_guess_set(cgp_solver* s, const cgp_mlp* m, cgp_stream_t stream);
 void cgp_mlp_destroy(cgp_mlp* m);
+
+/* ---- allocation-free solve (the paper has no counterpart) ----
+ * For callers that cannot call cudaMalloc (a host program that owns every device
+ * allocation, a fixed-memory real-time loop, a plug-in handed only the buffers it may
+ * touch): solves A x = b for a symmetric positive definite A with the library's Jacobi-
+ * preconditioned, one-launch PCG (the coarse-solve kernel of Eq. 23, Chronopoulos-Gear
+ * recurrence, true-residual stopping test ||b - A x|| <= tol ||b||) and allocates nothing:
+ * every scratch word lives in one fixed file-scope device array of about 4.3 MB that each
+ * device loading the library keeps until the process exits.
+ *  - A in SELL-32 form (see cgp_mesh_get_level: slice s = rows 32s..32s+31, entries of a
+ *    slice column-major, width = its longest row, padding with value 0): sell_ptr
+ *    (nslices+1 offsets), sell_col, val; dinv = 1/diag(A).  n <= 65536 rows, else
+ *    CGP_EINVAL.  All pointers are device memory owned by the caller.
+ *  - x: initial guess on entry, solution on exit.  info: 2 device int32 written at the end
+ *    of the solve: iterations, status (CGP_OK, CGP_ENOTCONV, CGP_EBREAKDOWN, ...).
+ *  - Asynchronous on `stream`.  The first call on a device looks up the array's device
+ *    address and the launch size (make it before any stream capture); later calls only
+ *    enqueue a memset of the barrier counter, the solve and a status copy.
+ *  - Every call shares the one array: calls whose solves may overlap on the GPU (different
+ *    streams without ordering, or other host threads) race and must not be made. */
+int cgp_pcg_sell_noalloc(int32_t n, int32_t nslices, const int32_t* sell_ptr, const int32_t* sell_col,
+                         const double* val, const double* dinv, const double* b, double* x, double tol,
+                         int32_t maxit, int32_t* info, cgp_stream_t stream);
 
 #ifdef __cplusplus
 }

@@ -101,6 +101,8 @@ _SIGS = {
     "cgp_batch_info": (c_int32, [c_void_p, POINTER(c_int32), POINTER(c_int32), POINTER(c_int32), c_void_p,
                                  c_int32]),
     "cgp_batch_destroy": (None, [c_void_p]),
+    "cgp_pcg_sell_noalloc": (c_int32, [c_int32, c_int32, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
+                                       c_double, c_int32, c_void_p, c_void_p]),
 }
 
 BATCH_CANDIDATES = [(c, t) for c in (1, 2, 4, 8) for t in (256, 512, 1024)]
@@ -314,6 +316,13 @@ def cgp_profile_step(solver, stream=None):
 
 def cgp_solver_destroy(solver):
     load().cgp_solver_destroy(solver)
+
+
+# ---------------------------------------------------------------- allocation-free solve
+def cgp_pcg_sell_noalloc(n, nslices, sell_ptr, sell_col, val, dinv, b, x, tol, maxit, info, stream=None):
+    """All array arguments are device tensors; see include/cgp.h.  Asynchronous."""
+    _check(load().cgp_pcg_sell_noalloc(int(n), int(nslices), _ptr(sell_ptr), _ptr(sell_col), _ptr(val), _ptr(dinv),
+                                       _ptr(b), _ptr(x), float(tol), int(maxit), _ptr(info), _stream(stream)))
 
 
 # ---------------------------------------------------------------- batches

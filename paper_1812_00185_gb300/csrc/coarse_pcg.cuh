@@ -39,7 +39,8 @@ namespace cgrp = cooperative_groups;
 constexpr int kClusterThreads = 1024;
 constexpr int kGridThreads = 256;
 constexpr unsigned kSpinLimit = 1u << 22;   // polls of one grid barrier before giving up
-constexpr int kStagnation = 2000;           // inner iterations without halving the best residual
+constexpr int kStagnation = 2000;           // FP64 inner iterations without halving the best residual
+constexpr int kStagnation32 = 300;          // the same for the FP32 inner solve of the mixed form
 
 struct CoarsePcgArgs {
     SellView A;
@@ -345,8 +346,8 @@ __device__ bool inner_pcg(const CoarsePcgArgs& a, Sync& sy, const InnerVecs<T>& 
             if (t3[2] < 0.5 * rr_best) {
                 rr_best = t3[2];
                 best_k = k;
-            } else if (k - best_k > kStagnation) {
-                return true;
+            } else if (k - best_k > (sizeof(T) == 4 ? kStagnation32 : kStagnation) || t3[2] > 1e4 * rr_best) {
+                return true;   // stagnating, or the low-precision recurrence is drifting away
             }
         }
     }
@@ -519,7 +520,7 @@ __device__ void coarse_pcg_body(const CoarsePcgArgs& a, Sync& sy) {
     sy.finish();
 }
 
-__global__ void __launch_bounds__(kClusterThreads, 1) k_pcg_cluster(CoarsePcgArgs a) {
+static __global__ void __launch_bounds__(kClusterThreads, 1) k_pcg_cluster(CoarsePcgArgs a) {
     __shared__ double slots[2][4];
     __shared__ double wsum[kClusterThreads / 32][4];
     ClusterSync sy(slots, wsum);
@@ -529,7 +530,7 @@ __global__ void __launch_bounds__(kClusterThreads, 1) k_pcg_cluster(CoarsePcgArg
 // Coarse solves of many independent CGP instances in ONE persistent launch: every cluster
 // of the launch takes instances from a queue (the host orders them largest first) and
 // solves each with the ClusterSync body; clusters never wait on one another.
-__global__ void __launch_bounds__(kClusterThreads, 1) k_pcg_batch(const CoarsePcgArgs* __restrict__ args, int ninst,
+static __global__ void __launch_bounds__(kClusterThreads, 1) k_pcg_batch(const CoarsePcgArgs* __restrict__ args, int ninst,
                                                                   unsigned int* queue) {
     __shared__ double slots[2][4];
     __shared__ double wsum[kClusterThreads / 32][4];
@@ -546,7 +547,7 @@ __global__ void __launch_bounds__(kClusterThreads, 1) k_pcg_batch(const CoarsePc
     }
 }
 
-__global__ void __launch_bounds__(kGridThreads) k_pcg_grid(CoarsePcgArgs a) {
+static __global__ void __launch_bounds__(kGridThreads) k_pcg_grid(CoarsePcgArgs a) {
     __shared__ double wsum[kGridThreads / 32][4];
     GridSync sy(a.bar_count, a.bar_err, a.partials, wsum);
     coarse_pcg_body(a, sy);
