@@ -100,10 +100,13 @@ typedef struct {
 
 /* Coarse Poisson solver kinds.  KERNELS: two kernel launches per PCG iteration (graph
  * WHILE loop).  PERSISTENT: the whole solve in one cooperative launch over the GPU with a
- * bounded software grid barrier.  CLUSTER: the whole solve in one launch of one
- * thread-block cluster, reductions through distributed shared memory.  AUTO = PERSISTENT.
- * CGP_MIXED needs PERSISTENT or CLUSTER. */
-enum { CGP_COARSE_AUTO = 0, CGP_COARSE_KERNELS = 1, CGP_COARSE_CLUSTER = 2, CGP_COARSE_PERSISTENT = 3 };
+ * bounded software grid barrier; in FP64, when every row has at most 16 entries and the
+ * mesh fits one 32-row slice per warp, each thread keeps its row and its PCG vectors in
+ * registers.  PERSISTENT_MEM: the same without register residency.  CLUSTER: the whole
+ * solve in one launch of one thread-block cluster, reductions through distributed shared
+ * memory.  AUTO = PERSISTENT.  CGP_MIXED needs PERSISTENT(_MEM) or CLUSTER. */
+enum { CGP_COARSE_AUTO = 0, CGP_COARSE_KERNELS = 1, CGP_COARSE_CLUSTER = 2, CGP_COARSE_PERSISTENT = 3,
+       CGP_COARSE_PERSISTENT_MEM = 4 };
 
 /* Per-run statistics. */
 typedef struct {

@@ -21,7 +21,7 @@ CGP_BC_CAVITY, CGP_BC_CHANNEL, CGP_BC_TG, CGP_BC_TG_PERIODIC = 0, 1, 2, 3
 CGP_FP64, CGP_MIXED = 0, 1
 CGP_GUESS_ZERO, CGP_GUESS_PREV, CGP_GUESS_LEARNED = 0, 1, 2
 CGP_MASS_CONSISTENT, CGP_MASS_LUMPED = 0, 1
-CGP_COARSE_AUTO, CGP_COARSE_KERNELS, CGP_COARSE_CLUSTER, CGP_COARSE_PERSISTENT = 0, 1, 2, 3
+CGP_COARSE_AUTO, CGP_COARSE_KERNELS, CGP_COARSE_CLUSTER, CGP_COARSE_PERSISTENT, CGP_COARSE_PERSISTENT_MEM = 0, 1, 2, 3, 4
 CGP_HOST, CGP_DEVICE = 0, 1
 (CGP_VEC_U, CGP_VEC_UPREV, CGP_VEC_P, CGP_VEC_UTILDE, CGP_VEC_RHS_C, CGP_VEC_PHI_C,
  CGP_VEC_PHI_F) = range(7)

@@ -202,7 +202,7 @@ static int check_params(const cgp_mesh* m, const cgp_params* p) {
         p->max_it_poisson < 1 || p->max_it_mass < 1 || p->bc_kind < 0 || p->bc_kind > CGP_BC_TG_PERIODIC ||
         (p->precision != CGP_FP64 && p->precision != CGP_MIXED) || p->guess < 0 || p->guess > 2 ||
         (p->mass_mode != CGP_MASS_CONSISTENT && p->mass_mode != CGP_MASS_LUMPED) || p->coarse_mode < 0 ||
-        p->coarse_mode > CGP_COARSE_PERSISTENT || p->cluster_size < 0 || p->cluster_size > 16 || p->tol_inner < 0 ||
+        p->coarse_mode > CGP_COARSE_PERSISTENT_MEM || p->cluster_size < 0 || p->cluster_size > 16 || p->tol_inner < 0 ||
         p->tol_inner >= 1) {
         set_error("invalid cgp_params");
         return CGP_EINVAL;

@@ -38,7 +38,7 @@ namespace cgrp = cooperative_groups;
 
 constexpr int kClusterThreads = 1024;
 constexpr int kGridThreads = 256;
-constexpr unsigned kSpinLimit = 1u << 22;   // polls of one grid barrier before giving up
+constexpr unsigned kSpinLimit = 1u << 24;   // polls of one grid barrier before giving up (~seconds)
 constexpr int kStagnation = 2000;           // FP64 inner iterations without halving the best residual
 constexpr int kStagnation32 = 300;          // the same for the FP32 inner solve of the mixed form
 
@@ -144,22 +144,24 @@ struct GridSync {
         ++gen;
         if (threadIdx.x == 0) {
             int good = 1;
-            __threadfence();
-            atomicAdd(count, 1u);
+            // arrive: a release-ordered add publishes this CTA's writes (cumulative over the
+            // CTA through the barrier above); wait: acquire-spin on the counter
+            asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(count) : "memory");
             const unsigned target = gen * gridDim.x;
             unsigned spins = 0;
             for (;;) {
                 const unsigned v = ld_acquire_gpu(count);
                 if ((int)(v - target) >= 0) break;
-                if (*(volatile int*)err) { good = 0; break; }
                 if (++spins > kSpinLimit) {
                     atomicExch(err, 1);
                     good = 0;
                     break;
                 }
-                __nanosleep(32);
+                if ((spins & 63) == 0 && *(volatile int*)err) {
+                    good = 0;
+                    break;
+                }
             }
-            __threadfence();
             ok = good;
         }
         __syncthreads();
@@ -254,10 +256,13 @@ __device__ __forceinline__ T row_spmv(const SellView& A, const double* __restric
 // Inner PCG (Chronopoulos-Gear) on A e = r0 in precision T, starting from e = 0 and from
 // r = r0, u = D^{-1} r0 already in V (written before the last barrier).  gamma0 = <r0,u0>.
 // Returns false on a barrier timeout.  iters counts iterations across calls.
+// outcome: 0 = ended normally (target met, or stagnation), 1 = breakdown before an update
+// (the iterate is intact), 2 = a non-finite value after an update (the iterate is not).
 template <class T, class Sync>
 __device__ bool inner_pcg(const CoarsePcgArgs& a, Sync& sy, const InnerVecs<T>& V, const T* __restrict__ dinv,
-                          int s_begin, int s_end, double gamma, double stop2, int& iters, int& status,
+                          int s_begin, int s_end, double gamma, double stop2, int& iters, int& outcome,
                           double& rr_last, bool& done) {
+    outcome = 0;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const SellView& A = a.A;
     // w0 = A u, delta = <w0, u>
@@ -290,7 +295,7 @@ __device__ bool inner_pcg(const CoarsePcgArgs& a, Sync& sy, const InnerVecs<T>& 
                 alpha = gamma / (delta - beta * gamma / alpha_prev);
             }
             if (!isfinite(alpha) || alpha == 0.0) {
-                status = isfinite(alpha) ? CGP_EBREAKDOWN : CGP_ENONFINITE;
+                outcome = 1;
                 return true;
             }
             const T al = (T)alpha, be = (T)beta;
@@ -329,8 +334,12 @@ __device__ bool inner_pcg(const CoarsePcgArgs& a, Sync& sy, const InnerVecs<T>& 
             gamma = t3[0];
             delta = t3[1];
             rr_last = t3[2];
-            if (!isfinite(t3[2]) || !isfinite(t3[0])) {
-                status = CGP_ENONFINITE;
+            if (!isfinite(t3[2]) || !isfinite(t3[0]) || !isfinite(t3[1])) {
+                outcome = 2;
+                return true;
+            }
+            if (t3[0] == 0.0 || t3[2] == 0.0) {   // exact solution reached: nothing left to do
+                done = true;
                 return true;
             }
             T* tmp = wc;
@@ -346,9 +355,101 @@ __device__ bool inner_pcg(const CoarsePcgArgs& a, Sync& sy, const InnerVecs<T>& 
             if (t3[2] < 0.5 * rr_best) {
                 rr_best = t3[2];
                 best_k = k;
-            } else if (k - best_k > (sizeof(T) == 4 ? kStagnation32 : kStagnation) || t3[2] > 1e4 * rr_best) {
-                return true;   // stagnating, or the low-precision recurrence is drifting away
+            } else if (sizeof(T) == 4 && t3[2] > 1e4 * rr_best) {
+                outcome = 2;   // the FP32 recurrence is drifting away: its iterate is not to be used
+                return true;
+            } else if (k - best_k > (sizeof(T) == 4 ? kStagnation32 : kStagnation)) {
+                return true;   // stagnating: restart from the true residual
             }
+        }
+    }
+    return true;
+}
+
+// Inner PCG in its classical form (two reductions per iteration) on A e = r0 in precision
+// T, from e = 0 and r = r0, u = D^{-1} r0 in V; p and q use V.p/V.s (p double-buffered
+// with V.q because the SpMV gathers p at neighbouring rows while rows are rewritten).
+// Used for the FP32 inner solves of the mixed form, where the longer recurrence of the
+// one-reduction form drifts.  Same outcome codes as inner_pcg.
+template <class T, class Sync>
+__device__ bool inner_pcg_classic(const CoarsePcgArgs& a, Sync& sy, const InnerVecs<T>& V,
+                                  const T* __restrict__ dinv, int s_begin, int s_end, double rz, double stop2,
+                                  int& iters, int& outcome, bool& done) {
+    outcome = 0;
+    done = false;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const SellView& A = a.A;
+    T* p_old = V.u;   // the first direction is z = u itself
+    T* p_new = V.p;
+    T* z = V.u;       // u holds D^{-1} r
+    T* q = V.q;
+    double beta = 0.0, rr_best = INFINITY;
+    int best_k = 0;
+    for (int k = 0; iters < a.maxit; ++k) {
+        // phase A: p_new = z + beta p_old (p_old = z at k = 0), q = A p_new, <p_new, q>
+        const T be = (T)beta;
+        double pq_acc[1] = {0.0};
+        for (int sl = s_begin + wid; sl < s_end; sl += nw) {
+            const int i = sl * 32 + lane;
+            const T qi = row_spmv<T>(A, a.val, a.valf, sl, lane,
+                                     [&](int j) { return k ? ldcg(z + j) + be * ldcg(p_old + j) : ldcg(z + j); });
+            if (i < A.n) {
+                const T pv = k ? ldcg(z + i) + be * ldcg(p_old + i) : ldcg(z + i);
+                __stcg(p_new + i, pv);
+                __stcg(q + i, qi);
+                pq_acc[0] += (double)pv * (double)qi;
+            }
+        }
+        double pq[1];
+        if (!sy.template sum<1>(pq_acc, pq)) return false;
+        if (!(pq[0] != 0.0) || !isfinite(pq[0])) {
+            outcome = 1;
+            return true;
+        }
+        const double alpha = rz / pq[0];
+        const T al = (T)alpha;
+        // phase B: e += alpha p, r -= alpha q, z = D^{-1} r; <r,z>, <r,r>
+        double acc2[2] = {0.0, 0.0};
+        for (int sl = s_begin + wid; sl < s_end; sl += nw) {
+            const int i = sl * 32 + lane;
+            if (i >= A.n) continue;
+            __stcg(V.e + i, ldcg(V.e + i) + al * ldcg(p_new + i));
+            const T rv = ldcg(V.r + i) - al * ldcg(q + i);
+            const T zv = __ldg(dinv + i) * rv;
+            __stcg(V.r + i, rv);
+            __stcg(V.z + i, zv);
+            acc2[0] += (double)rv * (double)zv;
+            acc2[1] += (double)rv * (double)rv;
+        }
+        double t2[2];
+        if (!sy.template sum<2>(acc2, t2)) return false;
+        ++iters;
+        if (!isfinite(t2[0]) || !isfinite(t2[1])) {
+            outcome = 2;
+            return true;
+        }
+        if (t2[0] == 0.0 || t2[1] == 0.0) {
+            done = true;
+            return true;
+        }
+        beta = t2[0] / rz;
+        rz = t2[0];
+        // from now on z lives in V.z, and the directions alternate between V.p and V.s
+        z = V.z;
+        p_old = p_new;
+        p_new = (p_new == V.p) ? V.s : V.p;
+        if (t2[1] <= stop2) {
+            done = true;
+            return true;
+        }
+        if (t2[1] < 0.5 * rr_best) {
+            rr_best = t2[1];
+            best_k = k;
+        } else if (t2[1] > 1e4 * rr_best) {
+            outcome = 2;
+            return true;
+        } else if (k - best_k > kStagnation32) {
+            return true;
         }
     }
     return true;
@@ -371,6 +472,7 @@ __device__ void coarse_pcg_body(const CoarsePcgArgs& a, Sync& sy) {
                          a.w32 + 6 * n, a.w32 + 7 * n, a.w32 + 8 * n};
     double bb = 0.0, rr_final = 0.0;
     int iters = 0, status = 0, outer = 0, used_alt = 0;
+    bool mixed_now = a.mixed != 0;   // cleared if an FP32 inner solve ever produces a non-finite value
     bool converged = false;
     if (a.x_alt && !a.zero_x) {
         // the judge of the learned guess: keep whichever start has the smaller FP64 residual
@@ -414,7 +516,7 @@ __device__ void coarse_pcg_body(const CoarsePcgArgs& a, Sync& sy) {
                 }
                 if (a.zero_x && outer == 0) __stcg(xv + i, 0.0);
                 const double ri = bi - axv[0];
-                if (a.mixed) {
+                if (mixed_now) {
                     const float rf = (float)ri;
                     const float uf = __ldg(a.dinvf + i) * rf;
                     __stcg(V32.r + i, rf);
@@ -453,23 +555,29 @@ __device__ void coarse_pcg_body(const CoarsePcgArgs& a, Sync& sy) {
         }
         bool inner_done = false;
         bool ok;
-        if (a.mixed) {
+        int outcome = 0;
+        double rr_in = 0.0;
+        if (mixed_now) {
             const double stop2 = fmax(a.inner_tol * a.inner_tol * rr0, 0.25 * tol2 * bb);
-            double rr_in = 0.0;
-            ok = inner_pcg<float>(a, sy, V32, a.dinvf, s_begin, s_end, tot[2], stop2, iters, status, rr_in,
-                                  inner_done);
+            ok = inner_pcg_classic<float>(a, sy, V32, a.dinvf, s_begin, s_end, tot[2], stop2, iters, outcome,
+                                          inner_done);
         } else {
             // FP64: the inner recurrence updates x itself; the next outer pass re-checks the true residual
-            double rr_in = 0.0;
-            ok = inner_pcg<double>(a, sy, V64, a.dinv, s_begin, s_end, tot[2], 0.25 * tol2 * bb, iters, status,
+            ok = inner_pcg<double>(a, sy, V64, a.dinv, s_begin, s_end, tot[2], 0.25 * tol2 * bb, iters, outcome,
                                    rr_in, inner_done);
         }
         if (!ok) {
             status = CGP_ETIMEOUT;
             break;
         }
-        if (status) break;
-        if (a.mixed) {
+        if (outcome == 2 && !mixed_now) {
+            status = CGP_ENONFINITE;   // x itself is no longer finite
+            break;
+        }
+        if (outcome == 2) {
+            // the FP32 correction blew up: drop it and finish this solve with FP64 inner solves
+            mixed_now = false;
+        } else if (mixed_now) {
             for (int sl = s_begin + wid; sl < s_end; sl += nw) {
                 const int i = sl * 32 + lane;
                 if (i < A.n) __stcg(xv + i, ldcg(xv + i) + (double)ldcg(V32.e + i));

@@ -62,6 +62,7 @@ struct Solver {
     int coarse_kind = 0;          // CGP_COARSE_KERNELS / _CLUSTER / _PERSISTENT (AUTO resolved)
     int cluster_size = 0;         // CTAs of the one-cluster solver
     int coarse_grid = 0;          // CTAs of the persistent (cooperative) solver
+    bool coarse_rr = false;       // the persistent FP64 solve may keep its rows in registers
     unsigned int* bar_count = nullptr;   // grid barrier counter, followed by the error word
     int* bar_err = nullptr;
     double* coarse_partials = nullptr;   // 2 x max_grid x 4

@@ -1,9 +1,11 @@
 // One CGP time step on the device (paper Section 2.2, Eqs. 21-26) and its host
 // orchestration: eager launches with host-polled loop control, or a CUDA graph whose
 // Krylov loops are conditional WHILE nodes driven by the kernels themselves.
+#include <algorithm>
 #include <cstring>
 
 #include "coarse_pcg.cuh"
+#include "coarse_rr.cuh"
 #include "flows.cuh"
 #include "solver.cuh"
 
@@ -418,6 +420,8 @@ int choose_coarse_solver(Solver& s) {
     const cgp_params& p = s.prm;
     int mode = p.coarse_mode;
     if (mode == CGP_COARSE_AUTO) mode = CGP_COARSE_PERSISTENT;
+    const bool allow_rr = mode == CGP_COARSE_PERSISTENT;
+    if (mode == CGP_COARSE_PERSISTENT_MEM) mode = CGP_COARSE_PERSISTENT;
     s.coarse_kind = mode;
     s.cluster_size = 0;
     s.coarse_grid = 0;
@@ -445,6 +449,17 @@ int choose_coarse_solver(Solver& s) {
         const int cap = sms * (per_sm < 2 ? per_sm : 2);
         s.coarse_grid = need < cap ? need : cap;
         if (s.coarse_grid < 1) s.coarse_grid = 1;
+        // register-resident variant: every slice no wider than kRRWidth and one slice per warp
+        s.coarse_rr = false;
+        if (allow_rr) {
+            std::vector<int32_t> ptr(C.nslices + 1);
+            CGP_CUDA(cudaMemcpy(ptr.data(), C.sell_ptr, sizeof(int32_t) * (C.nslices + 1), cudaMemcpyDeviceToHost));
+            int wmax = 0;
+            for (int k = 0; k < C.nslices; ++k) wmax = std::max(wmax, (ptr[k + 1] - ptr[k]) / 32);
+            int per_sm_rr = 0;
+            CGP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_rr, k_pcg_grid_rr, kGridThreads, 0));
+            s.coarse_rr = wmax <= kRRWidth && per_sm_rr > 0 && rr_ctas_needed(C.nslices) <= sms * per_sm_rr;
+        }
         return CGP_OK;
     }
     CGP_CUDA(cudaFuncSetAttribute(k_pcg_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
@@ -485,7 +500,7 @@ CoarsePcgArgs coarse_args(Solver& s) {
     a.mlump = s.pure_neumann ? s.mlumpC : nullptr;
     a.st = &s.ks[KS_POIS];
     a.tol2 = s.prm.tol_poisson * s.prm.tol_poisson;
-    a.inner_tol = s.prm.tol_inner > 0 ? s.prm.tol_inner : 1e-4;
+    a.inner_tol = s.prm.tol_inner > 0 ? s.prm.tol_inner : 1e-3;
     a.maxit = s.prm.max_it_poisson;
     a.zero_x = s.prm.guess == CGP_GUESS_ZERO;
     a.project = s.pure_neumann;
@@ -522,7 +537,8 @@ static int coarse_solve(Ctx& c) {
         }
         CGP_CUDA(cudaMemsetAsync(s.bar_count, 0, 2 * sizeof(unsigned int), c.st));   // counter + error word
         cudaLaunchConfig_t cfg = {};
-        cfg.gridDim = dim3(s.coarse_grid, 1, 1);
+        const bool rr = s.coarse_rr && s.prm.precision == CGP_FP64;
+        cfg.gridDim = dim3(rr ? rr_ctas_needed(C.nslices) : s.coarse_grid, 1, 1);
         cfg.blockDim = dim3(kGridThreads, 1, 1);
         cfg.stream = c.st;
         cudaLaunchAttribute attr[1];
@@ -530,7 +546,8 @@ static int coarse_solve(Ctx& c) {
         attr[0].val.cooperative = 1;
         cfg.attrs = attr;
         cfg.numAttrs = 1;
-        PL(c, CGP_PROF_POIS_CLUSTER, CGP_CUDA(cudaLaunchKernelEx(&cfg, k_pcg_grid, a)));
+        if (rr) PL(c, CGP_PROF_POIS_CLUSTER, CGP_CUDA(cudaLaunchKernelEx(&cfg, k_pcg_grid_rr, a)));
+        else PL(c, CGP_PROF_POIS_CLUSTER, CGP_CUDA(cudaLaunchKernelEx(&cfg, k_pcg_grid, a)));
         return CGP_OK;
     }
     CGP_TRY(pcg<1>(c, Ac, s.Kc0, s.dinvKc, s.rc, s.phi, &s.ks[KS_POIS], s.prm.tol_poisson, s.prm.max_it_poisson,

@@ -79,7 +79,7 @@ def test_prolongation_bit_exact(cg):
     s.close(); m.close()
 
 
-@pytest.mark.parametrize("mode", ["kernels", "cluster", "persistent", "mixed", "mixed_cluster"])
+@pytest.mark.parametrize("mode", ["kernels", "cluster", "persistent", "persistent_mem", "mixed", "mixed_cluster"])
 @pytest.mark.parametrize("kind", ["neumann", "dirichlet"])
 def test_coarse_poisson_solve(cg, kind, mode):
     if kind == "neumann":
@@ -89,6 +89,7 @@ def test_coarse_poisson_solve(cg, kind, mode):
     m = cg.Mesh(base.xy, base.tri, base.tag, 2)
     extra = {"kernels": dict(coarse_mode=cg.CGP_COARSE_KERNELS), "cluster": dict(coarse_mode=cg.CGP_COARSE_CLUSTER),
              "persistent": dict(coarse_mode=cg.CGP_COARSE_PERSISTENT), "mixed": dict(precision=cg.CGP_MIXED),
+             "persistent_mem": dict(coarse_mode=cg.CGP_COARSE_PERSISTENT_MEM),
              "mixed_cluster": dict(precision=cg.CGP_MIXED, coarse_mode=cg.CGP_COARSE_CLUSTER)}[mode]
     s = cg.Solver(m, cg.make_params(100.0, 0.01, k=1, bc_kind=bc, bc_param=bp, guess=cg.CGP_GUESS_ZERO,
                                     **TIGHT, **extra))
@@ -129,14 +130,15 @@ def test_one_step_intermediates(cg):
     s.close(); m.close()
 
 
-@pytest.mark.parametrize("form", ["fp64", "fp64_kernels", "fp64_cluster", "mixed"])
+@pytest.mark.parametrize("form", ["fp64", "fp64_kernels", "fp64_cluster", "fp64_mem", "mixed"])
 def test_cavity64_k1_full_run(cg, form):
     # 64x64 lid-driven cavity, Re 100, pressure on 32x32, 50 steps at tolerance 1e-10:
     # FP64 within 1e-6 of the oracle, FP32-inner/FP64-outer within 1e-4 (it lands far closer)
     w = WORKLOADS["cavity64_k1"]
     base = w.base_mesh()
     extra = {"fp64": {}, "fp64_kernels": dict(coarse_mode=cg.CGP_COARSE_KERNELS),
-             "fp64_cluster": dict(coarse_mode=cg.CGP_COARSE_CLUSTER), "mixed": dict(precision=cg.CGP_MIXED)}[form]
+             "fp64_cluster": dict(coarse_mode=cg.CGP_COARSE_CLUSTER), "mixed": dict(precision=cg.CGP_MIXED),
+             "fp64_mem": dict(coarse_mode=cg.CGP_COARSE_PERSISTENT_MEM)}[form]
     m, s, o = _pair(cg, base, w.n_levels, w.k, w.Re, w.dt, w.chi, w.bc, tol_mom=w.tol_mom,
                     tol_poisson=w.tol_poisson, tol_mass=1e-12, **extra)
     s.step(w.steps)
@@ -180,7 +182,7 @@ def test_periodic_taylor_green(cg):
     s.close(); m.close()
 
 
-@pytest.mark.parametrize("mode", [1, 2, 3])
+@pytest.mark.parametrize("mode", [1, 2, 3, 4])
 def test_graph_replay_equals_eager_launches(cg, mode):
     res = []
     for g in (0, 1):
