@@ -107,14 +107,14 @@ def workload_problem(name):
     return w, w.base_mesh()
 
 
-def make_params(cg, w, form, use_graph=1):
+def make_params(cg, w, form, use_graph=1, tol_inner=0.0):
     mixed = form in ("mixed", "mixed_learned")
     learned = form in ("learned", "mixed_learned")
     return cg.make_params(w.Re, w.dt, chi=w.chi, k=w.k, tol_mom=w.tol_mom, tol_poisson=w.tol_poisson,
                           tol_mass=1e-10, max_it_mom=1000, max_it_poisson=20000, max_it_mass=1000,
                           precision=cg.CGP_MIXED if mixed else cg.CGP_FP64,
                           guess=cg.CGP_GUESS_LEARNED if learned else cg.CGP_GUESS_PREV, bc_kind=w.bc,
-                          bc_param=w.bc_param, use_graph=use_graph)
+                          bc_param=w.bc_param, use_graph=use_graph, tol_inner=tol_inner)
 
 
 def train_guess(cg, w, args):
@@ -194,7 +194,7 @@ def run_gpu(args, rank, world):
 
     def run_form(form, steps, warmup, timed=True):
         t0 = time.time()
-        s = cg.Solver(mesh, make_params(cg, w, form, args.graph))
+        s = cg.Solver(mesh, make_params(cg, w, form, args.graph, args.tol_inner))
         if form in ("learned", "mixed_learned"):
             cg.cgp_guess_set(s.handle, learned["net"])
         torch.cuda.synchronize()
@@ -215,6 +215,7 @@ def run_gpu(args, rank, world):
         ms = ev0.elapsed_time(ev1)
         U, P, t, st1, rc = s.fields()
         its = {k: (st1["sum_it_" + k] - st0["sum_it_" + k]) / steps for k in ("mom", "poisson", "corr", "mass")}
+        its["poisson_outer"] = (st1["sum_outer_poisson"] - st0["sum_outer_poisson"]) / steps
         return s, {"ms": ms, "ms_per_step": ms / steps, "steps_per_s": 1000.0 * steps / ms, "iters": its,
                    "guess_used": st1["guess_used"] - st0["guess_used"],
                    "launches": st1["launches"] - st0["launches"], "status": rc,
@@ -431,6 +432,8 @@ def main():
     ap.add_argument("--train-iters", type=int, default=400)
     ap.add_argument("--pcg-n", type=int, default=2048)
     ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--tol-inner", type=float, default=0.0,
+                    help="mixed form: residual reduction of each FP32 inner solve (0: library default)")
     ap.add_argument("--quick", action="store_true", help="skip the secondary measurements")
     ap.add_argument("--graph", type=int, default=1, choices=[0, 1],
                     help="1: replay steps as CUDA graphs; 0: eager launches (what ncu can profile)")

@@ -94,7 +94,7 @@ typedef struct {
     double bc_param[4];
     int32_t use_graph;         /* 1: replay each step as a CUDA graph with device-side loop control */
     double tol_inner;          /* CGP_MIXED: residual reduction asked of each FP32 inner solve (0 = 1e-3) */
-    int32_t coarse_mode;       /* coarse Poisson solver: CGP_COARSE_AUTO | _GRID | _CLUSTER */
+    int32_t coarse_mode;       /* coarse Poisson solver: CGP_COARSE_* */
     int32_t cluster_size;      /* CTAs of the cluster solver (0 = largest that fits, else 2..16) */
 } cgp_params;
 
@@ -103,10 +103,14 @@ typedef struct {
  * bounded software grid barrier; in FP64, when every row has at most 16 entries and the
  * mesh fits one 32-row slice per warp, each thread keeps its row and its PCG vectors in
  * registers.  PERSISTENT_MEM: the same without register residency.  CLUSTER: the whole
- * solve in one launch of one thread-block cluster, reductions through distributed shared
- * memory.  AUTO = PERSISTENT.  CGP_MIXED needs PERSISTENT(_MEM) or CLUSTER. */
+ * solve in one launch of one thread-block cluster, vectors in global memory, reductions
+ * through distributed shared memory.  ONCHIP (CGP_MIXED only): the FP32 inner solve on one
+ * cluster of 8 or 16 CTAs with the FP32 matrix and the vectors held in distributed shared
+ * memory and hardware cluster barriers (cgp_assemble fails with CGP_EINVAL if the coarse
+ * system does not fit).  AUTO: ONCHIP for CGP_MIXED when it fits, else PERSISTENT.
+ * CGP_MIXED needs a one-launch kind (not KERNELS). */
 enum { CGP_COARSE_AUTO = 0, CGP_COARSE_KERNELS = 1, CGP_COARSE_CLUSTER = 2, CGP_COARSE_PERSISTENT = 3,
-       CGP_COARSE_PERSISTENT_MEM = 4 };
+       CGP_COARSE_PERSISTENT_MEM = 4, CGP_COARSE_ONCHIP = 5 };
 
 /* Per-run statistics. */
 typedef struct {
@@ -118,6 +122,8 @@ typedef struct {
     int32_t status;            /* first non-zero CGP_E* code seen by any solve, else 0 */
     int64_t launches;          /* kernel launches of graph-replayed steps (Krylov loop trips included) */
     int64_t guess_used;        /* steps whose coarse solve started from the learned prediction */
+    int64_t sum_outer_poisson; /* FP64 residual sweeps (refinement steps) of the one-launch coarse
+                                  solves, summed over steps; 0 for CGP_COARSE_KERNELS */
 } cgp_stats;
 
 /* Library message for the last failing call of this thread ("" if none). */
@@ -182,6 +188,11 @@ enum { CGP_MAT_M = 0, CGP_MAT_K = 1, CGP_MAT_CX = 2, CGP_MAT_CY = 3,      /* vel
 int cgp_get_matrix(cgp_solver* s, int32_t which, double* vals, int32_t where, cgp_stream_t stream);
 /* Sizes: fine/coarse vertex counts and the CSR entry counts of both levels. */
 int cgp_solver_info(const cgp_solver* s, int32_t* n_fine, int32_t* n_coarse, int64_t* nnz_fine, int64_t* nnz_coarse);
+/* The coarse Poisson solver cgp_assemble picked: *kind = the CGP_COARSE_* kind that runs
+ * (never AUTO; PERSISTENT_MEM when the persistent solve keeps its vectors in memory),
+ * *ctas = CTAs of its launch (0 for KERNELS), *cluster = CTAs per cluster (0 if none).
+ * Any output pointer may be NULL.  CGP_EINVAL before cgp_assemble. */
+int cgp_coarse_info(const cgp_solver* s, int32_t* kind, int32_t* ctas, int32_t* cluster);
 
 /* Eq. 23 alone: solve K_c phi = rhs (N_c values; phi=0 rows and the pure-Neumann
  * projection/mean fix as in a step) with the configured precision and tolerance.

@@ -21,7 +21,8 @@ CGP_BC_CAVITY, CGP_BC_CHANNEL, CGP_BC_TG, CGP_BC_TG_PERIODIC = 0, 1, 2, 3
 CGP_FP64, CGP_MIXED = 0, 1
 CGP_GUESS_ZERO, CGP_GUESS_PREV, CGP_GUESS_LEARNED = 0, 1, 2
 CGP_MASS_CONSISTENT, CGP_MASS_LUMPED = 0, 1
-CGP_COARSE_AUTO, CGP_COARSE_KERNELS, CGP_COARSE_CLUSTER, CGP_COARSE_PERSISTENT, CGP_COARSE_PERSISTENT_MEM = 0, 1, 2, 3, 4
+(CGP_COARSE_AUTO, CGP_COARSE_KERNELS, CGP_COARSE_CLUSTER, CGP_COARSE_PERSISTENT, CGP_COARSE_PERSISTENT_MEM,
+ CGP_COARSE_ONCHIP) = 0, 1, 2, 3, 4, 5
 CGP_HOST, CGP_DEVICE = 0, 1
 (CGP_VEC_U, CGP_VEC_UPREV, CGP_VEC_P, CGP_VEC_UTILDE, CGP_VEC_RHS_C, CGP_VEC_PHI_C,
  CGP_VEC_PHI_F) = range(7)
@@ -57,7 +58,7 @@ class Stats(ctypes.Structure):
                 ("it_corr", c_int32), ("it_mass", c_int32), ("sum_it_mom", c_int64),
                 ("sum_it_poisson", c_int64), ("sum_it_corr", c_int64), ("sum_it_mass", c_int64),
                 ("res_mom", c_double), ("res_poisson", c_double), ("status", c_int32), ("launches", c_int64),
-                ("guess_used", c_int64)]
+                ("guess_used", c_int64), ("sum_outer_poisson", c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -81,6 +82,7 @@ _SIGS = {
     "cgp_get_matrix": (c_int32, [c_void_p, c_int32, c_void_p, c_int32, c_void_p]),
     "cgp_solver_info": (c_int32, [c_void_p, POINTER(c_int32), POINTER(c_int32), POINTER(c_int64),
                                   POINTER(c_int64)]),
+    "cgp_coarse_info": (c_int32, [c_void_p, POINTER(c_int32), POINTER(c_int32), POINTER(c_int32)]),
     "cgp_poisson_solve": (c_int32, [c_void_p, c_void_p, c_void_p, POINTER(c_int32), c_int32, c_void_p]),
     "cgp_prolong": (c_int32, [c_void_p, c_void_p, c_void_p, c_int32, c_void_p]),
     "cgp_profile_step": (c_int32, [c_void_p, c_void_p, c_int32, c_void_p, c_void_p]),
@@ -253,6 +255,13 @@ def cgp_get_fields(solver, U=None, P=None, where=CGP_HOST, stream=None, allow=(C
         _check(rc)
     _check(rc, allow=allow)
     return U, P, t.value, st.as_dict(), rc
+
+
+def cgp_coarse_info(solver):
+    """(kind, ctas, cluster) of the coarse Poisson solver that runs."""
+    k, n, c = c_int32(), c_int32(), c_int32()
+    _check(load().cgp_coarse_info(solver, byref(k), byref(n), byref(c)))
+    return k.value, n.value, c.value
 
 
 def cgp_solver_info(solver):
@@ -446,6 +455,9 @@ class Solver:
 
     def vector(self, which):
         return cgp_get_vector(self.handle, which)
+
+    def coarse_info(self):
+        return cgp_coarse_info(self.handle)
 
     def matrix(self, which):
         return cgp_get_matrix(self.handle, which)

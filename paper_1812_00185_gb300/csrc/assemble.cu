@@ -166,6 +166,16 @@ static int layout(Solver& s, void* base, size_t* bytes) {
         s.mlp.carve(cv, (int)nc, 1);
     }
     s.cw32 = cv.take<float>(9 * nc);
+    if (s.prm.precision == CGP_MIXED) {
+        s.oc_slist = cv.take<int32_t>(C.nslices);
+        s.oc_ebase = cv.take<int32_t>(C.nslices);
+        s.oc_soff = cv.take<int32_t>(kOnchipMaxCluster + 1);
+        s.oc_send_off = cv.take<int32_t>(kOnchipMaxCluster + 1);
+        s.oc_li = cv.take<int32_t>(nnzc);
+        s.oc_src = cv.take<int32_t>(nnzc);
+        s.oc_send_lr = cv.take<int32_t>(nnzc);     // sends <= entries with a remote column
+        s.oc_send_dst = cv.take<int32_t>(nnzc);
+    }
     s.csr_tmp = cv.take<double>(F.nnz > C.nnz ? F.nnz : C.nnz);
     s.val_begin = s.M;
     s.val_end = s.geo;
@@ -202,7 +212,7 @@ static int check_params(const cgp_mesh* m, const cgp_params* p) {
         p->max_it_poisson < 1 || p->max_it_mass < 1 || p->bc_kind < 0 || p->bc_kind > CGP_BC_TG_PERIODIC ||
         (p->precision != CGP_FP64 && p->precision != CGP_MIXED) || p->guess < 0 || p->guess > 2 ||
         (p->mass_mode != CGP_MASS_CONSISTENT && p->mass_mode != CGP_MASS_LUMPED) || p->coarse_mode < 0 ||
-        p->coarse_mode > CGP_COARSE_PERSISTENT_MEM || p->cluster_size < 0 || p->cluster_size > 16 || p->tol_inner < 0 ||
+        p->coarse_mode > CGP_COARSE_ONCHIP || p->cluster_size < 0 || p->cluster_size > 16 || p->tol_inner < 0 ||
         p->tol_inner >= 1) {
         set_error("invalid cgp_params");
         return CGP_EINVAL;

@@ -1,0 +1,428 @@
+// On-chip mixed-precision coarse solve (Eq. 23): one thread-block cluster holds the whole
+// FP32 inner problem in distributed shared memory.
+//
+// The coarse systems of CGP are small (tens of thousands of rows), and on this GPU the FP64
+// pipe is narrow while a cluster barrier is far cheaper than a grid-wide one, so the FP32
+// inner PCG of the mixed form runs on a single cluster of 8 or 16 CTAs.  A host-side plan
+// (onchip_plan.cu) gives each CTA a spatially compact set of SELL-32 slices.  Each CTA keeps
+// in its shared memory:
+//   * z for its own rows followed by a halo: z of the other CTAs' rows that its rows use;
+//   * its slices of the FP32 matrix, each entry's column as the shared address of that z;
+//   * a send list: after z changes, every CTA stores the z its neighbours need straight
+//     into their halos (remote shared-memory stores), before the barrier of the reduction
+//     that follows, so every gather of the SpMV is a local shared-memory load;
+//   * the slots of the cluster reductions: every CTA stores its partial sums into every
+//     other CTA's slot array, then one hardware cluster barrier makes them visible and each
+//     CTA adds the slots in the same fixed order (identical scalars everywhere).
+// The inner iteration is classical PCG with the SpMV applied to z: w = A z, p = z + beta p,
+// q = w + beta q (= A p), so z is the only vector that travels; the other vectors (e, r, z,
+// p, q, D^{-1}) live in registers.  Two reductions per iteration (<p, q>, then <r, z> and
+// <r, r>), all in FP32 on the residual scaled to unit norm, so the inner scalars stay well
+// inside the FP32 range.  The FP64 outer loop (true residual, its norm, the convergence
+// test, x += ||r|| e) reads the FP64 matrix and x from global memory a few times per solve;
+// only warp 0 of each CTA does its FP64 scalar work.
+#pragma once
+
+#include <cooperative_groups.h>
+
+#include "coarse_pcg.cuh"
+#include "onchip_plan.cuh"
+
+namespace cgp {
+
+// ---- shared::cluster access
+__device__ __forceinline__ uint32_t oc_map(const void* p, int rank) {
+    const uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
+    return r;
+}
+__device__ __forceinline__ void oc_st(uint32_t addr, double v) {
+    asm volatile("st.shared::cluster.f64 [%0], %1;" ::"r"(addr), "d"(v) : "memory");
+}
+__device__ __forceinline__ void oc_st32(uint32_t addr, float v) {
+    asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(addr), "f"(v) : "memory");
+}
+__device__ __forceinline__ float oc_lds(uint32_t addr) {
+    float v;
+    asm volatile("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(addr) : "memory");
+    return v;
+}
+// all threads of all CTAs of the cluster; orders shared and global memory at cluster scope
+__device__ __forceinline__ void oc_barrier() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+__device__ __forceinline__ float warp_sum_f(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// what warp 0 tells its CTA after an FP64 reduction
+struct OnchipScalars {
+    int act;
+    float rz0, stop2;          // scaled inner problem: <r, z> and the stop threshold on <r, r>
+    double inv, norm, mu;      // 1 / ||r||, ||r|| of the outer residual; mean of the Neumann fix
+};
+
+static __global__ void __launch_bounds__(kOnchipThreads, 1) k_pcg_onchip(CoarsePcgArgs a, OnchipPlan pl) {
+    namespace cg = cooperative_groups;
+    cg::cluster_group cluster = cg::this_cluster();
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ double wsum[kOnchipThreads / 32][4];
+    __shared__ float wsum32[kOnchipThreads / 32][4];
+    __shared__ OnchipScalars sc;
+    const int rank = (int)cluster.block_rank(), ncl = (int)cluster.num_blocks();
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const SellView& A = a.A;
+    const int rows_max = pl.rows_max, zn = rows_max + pl.halo_max;
+    float* zl = reinterpret_cast<float*>(smem);
+    double* red64 = reinterpret_cast<double*>(smem + onchip_z_bytes(rows_max, pl.halo_max));
+    float* red32 = reinterpret_cast<float*>(red64 + 128);
+    uint2* send = reinterpret_cast<uint2*>(red32 + 128);
+    uint32_t* caddr = reinterpret_cast<uint32_t*>(send + pl.send_max);
+    const int q0 = __ldg(pl.soff + rank), nsl = __ldg(pl.soff + rank + 1) - q0;
+    const int eb0 = nsl > 0 ? __ldg(pl.ebase + q0) : 0;
+    float* cval = reinterpret_cast<float*>(caddr + pl.ent_max);
+    const uint32_t z_sh = (uint32_t)__cvta_generic_to_shared(zl);
+    for (int i = threadIdx.x; i < zn; i += blockDim.x) zl[i] = 0.0f;
+    // ---- rows of this thread: list positions wid + nw * t of its CTA (a warp owns whole
+    // slices); their matrix entries are copied to shared memory by the owning warp
+    int nrow = 0;
+    int base_[kOnchipRows], width_[kOnchipRows], slice_[kOnchipRows];
+#pragma unroll
+    for (int t = 0; t < kOnchipRows; ++t) {
+        const int q = wid + nw * t;
+        base_[t] = 0;
+        width_[t] = 0;
+        slice_[t] = -1;
+        if (q < nsl) {
+            nrow = t + 1;
+            const int sl = __ldg(pl.slist + q0 + q);
+            slice_[t] = sl;
+            base_[t] = __ldg(pl.ebase + q0 + q) - eb0;
+            width_[t] = (__ldg(A.ptr + sl + 1) - __ldg(A.ptr + sl)) >> 5;
+            for (int k = 0; k < width_[t]; ++k) {
+                const int el = base_[t] + 32 * k + lane;
+                caddr[el] = z_sh + 4u * (uint32_t)__ldg(pl.li + eb0 + el);
+                cval[el] = __ldg(a.valf + __ldg(pl.src + eb0 + el));
+            }
+        }
+    }
+    auto row_of = [&](int t) {   // global row of slot t, or -1
+        const int i = 32 * slice_[t] + lane;
+        return (slice_[t] >= 0 && i < A.n) ? i : -1;
+    };
+    auto lrow_of = [&](int t) { return 32 * (wid + nw * t) + lane; };
+    const int ns0 = __ldg(pl.send_off + rank), nsend = __ldg(pl.send_off + rank + 1) - ns0;
+    for (int i = threadIdx.x; i < nsend; i += blockDim.x) {
+        const int d = __ldg(pl.send_dst + ns0 + i);
+        send[i] = make_uint2((uint32_t)__ldg(pl.send_lr + ns0 + i), oc_map(zl + rows_max + (d & 0xFFFF), d >> 16));
+    }
+    // remote slot addresses of the reductions: lane l < ncl stores into CTA l
+    const uint32_t red64_remote = oc_map(red64, lane < ncl ? lane : 0);
+    const uint32_t red32_remote = oc_map(red32, lane < ncl ? lane : 0);
+    // z of the own rows to the neighbours' halos (after a __syncthreads, before a barrier)
+    auto push = [&]() {
+        for (int i = threadIdx.x; i < nsend; i += blockDim.x) {
+            const uint2 sd = send[i];
+            oc_st32(sd.y, zl[sd.x]);
+        }
+    };
+    // Cluster sums.  Partial sums go warp -> CTA (warp 0) -> every CTA's slot array, one
+    // hardware cluster barrier, then the ncl slots are added; all in a fixed order, so every
+    // CTA gets the same totals.  Consecutive reductions alternate between two slot sets, so a
+    // slot is rewritten only after the barrier that follows every read of it.
+    int slot = 0;
+    // FP64: totals in every lane of warp 0, which alone does the FP64 scalar work (the FP64
+    // pipe is narrow) and hands results to the CTA through `sc` and a __syncthreads.
+    auto cred64 = [&](auto& v, double (&tot)[4]) {
+        constexpr int NR = sizeof(v) / sizeof(double);
+#pragma unroll
+        for (int k = 0; k < NR; ++k) {
+            const double s = warp_sum(v[k]);
+            if (lane == 0) wsum[wid][k] = s;
+        }
+        __syncthreads();
+        if (wid == 0) {
+#pragma unroll
+            for (int k = 0; k < NR; ++k) {
+                const double s = __shfl_sync(0xffffffffu, warp_sum(lane < nw ? wsum[lane][k] : 0.0), 0);
+                if (lane < ncl) oc_st(red64_remote + (uint32_t)(8 * ((slot * 16 + rank) * 4 + k)), s);
+            }
+        }
+        oc_barrier();
+        if (wid == 0) {
+#pragma unroll
+            for (int k = 0; k < NR; ++k)
+                tot[k] = __shfl_sync(0xffffffffu, warp_sum(lane < ncl ? red64[(slot * 16 + lane) * 4 + k] : 0.0), 0);
+        }
+        slot ^= 1;
+    };
+    // FP32 (inner iterations): totals in every thread, each warp adding the slots itself;
+    // with `publish`, the CTA's new z also goes to the neighbours' halos before the barrier
+    auto cred32 = [&](float (&v)[2], int nr, float (&tot)[2], bool publish) {
+        for (int k = 0; k < nr; ++k) {
+            const float s = warp_sum_f(v[k]);
+            if (lane == 0) wsum32[wid][k] = s;
+        }
+        __syncthreads();
+        if (publish) push();
+        if (wid == 0) {
+            for (int k = 0; k < nr; ++k) {
+                const float s = __shfl_sync(0xffffffffu, warp_sum_f(lane < nw ? wsum32[lane][k] : 0.0f), 0);
+                if (lane < ncl) oc_st32(red32_remote + (uint32_t)(4 * ((slot * 16 + rank) * 4 + k)), s);
+            }
+        }
+        oc_barrier();
+        for (int k = 0; k < nr; ++k)
+            tot[k] = __shfl_sync(0xffffffffu, warp_sum_f(lane < ncl ? red32[(slot * 16 + lane) * 4 + k] : 0.0f), 0);
+        slot ^= 1;
+    };
+    const double mean = a.project ? a.st->mean : 0.0;
+    const double tol2 = a.tol2;
+    double* xv = a.x;
+    float e_[kOnchipRows], r_[kOnchipRows], z_[kOnchipRows], p_[kOnchipRows], q_[kOnchipRows], d_[kOnchipRows];
+#pragma unroll
+    for (int t = 0; t < kOnchipRows; ++t) {
+        e_[t] = r_[t] = z_[t] = p_[t] = q_[t] = d_[t] = 0.0f;
+        const int i = row_of(t);
+        if (i >= 0) {
+            d_[t] = __ldg(a.dinvf + i);
+            if (a.project) a.b[i] -= mean;
+            if (a.zero_x) __stcg(xv + i, 0.0);
+        }
+    }
+    oc_barrier();   // matrix and sends loaded, z zeroed, b projected and x zeroed where asked
+    // FP64 row of A times a global vector (`ro`: v is read-only during the launch)
+    auto row_a = [&](int t, const double* v, bool ro) {
+        double ax[1] = {0.0};
+        if (ro)
+            sell_accum<1>(A, a.val, slice_[t], lane, [&](int j, double (&o)[1]) { o[0] = __ldg(v + j); }, ax);
+        else
+            sell_accum<1>(A, a.val, slice_[t], lane, [&](int j, double (&o)[1]) { o[0] = ldcg(v + j); }, ax);
+        return ax[0];
+    };
+    int iters = 0, status = 0, outer = 0, used_alt = 0;
+    bool converged = false;
+    double tot[4];
+    if (a.x_alt && !a.zero_x) {
+        double acc[2] = {0.0, 0.0};
+#pragma unroll
+        for (int t = 0; t < kOnchipRows; ++t) {
+            if (t >= nrow) break;
+            const double ax = row_a(t, xv, false), aa = row_a(t, a.x_alt, true);
+            const int i = row_of(t);
+            if (i >= 0) {
+                const double bi = ldcg(a.b + i);
+                acc[0] += (bi - ax) * (bi - ax);
+                acc[1] += (bi - aa) * (bi - aa);
+            }
+        }
+        cred64(acc, tot);
+        if (threadIdx.x == 0) sc.act = tot[1] < tot[0];
+        __syncthreads();
+        if (sc.act) {
+            used_alt = 1;
+#pragma unroll
+            for (int t = 0; t < kOnchipRows; ++t) {
+                const int i = row_of(t);
+                if (i >= 0) __stcg(xv + i, __ldg(a.x_alt + i));
+            }
+            oc_barrier();
+        }
+    }
+    double bb = 0.0, rr_final = 0.0;   // meaningful in warp 0
+    enum { kInner = 0, kConverged, kNonfinite, kNotconv };
+    for (;;) {
+        // ---- outer: r = b - A x in FP64 (global memory); the inner problem A e = r / ||r||
+        double acc[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+        for (int t = 0; t < kOnchipRows; ++t) {
+            if (t >= nrow) break;
+            const double ax = row_a(t, xv, false);
+            const int i = row_of(t);
+            if (i >= 0) {
+                const double bi = ldcg(a.b + i);
+                const double ri = bi - ax;
+                r_[t] = (float)ri;
+                acc[0] += ri * ri;
+                acc[1] += bi * bi;
+                acc[2] += ri * ri * (double)d_[t];
+            }
+        }
+        cred64(acc, tot);
+        if (wid == 0) {
+            if (outer == 0) bb = tot[1];
+            rr_final = tot[0];
+            int act = kInner;
+            if (!isfinite(tot[0])) act = kNonfinite;
+            else if (tot[0] <= tol2 * bb) act = kConverged;
+            else if (outer >= a.max_outer || iters >= a.maxit) act = kNotconv;
+            if (lane == 0) {
+                sc.act = act;
+                if (act == kInner) {
+                    sc.norm = sqrt(tot[0]);
+                    sc.inv = 1.0 / sc.norm;
+                    sc.rz0 = (float)(tot[2] / tot[0]);
+                    sc.stop2 = (float)fmax(a.inner_tol * a.inner_tol, 0.25 * tol2 * bb / tot[0]);
+                }
+            }
+        }
+        __syncthreads();
+        {
+            const int act = sc.act;
+            if (act == kNonfinite) {
+                status = CGP_ENONFINITE;
+                break;
+            }
+            if (act == kConverged) {
+                converged = true;
+                break;
+            }
+            if (act == kNotconv) {
+                status = CGP_ENOTCONV;
+                break;
+            }
+        }
+        const float inv = (float)sc.inv;
+#pragma unroll
+        for (int t = 0; t < kOnchipRows; ++t) {
+            if (row_of(t) >= 0) {
+                r_[t] *= inv;
+                z_[t] = d_[t] * r_[t];
+                e_[t] = 0.0f;
+                p_[t] = 0.0f;
+                q_[t] = 0.0f;
+                zl[lrow_of(t)] = z_[t];
+            }
+        }
+        __syncthreads();
+        push();
+        oc_barrier();   // the first z in every halo
+        // ---- inner classical PCG in FP32 on the scaled residual; every warp carries the same
+        // scalars (rz, beta, rr_best), computed from the same totals
+        float rz = sc.rz0, beta = 0.0f, rr_best = INFINITY;
+        const float stop2 = sc.stop2;
+        int best_k = 0;
+        bool drift = false;
+        for (int k = 0; iters < a.maxit; ++k) {
+            // phase A: w = A z (local gathers), p = z + beta p, q = w + beta q, <p, q>
+            const float be = beta;
+            float pq_acc[2] = {0.0f, 0.0f};
+#pragma unroll
+            for (int t = 0; t < kOnchipRows; ++t) {
+                if (t >= nrow) break;
+                const int b = base_[t] + lane, w = width_[t];
+                float s = 0.0f;
+                for (int k0 = 0; k0 < w; k0 += 8) {
+                    uint32_t ad[8];
+                    float v[8];
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) {
+                        const bool in = k0 + u < w;
+                        ad[u] = in ? caddr[b + 32 * (k0 + u)] : z_sh;
+                        v[u] = in ? cval[b + 32 * (k0 + u)] : 0.0f;
+                    }
+                    float g[8];
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) g[u] = oc_lds(ad[u]);
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) s = fmaf(v[u], g[u], s);
+                }
+                if (row_of(t) >= 0) {
+                    p_[t] = fmaf(be, p_[t], z_[t]);
+                    q_[t] = fmaf(be, q_[t], s);
+                    pq_acc[0] = fmaf(p_[t], q_[t], pq_acc[0]);
+                }
+            }
+            float pq[2];
+            cred32(pq_acc, 1, pq, false);
+            if (!(pq[0] != 0.0f) || !isfinite(pq[0])) break;   // restart from the true residual
+            const float al = rz / pq[0];
+            // phase B (own rows): e += alpha p, r -= alpha q, z = D^{-1} r
+            float acc2[2] = {0.0f, 0.0f};
+#pragma unroll
+            for (int t = 0; t < kOnchipRows; ++t) {
+                if (row_of(t) >= 0) {
+                    e_[t] = fmaf(al, p_[t], e_[t]);
+                    r_[t] = fmaf(-al, q_[t], r_[t]);
+                    z_[t] = d_[t] * r_[t];
+                    zl[lrow_of(t)] = z_[t];
+                    acc2[0] = fmaf(r_[t], z_[t], acc2[0]);
+                    acc2[1] = fmaf(r_[t], r_[t], acc2[1]);
+                }
+            }
+            float t2[2];
+            cred32(acc2, 2, t2, true);
+            ++iters;
+            if (!isfinite(t2[0]) || !isfinite(t2[1])) {
+                drift = true;
+                break;
+            }
+            if (t2[1] <= stop2 || t2[0] == 0.0f || t2[1] == 0.0f) break;
+            beta = t2[0] / rz;
+            rz = t2[0];
+            if (t2[1] < 0.5f * rr_best) {
+                rr_best = t2[1];
+                best_k = k;
+            } else if (t2[1] > 1e4f * rr_best) {
+                drift = true;
+                break;
+            } else if (k - best_k > kStagnation32) {
+                break;
+            }
+        }
+        // ---- x += ||r|| e (FP64) unless the FP32 recurrence drifted away
+        if (!drift) {
+            const double norm = sc.norm;
+#pragma unroll
+            for (int t = 0; t < kOnchipRows; ++t) {
+                const int i = row_of(t);
+                if (i >= 0) __stcg(xv + i, ldcg(xv + i) + norm * (double)e_[t]);
+            }
+        }
+        oc_barrier();
+        ++outer;
+        if (drift && outer > 2) {
+            status = CGP_ENONFINITE;   // the FP32 solve keeps failing: let the caller see it
+            break;
+        }
+    }
+    // ---- pure-Neumann mean fix
+    if (a.mlump) {
+        double acc[2] = {0.0, 0.0};
+#pragma unroll
+        for (int t = 0; t < kOnchipRows; ++t) {
+            const int i = row_of(t);
+            if (i >= 0) {
+                acc[0] += __ldg(a.mlump + i) * ldcg(xv + i);
+                acc[1] += __ldg(a.mlump + i);
+            }
+        }
+        cred64(acc, tot);
+        if (threadIdx.x == 0) sc.mu = tot[0] / tot[1];
+        __syncthreads();
+        const double mu = sc.mu;
+#pragma unroll
+        for (int t = 0; t < kOnchipRows; ++t) {
+            const int i = row_of(t);
+            if (i >= 0) __stcg(xv + i, ldcg(xv + i) - mu);
+        }
+    }
+    if (rank == 0 && threadIdx.x == 0) {
+        KrylovState* st = a.st;
+        st->iter = iters;
+        st->bb[0] = bb;
+        st->rr[0] = rr_final;
+        st->bb[1] = 0.0;
+        st->rr[1] = 0.0;
+        st->status = status ? status : (converged ? 0 : CGP_ENOTCONV);
+        st->done = 1;
+        st->pad[0] = outer;
+        st->pad[1] = used_alt;
+    }
+    oc_barrier();   // no CTA leaves while another may still access its shared memory
+}
+
+}  // namespace cgp

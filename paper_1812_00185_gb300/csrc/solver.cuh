@@ -4,6 +4,7 @@
 
 #include "krylov.cuh"
 #include "mlp.cuh"
+#include "onchip_plan.cuh"
 
 namespace cgp {
 
@@ -27,6 +28,7 @@ struct DeviceStats {
     int64_t steps;
     int64_t launches;             // kernels launched by graph-replayed steps (loop trips included)
     int64_t guess_used;           // steps that started the coarse solve from the learned prediction
+    int64_t sum_outer;            // FP64 residual sweeps of the one-launch coarse solves
     int64_t sum_it[KS_COUNT];
     int32_t last_it[KS_COUNT];
     int32_t status;
@@ -63,6 +65,11 @@ struct Solver {
     int cluster_size = 0;         // CTAs of the one-cluster solver
     int coarse_grid = 0;          // CTAs of the persistent (cooperative) solver
     bool coarse_rr = false;       // the persistent FP64 solve may keep its rows in registers
+    size_t onchip_bytes = 0;      // mixed: shared memory per CTA of the on-chip cluster solve (0 = not used)
+    // mixed: workspace arrays of the on-chip plan (sized for the coarse level) and its device view
+    int32_t *oc_slist = nullptr, *oc_soff = nullptr, *oc_ebase = nullptr, *oc_li = nullptr, *oc_src = nullptr;
+    int32_t *oc_send_lr = nullptr, *oc_send_dst = nullptr, *oc_send_off = nullptr;
+    OnchipPlan onchip{};
     unsigned int* bar_count = nullptr;   // grid barrier counter, followed by the error word
     int* bar_err = nullptr;
     double* coarse_partials = nullptr;   // 2 x max_grid x 4

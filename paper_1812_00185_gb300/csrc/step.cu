@@ -6,6 +6,7 @@
 
 #include "coarse_pcg.cuh"
 #include "coarse_rr.cuh"
+#include "coarse_onchip.cuh"
 #include "flows.cuh"
 #include "solver.cuh"
 
@@ -241,6 +242,7 @@ __global__ void k_finish(int nf, double* __restrict__ U, double* __restrict__ Up
             if (k != KS_POIS || pois_loop) l += 4 * (int64_t)((ks[k].iter + 1) / 2);
         stats->launches += l;
         if (ks[KS_POIS].pad[1]) stats->guess_used += 1;
+        stats->sum_outer += ks[KS_POIS].pad[0];
         for (int k = 0; k < KS_COUNT; ++k) {
             stats->last_it[k] = ks[k].iter;
             stats->sum_it[k] += ks[k].iter;
@@ -260,6 +262,8 @@ __global__ void k_ks_setup(KrylovState* st, double tol2, int maxit) {
     st->iter = 0;
     st->done = 0;
     st->status = 0;
+    st->pad[0] = 0;
+    st->pad[1] = 0;
 }
 
 // ---------------------------------------------------------------- loop control
@@ -419,7 +423,13 @@ static cudaLaunchConfig_t cluster_config(int csize, cudaStream_t st, cudaLaunchA
 int choose_coarse_solver(Solver& s) {
     const cgp_params& p = s.prm;
     int mode = p.coarse_mode;
-    if (mode == CGP_COARSE_AUTO) mode = CGP_COARSE_PERSISTENT;
+    if (mode == CGP_COARSE_ONCHIP && p.precision != CGP_MIXED) {
+        set_error("CGP_COARSE_ONCHIP is the FP32 inner solve of CGP_MIXED");
+        return CGP_EINVAL;
+    }
+    // the on-chip cluster solve when asked for, or by default for the mixed form if it fits
+    const bool want_onchip = p.precision == CGP_MIXED && (mode == CGP_COARSE_ONCHIP || mode == CGP_COARSE_AUTO);
+    if (mode == CGP_COARSE_AUTO || mode == CGP_COARSE_ONCHIP) mode = CGP_COARSE_PERSISTENT;
     const bool allow_rr = mode == CGP_COARSE_PERSISTENT;
     if (mode == CGP_COARSE_PERSISTENT_MEM) mode = CGP_COARSE_PERSISTENT;
     s.coarse_kind = mode;
@@ -449,6 +459,55 @@ int choose_coarse_solver(Solver& s) {
         const int cap = sms * (per_sm < 2 ? per_sm : 2);
         s.coarse_grid = need < cap ? need : cap;
         if (s.coarse_grid < 1) s.coarse_grid = 1;
+        // mixed precision: the whole FP32 inner solve on one cluster, if it fits on chip
+        s.onchip_bytes = 0;
+        if (want_onchip && s.oc_li) {
+            std::vector<int32_t> ptr(C.nslices + 1), col(C.nnz_sell);
+            std::vector<double> xy(2 * (size_t)C.nv);
+            CGP_CUDA(cudaMemcpy(ptr.data(), C.sell_ptr, sizeof(int32_t) * (C.nslices + 1), cudaMemcpyDeviceToHost));
+            CGP_CUDA(cudaMemcpy(col.data(), C.sell_col, sizeof(int32_t) * C.nnz_sell, cudaMemcpyDeviceToHost));
+            CGP_CUDA(cudaMemcpy(xy.data(), C.xy, sizeof(double) * 2 * C.nv, cudaMemcpyDeviceToHost));
+            int optin = 0;
+            CGP_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+            const size_t limit = (size_t)optin - 2048;   // static shared memory of the kernel
+            CGP_CUDA(cudaFuncSetAttribute(k_pcg_onchip, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+            CGP_CUDA(cudaFuncSetAttribute(k_pcg_onchip, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)limit));
+            for (int cs : {16, 8}) {
+                OnchipHostPlan P;
+                if (!onchip_plan(C.nv, ptr, col, xy, cs, limit, P)) continue;
+                cudaLaunchAttribute attr[1];
+                cudaLaunchConfig_t cfg = cluster_config(cs, nullptr, attr);
+                cfg.blockDim = dim3(kOnchipThreads, 1, 1);
+                cfg.dynamicSmemBytes = P.bytes;
+                int n = 0;
+                if (cudaOccupancyMaxActiveClusters(&n, k_pcg_onchip, &cfg) != cudaSuccess || n < 1) {
+                    cudaGetLastError();
+                    continue;
+                }
+                auto up = [](int32_t* dst, const std::vector<int32_t>& v) {
+                    return v.empty() ? cudaSuccess
+                                     : cudaMemcpy(dst, v.data(), sizeof(int32_t) * v.size(), cudaMemcpyHostToDevice);
+                };
+                CGP_CUDA(up(s.oc_slist, P.slist));
+                CGP_CUDA(up(s.oc_soff, P.soff));
+                CGP_CUDA(up(s.oc_ebase, P.ebase));
+                CGP_CUDA(up(s.oc_li, P.li));
+                CGP_CUDA(up(s.oc_src, P.src));
+                CGP_CUDA(up(s.oc_send_lr, P.send_lr));
+                CGP_CUDA(up(s.oc_send_dst, P.send_dst));
+                CGP_CUDA(up(s.oc_send_off, P.send_off));
+                s.onchip = OnchipPlan{s.oc_slist, s.oc_soff, s.oc_ebase, s.oc_li, s.oc_src, s.oc_send_lr,
+                                      s.oc_send_dst, s.oc_send_off, P.rows_max, P.halo_max, P.send_max,
+                                      (int)P.ent_max};
+                s.onchip_bytes = P.bytes;
+                s.cluster_size = cs;
+                break;
+            }
+            if (p.coarse_mode == CGP_COARSE_ONCHIP && !s.onchip_bytes) {
+                set_error("the coarse system does not fit on one thread-block cluster");
+                return CGP_EINVAL;
+            }
+        }
         // register-resident variant: every slice no wider than kRRWidth and one slice per warp
         s.coarse_rr = false;
         if (allow_rr) {
@@ -533,6 +592,14 @@ static int coarse_solve(Ctx& c) {
             cudaLaunchAttribute attr[1];
             cudaLaunchConfig_t cfg = cluster_config(s.cluster_size, c.st, attr);
             PL(c, CGP_PROF_POIS_CLUSTER, CGP_CUDA(cudaLaunchKernelEx(&cfg, k_pcg_cluster, a)));
+            return CGP_OK;
+        }
+        if (s.onchip_bytes) {
+            cudaLaunchAttribute attr[1];
+            cudaLaunchConfig_t cfg = cluster_config(s.cluster_size, c.st, attr);
+            cfg.blockDim = dim3(kOnchipThreads, 1, 1);
+            cfg.dynamicSmemBytes = s.onchip_bytes;
+            PL(c, CGP_PROF_POIS_CLUSTER, CGP_CUDA(cudaLaunchKernelEx(&cfg, k_pcg_onchip, a, s.onchip)));
             return CGP_OK;
         }
         CGP_CUDA(cudaMemsetAsync(s.bar_count, 0, 2 * sizeof(unsigned int), c.st));   // counter + error word
@@ -788,6 +855,7 @@ extern "C" int cgp_get_fields(cgp_solver* h, double* U, double* P, double* t, cg
         stats->steps = ds.steps;
         stats->launches = ds.launches;
         stats->guess_used = ds.guess_used;
+        stats->sum_outer_poisson = ds.sum_outer;
         stats->t = th;
         stats->it_mom = ds.last_it[KS_MOM];
         stats->it_poisson = ds.last_it[KS_POIS];
@@ -904,6 +972,32 @@ extern "C" int cgp_set_vector(cgp_solver* h, int32_t which, const double* in, in
     cudaStream_t st = (cudaStream_t)stream;
     CGP_TRY(copy_in(dst, in, n * sizeof(double), where, st));
     if (where == CGP_HOST) CGP_CUDA(cudaStreamSynchronize(st));
+    return CGP_OK;
+}
+
+extern "C" int cgp_coarse_info(const cgp_solver* h, int32_t* kind, int32_t* ctas, int32_t* cluster) {
+    if (!h) {
+        set_error("null solver");
+        return CGP_EINVAL;
+    }
+    const Solver& s = h->s;
+    int k = s.coarse_kind, n = 0, cl = 0;
+    if (k == CGP_COARSE_CLUSTER) {
+        n = cl = s.cluster_size;
+    } else if (k == CGP_COARSE_PERSISTENT) {
+        if (s.onchip_bytes) {
+            k = CGP_COARSE_ONCHIP;
+            n = cl = s.cluster_size;
+        } else if (s.coarse_rr && s.prm.precision == CGP_FP64) {
+            n = rr_ctas_needed(s.mesh->lev[s.lc].nslices);
+        } else {
+            k = CGP_COARSE_PERSISTENT_MEM;
+            n = s.coarse_grid;
+        }
+    }
+    if (kind) *kind = k;
+    if (ctas) *ctas = n;
+    if (cluster) *cluster = cl;
     return CGP_OK;
 }
 

@@ -79,7 +79,8 @@ def test_prolongation_bit_exact(cg):
     s.close(); m.close()
 
 
-@pytest.mark.parametrize("mode", ["kernels", "cluster", "persistent", "persistent_mem", "mixed", "mixed_cluster"])
+@pytest.mark.parametrize("mode", ["kernels", "cluster", "persistent", "persistent_mem", "mixed", "mixed_cluster",
+                                  "mixed_persistent"])
 @pytest.mark.parametrize("kind", ["neumann", "dirichlet"])
 def test_coarse_poisson_solve(cg, kind, mode):
     if kind == "neumann":
@@ -90,9 +91,14 @@ def test_coarse_poisson_solve(cg, kind, mode):
     extra = {"kernels": dict(coarse_mode=cg.CGP_COARSE_KERNELS), "cluster": dict(coarse_mode=cg.CGP_COARSE_CLUSTER),
              "persistent": dict(coarse_mode=cg.CGP_COARSE_PERSISTENT), "mixed": dict(precision=cg.CGP_MIXED),
              "persistent_mem": dict(coarse_mode=cg.CGP_COARSE_PERSISTENT_MEM),
-             "mixed_cluster": dict(precision=cg.CGP_MIXED, coarse_mode=cg.CGP_COARSE_CLUSTER)}[mode]
+             "mixed_cluster": dict(precision=cg.CGP_MIXED, coarse_mode=cg.CGP_COARSE_CLUSTER),
+             "mixed_persistent": dict(precision=cg.CGP_MIXED, coarse_mode=cg.CGP_COARSE_PERSISTENT)}[mode]
     s = cg.Solver(m, cg.make_params(100.0, 0.01, k=1, bc_kind=bc, bc_param=bp, guess=cg.CGP_GUESS_ZERO,
                                     **TIGHT, **extra))
+    kind = {"kernels": cg.CGP_COARSE_KERNELS, "cluster": cg.CGP_COARSE_CLUSTER, "persistent": cg.CGP_COARSE_PERSISTENT,
+            "persistent_mem": cg.CGP_COARSE_PERSISTENT_MEM, "mixed": cg.CGP_COARSE_ONCHIP,
+            "mixed_cluster": cg.CGP_COARSE_CLUSTER, "mixed_persistent": cg.CGP_COARSE_PERSISTENT_MEM}[mode]
+    assert s.coarse_info()[0] == kind
     o = CGPOracle(base, 2, 1, 100.0, 0.01, 0, bc, bc_param=bp)
     r = np.random.default_rng(1).standard_normal(o.coarse.n_vert)
     r[o.phi0_mask] = 0.0
@@ -130,7 +136,7 @@ def test_one_step_intermediates(cg):
     s.close(); m.close()
 
 
-@pytest.mark.parametrize("form", ["fp64", "fp64_kernels", "fp64_cluster", "fp64_mem", "mixed"])
+@pytest.mark.parametrize("form", ["fp64", "fp64_kernels", "fp64_cluster", "fp64_mem", "mixed", "mixed_grid"])
 def test_cavity64_k1_full_run(cg, form):
     # 64x64 lid-driven cavity, Re 100, pressure on 32x32, 50 steps at tolerance 1e-10:
     # FP64 within 1e-6 of the oracle, FP32-inner/FP64-outer within 1e-4 (it lands far closer)
@@ -138,6 +144,7 @@ def test_cavity64_k1_full_run(cg, form):
     base = w.base_mesh()
     extra = {"fp64": {}, "fp64_kernels": dict(coarse_mode=cg.CGP_COARSE_KERNELS),
              "fp64_cluster": dict(coarse_mode=cg.CGP_COARSE_CLUSTER), "mixed": dict(precision=cg.CGP_MIXED),
+             "mixed_grid": dict(precision=cg.CGP_MIXED, coarse_mode=cg.CGP_COARSE_PERSISTENT),
              "fp64_mem": dict(coarse_mode=cg.CGP_COARSE_PERSISTENT_MEM)}[form]
     m, s, o = _pair(cg, base, w.n_levels, w.k, w.Re, w.dt, w.chi, w.bc, tol_mom=w.tol_mom,
                     tol_poisson=w.tol_poisson, tol_mass=1e-12, **extra)
@@ -213,3 +220,43 @@ def test_checkpoint_resume_is_bitwise(cg):
     assert np.array_equal(U, U4) and np.array_equal(P, P4)
     for x in (s, s2, s3, m, m2, m3):
         x.close()
+
+
+def test_mixed_onchip_cluster_solve_on_channel(cg):
+    # the mixed form's FP32 inner solve held on chip by one cluster, on a mesh with phi = 0 rows
+    m, s, o = _pair(cg, _channel_small(), 2, 1, 20.0, 0.005, 1, flows.BC_CHANNEL, bp=(0.3, 0.41, 0, 0),
+                    precision=cg.CGP_MIXED, coarse_mode=cg.CGP_COARSE_ONCHIP)
+    kind, ctas, cl = s.coarse_info()
+    assert kind == cg.CGP_COARSE_ONCHIP and cl in (8, 16) and ctas == cl
+    s.step(4)
+    o.run(4)
+    U, P, t, st, rc = s.fields()
+    assert rc == 0
+    assert rel(U, o.U) < 1e-6 and rel(P, o.P) < 1e-6, (rel(U, o.U), rel(P, o.P))
+    s.close(); m.close()
+
+
+def test_coarse_solver_choice(cg):
+    base = square_mesh(16)
+    m = cg.Mesh(base.xy, base.tri, base.tag, 2)
+
+    def info(**kw):
+        s = cg.Solver(m, cg.make_params(100.0, 0.01, k=1, **kw))
+        out = s.coarse_info()
+        s.close()
+        return out
+
+    assert info(coarse_mode=cg.CGP_COARSE_KERNELS) == (cg.CGP_COARSE_KERNELS, 0, 0)
+    k, n, c = info(coarse_mode=cg.CGP_COARSE_CLUSTER)
+    assert k == cg.CGP_COARSE_CLUSTER and n == c and c in (2, 4, 8, 16)
+    k, n, c = info()                                    # FP64 default: register-resident grid solve
+    assert k == cg.CGP_COARSE_PERSISTENT and n > 0 and c == 0
+    k, n, c = info(coarse_mode=cg.CGP_COARSE_PERSISTENT_MEM)
+    assert k == cg.CGP_COARSE_PERSISTENT_MEM and n > 0 and c == 0
+    k, n, c = info(precision=cg.CGP_MIXED)              # mixed default: on-chip cluster solve
+    assert k == cg.CGP_COARSE_ONCHIP and n == c and c in (8, 16)
+    with pytest.raises(RuntimeError):
+        info(coarse_mode=cg.CGP_COARSE_ONCHIP)          # the on-chip solve is FP32: mixed form only
+    with pytest.raises(RuntimeError):
+        info(precision=cg.CGP_MIXED, coarse_mode=cg.CGP_COARSE_KERNELS)
+    m.close()
