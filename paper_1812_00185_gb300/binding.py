@@ -112,7 +112,9 @@ BATCH_CANDIDATES = [(c, t) for c in (1, 2, 4, 8) for t in (256, 512, 1024)]
 PROF_NAMES = ["mom_prep", "mom_assemble", "mom_setup", "mom_init", "bicg_p", "bicg_v", "bicg_s", "bicg_t",
               "bicg_x", "coarse_rhs", "pois_setup", "pois_init", "pois_spmv", "pois_update", "phi_mean",
               "phi_sub", "prolong", "corr_rhs", "corr_setup", "corr_init", "corr_spmv", "corr_update", "div",
-              "mass_setup", "mass_init", "mass_spmv", "mass_update", "finish", "pois_onelaunch", "mlp_forward"]
+              "mass_setup", "mass_init", "mass_spmv", "mass_update", "finish", "pois_onelaunch", "mlp_forward",
+              "ir_resid", "ir_update", "to_f32", "f32_init", "f32_spmv", "f32_update", "f32_bicg_p", "f32_bicg_v",
+              "f32_bicg_s", "f32_bicg_t", "f32_bicg_x"]
 
 _LIB = None
 

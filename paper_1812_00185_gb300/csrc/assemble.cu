@@ -175,6 +175,14 @@ static int layout(Solver& s, void* base, size_t* bytes) {
         s.oc_src = cv.take<int32_t>(nnzc);
         s.oc_send_lr = cv.take<int32_t>(nnzc);     // sends <= entries with a remote column
         s.oc_send_dst = cv.take<int32_t>(nnzc);
+        s.Af = cv.take<float>(nnzf);
+        s.M0f = cv.take<float>(nnzf);
+        s.Mf = cv.take<float>(nnzf);
+        s.dinvAf = cv.take<float>(nf);
+        s.dinvM0f = cv.take<float>(nf);
+        s.dinvMf = cv.take<float>(nf);
+        s.frhs = cv.take<float>(2 * nf);
+        for (float*& v : s.fv) v = cv.take<float>(2 * nf);
     }
     s.csr_tmp = cv.take<double>(F.nnz > C.nnz ? F.nnz : C.nnz);
     s.val_begin = s.M;
@@ -194,7 +202,7 @@ static int layout(Solver& s, void* base, size_t* bytes) {
     s.bar_count = cv.take<unsigned int>(2);
     s.bar_err = (int*)(s.bar_count ? s.bar_count + 1 : nullptr);
     s.coarse_partials = cv.take<double>((size_t)2 * s.max_grid * 4);
-    s.ks = cv.take<KrylovState>(KS_COUNT);
+    s.ks = cv.take<KrylovState>(KS_COUNT + 1);   // + the inner state of the mixed fine solves
     s.stats = cv.take<DeviceStats>(1);
     s.tdev = cv.take<double>(1);
     s.scal = cv.take<double>(16);
@@ -319,6 +327,12 @@ extern "C" int cgp_assemble(const cgp_mesh* mesh, const cgp_params* params, void
                                                      s.Kc0, s.dinvKc);
     k_to_float<<<blocks_for(C.nnz_sell), kBlock, 0, st>>>(C.nnz_sell, s.Kc0, s.Kc0f);
     k_to_float<<<blocks_for(C.nv), kBlock, 0, st>>>(C.nv, s.dinvKc, s.dinvKcf);
+    if (s.Mf) {
+        k_to_float<<<blocks_for(F.nnz_sell), kBlock, 0, st>>>(F.nnz_sell, s.M0, s.M0f);
+        k_to_float<<<blocks_for(F.nnz_sell), kBlock, 0, st>>>(F.nnz_sell, s.M, s.Mf);
+        k_to_float<<<blocks_for(F.nv), kBlock, 0, st>>>(F.nv, s.dinvM0, s.dinvM0f);
+        k_to_float<<<blocks_for(F.nv), kBlock, 0, st>>>(F.nv, s.dinvM, s.dinvMf);
+    }
     if (cudaGetLastError() != cudaSuccess) {
         set_error("assembly launch failed");
         return fail(CGP_ECUDA);
@@ -328,7 +342,7 @@ extern "C" int cgp_assemble(const cgp_mesh* mesh, const cgp_params* params, void
         if (rc != CGP_OK) return fail(rc);
     }
     if (cudaMemsetAsync(s.tickets, 0, 64 * sizeof(unsigned int), st) != cudaSuccess ||
-        cudaMemsetAsync(s.ks, 0, KS_COUNT * sizeof(KrylovState), st) != cudaSuccess ||
+        cudaMemsetAsync(s.ks, 0, (KS_COUNT + 1) * sizeof(KrylovState), st) != cudaSuccess ||
         cudaMemsetAsync(s.stats, 0, sizeof(DeviceStats), st) != cudaSuccess ||
         cudaMemsetAsync(s.phi, 0, sizeof(double) * s.nf, st) != cudaSuccess ||
         cudaMemsetAsync(s.scal, 0, sizeof(double) * 16, st) != cudaSuccess) {

@@ -52,11 +52,6 @@ __device__ __forceinline__ float oc_lds(uint32_t addr) {
 __device__ __forceinline__ void oc_barrier() {
     asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
-__device__ __forceinline__ float warp_sum_f(float v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    return v;
-}
 
 // what warp 0 tells its CTA after an FP64 reduction
 struct OnchipScalars {
@@ -163,20 +158,20 @@ static __global__ void __launch_bounds__(kOnchipThreads, 1) k_pcg_onchip(CoarseP
     // with `publish`, the CTA's new z also goes to the neighbours' halos before the barrier
     auto cred32 = [&](float (&v)[2], int nr, float (&tot)[2], bool publish) {
         for (int k = 0; k < nr; ++k) {
-            const float s = warp_sum_f(v[k]);
+            const float s = warp_sum(v[k]);
             if (lane == 0) wsum32[wid][k] = s;
         }
         __syncthreads();
         if (publish) push();
         if (wid == 0) {
             for (int k = 0; k < nr; ++k) {
-                const float s = __shfl_sync(0xffffffffu, warp_sum_f(lane < nw ? wsum32[lane][k] : 0.0f), 0);
+                const float s = __shfl_sync(0xffffffffu, warp_sum(lane < nw ? wsum32[lane][k] : 0.0f), 0);
                 if (lane < ncl) oc_st32(red32_remote + (uint32_t)(4 * ((slot * 16 + rank) * 4 + k)), s);
             }
         }
         oc_barrier();
         for (int k = 0; k < nr; ++k)
-            tot[k] = __shfl_sync(0xffffffffu, warp_sum_f(lane < ncl ? red32[(slot * 16 + lane) * 4 + k] : 0.0f), 0);
+            tot[k] = __shfl_sync(0xffffffffu, warp_sum(lane < ncl ? red32[(slot * 16 + lane) * 4 + k] : 0.0f), 0);
         slot ^= 1;
     };
     const double mean = a.project ? a.st->mean : 0.0;

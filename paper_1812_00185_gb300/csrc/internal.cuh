@@ -78,29 +78,36 @@ __device__ __forceinline__ double warp_sum(double v) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
     return v;
 }
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
 
 // Deterministic grid-wide sum of NR values per thread.  Every block writes its
 // partial sums to partials[blockIdx.x*NR + r]; the last block to arrive (ticket)
 // adds the partials in block order and returns true with the totals in tot[]
 // (valid in every thread of that block).  Other blocks return false.  All blocks
 // of the grid must call it exactly once.  The ticket is reset for the next use.
-template <int NR>
-__device__ bool grid_sum(const double (&v)[NR], double* partials, unsigned int* ticket, double (&tot)[NR]) {
+// T = float: warp and block sums in FP32, block partials and the total in FP64.
+template <int NR, class T>
+__device__ bool grid_sum(const T (&v)[NR], double* partials, unsigned int* ticket, double (&tot)[NR]) {
+    __shared__ T smt[kBlock / 32][NR];
     __shared__ double sm[kBlock / 32][NR];
     __shared__ bool is_last;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
 #pragma unroll
     for (int r = 0; r < NR; ++r) {
-        double w = warp_sum(v[r]);
-        if (lane == 0) sm[wid][r] = w;
+        T w = warp_sum(v[r]);
+        if (lane == 0) smt[wid][r] = w;
     }
     __syncthreads();
     if (wid == 0) {
 #pragma unroll
         for (int r = 0; r < NR; ++r) {
-            double x = lane < nw ? sm[lane][r] : 0.0;
+            T x = lane < nw ? smt[lane][r] : T(0);
             x = warp_sum(x);
-            if (lane == 0) partials[(size_t)blockIdx.x * NR + r] = x;
+            if (lane == 0) partials[(size_t)blockIdx.x * NR + r] = (double)x;
         }
         if (lane == 0) {
             __threadfence();

@@ -7,6 +7,9 @@
 // the last block of each reduction, so no host round trip is needed per iteration.
 // Every kernel returns at once when the solve has finished (state->done), which lets
 // a loop be replayed a fixed number of times or inside a CUDA-graph WHILE node.
+// The kernels take the working type T of vectors, matrix values and per-row arithmetic:
+// double for the FP64 solves, float for the inner solves of the mixed form (whose
+// block partial sums are still added in FP64).
 #pragma once
 
 #include "internal.cuh"
@@ -20,6 +23,8 @@ struct KrylovState {
     int maxit, iter, done, status;
     int compdone[2];
     int pad[2];
+    int inner, trips;      // mixed form: FP32 inner iterations and inner loop trips of the solve
+    int skip, pad2;        // inner solves: set when the outer residual already meets the tolerance
 };
 
 // SELL-32 pattern of a level (see Level): one warp works on one slice of 32 rows,
@@ -37,10 +42,14 @@ inline SellView sell_of(const Level& L) { return SellView{L.nv, L.nslices, L.sel
     for (int sl = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); sl < (A).nslices;        \
          sl += (int)((gridDim.x * blockDim.x) >> 5))
 
-template <int NC>
-__device__ __forceinline__ void ldv(const double* __restrict__ p, int i, double (&o)[NC]) {
+template <class T> struct Vec2T;
+template <> struct Vec2T<double> { using type = double2; };
+template <> struct Vec2T<float> { using type = float2; };
+
+template <int NC, class T>
+__device__ __forceinline__ void ldv(const T* __restrict__ p, int i, T (&o)[NC]) {
     if constexpr (NC == 2) {
-        double2 v = reinterpret_cast<const double2*>(p)[i];
+        const auto v = reinterpret_cast<const typename Vec2T<T>::type*>(p)[i];
         o[0] = v.x;
         o[1] = v.y;
     } else {
@@ -48,41 +57,43 @@ __device__ __forceinline__ void ldv(const double* __restrict__ p, int i, double 
     }
 }
 
-template <int NC>
-__device__ __forceinline__ void stv(double* __restrict__ p, int i, const double (&o)[NC]) {
+template <int NC, class T>
+__device__ __forceinline__ void stv(T* __restrict__ p, int i, const T (&o)[NC]) {
     if constexpr (NC == 2) {
-        reinterpret_cast<double2*>(p)[i] = make_double2(o[0], o[1]);
+        typename Vec2T<T>::type v;
+        v.x = o[0];
+        v.y = o[1];
+        reinterpret_cast<typename Vec2T<T>::type*>(p)[i] = v;
     } else {
         p[i] = o[0];
     }
 }
 
-
 // acc[c] += sum_k val(row, k) * g(col(row, k))[c] over the row of (slice sl, lane).
 // The pattern and value loads of up to 8 entries are issued together, then the 8
 // gathers, so a row costs about three dependent memory round trips (slice offset,
 // pattern/values, gathered vector) instead of two per entry.
-template <int NC, class T, class Gather>
-__device__ __forceinline__ void sell_accum(const SellView& A, const T* __restrict__ val, int sl, int lane, Gather&& g,
-                                           double (&acc)[NC]) {
+template <int NC, class V, class Acc, class Gather>
+__device__ __forceinline__ void sell_accum(const SellView& A, const V* __restrict__ val, int sl, int lane, Gather&& g,
+                                           Acc (&acc)[NC]) {
     const int base = __ldg(A.ptr + sl), w = (__ldg(A.ptr + sl + 1) - base) >> 5;
     for (int k0 = 0; k0 < w; k0 += 8) {
         int cj[8];
-        double av[8];
+        Acc av[8];
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
             cj[u] = 0;
-            av[u] = 0.0;
+            av[u] = Acc(0);
             if (k0 + u < w) {
                 const int e = base + 32 * (k0 + u) + lane;
                 cj[u] = __ldg(A.col + e);
-                av[u] = (double)__ldg(val + e);
+                av[u] = (Acc)__ldg(val + e);
             }
         }
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
             if (k0 + u < w) {
-                double xv[NC];
+                Acc xv[NC];
                 g(cj[u], xv);
 #pragma unroll
                 for (int c = 0; c < NC; ++c) acc[c] += av[u] * xv[c];
@@ -101,29 +112,39 @@ __device__ __forceinline__ bool finite(double x) { return isfinite(x); }
 
 // ------------------------------------------------------------------ PCG
 // init: r = b - A x (x = 0 if zero_x), optional rhs projection b -= mean,
-// z = D^{-1} r, p = z; rz = <r,z>, rr = <r,r>, bb = <b,b>.
-template <int NC>
-__global__ void __launch_bounds__(kBlock) k_pcg_init(SellView A, const double* __restrict__ val,
-                                                    const double* __restrict__ dinv, double* __restrict__ b,
-                                                    double* __restrict__ x, double* __restrict__ r,
-                                                    double* __restrict__ z, double* __restrict__ p,
+// z = D^{-1} r, p = z; rz = <r,z>, rr = <r,r>, bb = <b,b>.  An inner solve whose `skip`
+// is set (the outer residual already converged) reports done at once.
+template <int NC, class T = double>
+__global__ void __launch_bounds__(kBlock) k_pcg_init(SellView A, const T* __restrict__ val,
+                                                    const T* __restrict__ dinv, T* __restrict__ b,
+                                                    T* __restrict__ x, T* __restrict__ r,
+                                                    T* __restrict__ z, T* __restrict__ p,
                                                     KrylovState* st, double* partials, unsigned int* ticket,
                                                     int zero_x, int project, unsigned long long cond) {
-    const double mean = project ? st->mean : 0.0;
+    if (st->skip) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            st->iter = 0;
+            st->status = 0;
+            st->done = 1;
+            set_loop_condition(cond, 0);
+        }
+        return;
+    }
+    const T mean = project ? (T)st->mean : T(0);
     const int lane = threadIdx.x & 31;
-    double acc[3 * NC];
+    T acc[3 * NC];
 #pragma unroll
-    for (int k = 0; k < 3 * NC; ++k) acc[k] = 0.0;
+    for (int k = 0; k < 3 * NC; ++k) acc[k] = T(0);
     CGP_SLICE_LOOP(A, sl) {
         const int i = sl * 32 + lane;
-        double ax[NC];
+        T ax[NC];
 #pragma unroll
-        for (int c = 0; c < NC; ++c) ax[c] = 0.0;
-        if (!zero_x) sell_accum<NC>(A, val, sl, lane, [&](int j, double (&o)[NC]) { ldv<NC>(x, j, o); }, ax);
+        for (int c = 0; c < NC; ++c) ax[c] = T(0);
+        if (!zero_x) sell_accum<NC>(A, val, sl, lane, [&](int j, T (&o)[NC]) { ldv<NC>(x, j, o); }, ax);
         if (i < A.n) {
-            double bv[NC], rv[NC], zv[NC];
+            T bv[NC], rv[NC], zv[NC];
             ldv<NC>(b, i, bv);
-            const double d = dinv[i];
+            const T d = dinv[i];
 #pragma unroll
             for (int c = 0; c < NC; ++c) {
                 if (project) bv[c] -= mean;
@@ -135,9 +156,9 @@ __global__ void __launch_bounds__(kBlock) k_pcg_init(SellView A, const double* _
             }
             if (project) stv<NC>(b, i, bv);
             if (zero_x) {
-                double zero[NC];
+                T zero[NC];
 #pragma unroll
-                for (int c = 0; c < NC; ++c) zero[c] = 0.0;
+                for (int c = 0; c < NC; ++c) zero[c] = T(0);
                 stv<NC>(x, i, zero);
             }
             stv<NC>(r, i, rv);
@@ -174,27 +195,27 @@ __global__ void __launch_bounds__(kBlock) k_pcg_init(SellView A, const double* _
 }
 
 // q = A p_new with p_new = z + beta p_old computed on the fly; pq = <p_new, q>.
-template <int NC>
-__global__ void __launch_bounds__(kBlock) k_pcg_spmv(SellView A, const double* __restrict__ val,
-                                                    const double* __restrict__ z, const double* __restrict__ pold,
-                                                    double* __restrict__ pnew, double* __restrict__ q,
+template <int NC, class T = double>
+__global__ void __launch_bounds__(kBlock) k_pcg_spmv(SellView A, const T* __restrict__ val,
+                                                    const T* __restrict__ z, const T* __restrict__ pold,
+                                                    T* __restrict__ pnew, T* __restrict__ q,
                                                     KrylovState* st, double* partials, unsigned int* ticket) {
     if (st->done) return;
     const int lane = threadIdx.x & 31;
-    double beta[NC];
+    T beta[NC];
 #pragma unroll
-    for (int c = 0; c < NC; ++c) beta[c] = st->beta[c];
-    double acc[NC];
+    for (int c = 0; c < NC; ++c) beta[c] = (T)st->beta[c];
+    T acc[NC];
 #pragma unroll
-    for (int c = 0; c < NC; ++c) acc[c] = 0.0;
+    for (int c = 0; c < NC; ++c) acc[c] = T(0);
     CGP_SLICE_LOOP(A, sl) {
         const int i = sl * 32 + lane;
-        double ax[NC];
+        T ax[NC];
 #pragma unroll
-        for (int c = 0; c < NC; ++c) ax[c] = 0.0;
+        for (int c = 0; c < NC; ++c) ax[c] = T(0);
         sell_accum<NC>(A, val, sl, lane,
-                       [&](int j, double (&o)[NC]) {
-                           double zv[NC], pv[NC];
+                       [&](int j, T (&o)[NC]) {
+                           T zv[NC], pv[NC];
                            ldv<NC>(z, j, zv);
                            ldv<NC>(pold, j, pv);
 #pragma unroll
@@ -202,7 +223,7 @@ __global__ void __launch_bounds__(kBlock) k_pcg_spmv(SellView A, const double* _
                        },
                        ax);
         if (i < A.n) {
-            double zv[NC], pv[NC];
+            T zv[NC], pv[NC];
             ldv<NC>(z, i, zv);
             ldv<NC>(pold, i, pv);
 #pragma unroll
@@ -232,30 +253,30 @@ __global__ void __launch_bounds__(kBlock) k_pcg_spmv(SellView A, const double* _
 }
 
 // x += alpha p, r -= alpha q, z = D^{-1} r; rz = <r,z>, rr = <r,r>; convergence test.
-template <int NC>
-__global__ void __launch_bounds__(kBlock) k_pcg_update(int n, const double* __restrict__ dinv,
-                                                      double* __restrict__ x, double* __restrict__ r,
-                                                      double* __restrict__ z, const double* __restrict__ p,
-                                                      const double* __restrict__ q, KrylovState* st,
+template <int NC, class T = double>
+__global__ void __launch_bounds__(kBlock) k_pcg_update(int n, const T* __restrict__ dinv,
+                                                      T* __restrict__ x, T* __restrict__ r,
+                                                      T* __restrict__ z, const T* __restrict__ p,
+                                                      const T* __restrict__ q, KrylovState* st,
                                                       double* partials, unsigned int* ticket,
                                                       unsigned long long cond) {
     if (st->done) {
         if (blockIdx.x == 0 && threadIdx.x == 0) set_loop_condition(cond, 0);
         return;
     }
-    double alpha[NC];
+    T alpha[NC];
 #pragma unroll
-    for (int c = 0; c < NC; ++c) alpha[c] = st->alpha[c];
-    double acc[2 * NC];
+    for (int c = 0; c < NC; ++c) alpha[c] = (T)st->alpha[c];
+    T acc[2 * NC];
 #pragma unroll
-    for (int k = 0; k < 2 * NC; ++k) acc[k] = 0.0;
+    for (int k = 0; k < 2 * NC; ++k) acc[k] = T(0);
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        double xv[NC], rv[NC], pv[NC], qv[NC], zv[NC];
+        T xv[NC], rv[NC], pv[NC], qv[NC], zv[NC];
         ldv<NC>(x, i, xv);
         ldv<NC>(r, i, rv);
         ldv<NC>(p, i, pv);
         ldv<NC>(q, i, qv);
-        const double d = dinv[i];
+        const T d = dinv[i];
 #pragma unroll
         for (int c = 0; c < NC; ++c) {
             xv[c] += alpha[c] * pv[c];
@@ -302,37 +323,53 @@ __global__ void __launch_bounds__(kBlock) k_pcg_update(int n, const double* __re
 //   p = r + beta (p - omega v);  y = D^{-1} p;  v = A y;  alpha = rho / <rhat, v>
 //   s = r - alpha v;  z = D^{-1} s;  t = A z;  omega = <t, s> / <t, t>
 //   x += alpha y + omega z;  r = s - omega t;  rho' = <rhat, r>;  beta = rho'/rho * alpha/omega
-struct BicgVecs {
-    double *x, *r, *rhat, *p, *v, *y, *s, *z, *t;   // 2 components interleaved
+template <class T>
+struct BicgVecsT {
+    T *x, *r, *rhat, *p, *v, *y, *s, *z, *t;   // 2 components interleaved
 };
+using BicgVecs = BicgVecsT<double>;
 
 // two-component SELL SpMV of row (sl, lane): returns A u at that row
-static __device__ __forceinline__ void spmv2_row(const SellView& A, const double* __restrict__ val,
-                                          const double* __restrict__ u, int sl, int lane, double (&ax)[2]) {
-    ax[0] = ax[1] = 0.0;
-    sell_accum<2>(A, val, sl, lane, [&](int j, double (&o)[2]) { ldv<2>(u, j, o); }, ax);
+template <class T>
+static __device__ __forceinline__ void spmv2_row(const SellView& A, const T* __restrict__ val,
+                                                 const T* __restrict__ u, int sl, int lane, T (&ax)[2]) {
+    ax[0] = ax[1] = T(0);
+    sell_accum<2>(A, val, sl, lane, [&](int j, T (&o)[2]) { ldv<2>(u, j, o); }, ax);
 }
 
-static __global__ void __launch_bounds__(kBlock) k_bicg_init(SellView A, const double* __restrict__ val,
-                                                     const double* __restrict__ b, BicgVecs V, KrylovState* st,
+// init: r = b - A x (x = 0 if zero_x), rhat = r, p = v = 0; rho, rr, bb.  An inner solve
+// whose `skip` is set reports done at once.
+template <class T>
+static __global__ void __launch_bounds__(kBlock) k_bicg_init(SellView A, const T* __restrict__ val,
+                                                     const T* __restrict__ b, BicgVecsT<T> V, KrylovState* st,
                                                      double* partials, unsigned int* ticket,
-                                                     unsigned long long cond) {
+                                                     unsigned long long cond, int zero_x = 0) {
+    if (st->skip) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            st->iter = 0;
+            st->status = 0;
+            st->done = 1;
+            set_loop_condition(cond, 0);
+        }
+        return;
+    }
     const int lane = threadIdx.x & 31;
-    double acc[6] = {0, 0, 0, 0, 0, 0};
+    T acc[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
     CGP_SLICE_LOOP(A, sl) {
         const int i = sl * 32 + lane;
-        double ax[2];
-        spmv2_row(A, val, V.x, sl, lane, ax);
+        T ax[2] = {T(0), T(0)};
+        if (!zero_x) spmv2_row(A, val, V.x, sl, lane, ax);
         if (i < A.n) {
-            double bv[2], rv[2];
+            T bv[2], rv[2];
             ldv<2>(b, i, bv);
-            const double zero[2] = {0.0, 0.0};
+            const T zero[2] = {T(0), T(0)};
             for (int c = 0; c < 2; ++c) {
                 rv[c] = bv[c] - ax[c];
                 acc[c] += rv[c] * rv[c];        // rho = <rhat, r> with rhat = r
                 acc[2 + c] += rv[c] * rv[c];
                 acc[4 + c] += bv[c] * bv[c];
             }
+            if (zero_x) stv<2>(V.x, i, zero);
             stv<2>(V.r, i, rv);
             stv<2>(V.rhat, i, rv);
             stv<2>(V.p, i, zero);
@@ -364,16 +401,17 @@ static __global__ void __launch_bounds__(kBlock) k_bicg_init(SellView A, const d
 }
 
 // p = r + beta (p - omega v); y = D^{-1} p
-static __global__ void __launch_bounds__(kBlock) k_bicg_p(int n, const double* __restrict__ dinv, BicgVecs V,
+template <class T>
+static __global__ void __launch_bounds__(kBlock) k_bicg_p(int n, const T* __restrict__ dinv, BicgVecsT<T> V,
                                                   const KrylovState* st) {
     if (st->done) return;
-    const double beta[2] = {st->beta[0], st->beta[1]}, omega[2] = {st->omega[0], st->omega[1]};
+    const T beta[2] = {(T)st->beta[0], (T)st->beta[1]}, omega[2] = {(T)st->omega[0], (T)st->omega[1]};
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        double rv[2], pv[2], vv[2], yv[2];
+        T rv[2], pv[2], vv[2], yv[2];
         ldv<2>(V.r, i, rv);
         ldv<2>(V.p, i, pv);
         ldv<2>(V.v, i, vv);
-        const double d = dinv[i];
+        const T d = dinv[i];
         for (int c = 0; c < 2; ++c) {
             pv[c] = rv[c] + beta[c] * (pv[c] - omega[c] * vv[c]);
             yv[c] = d * pv[c];
@@ -384,17 +422,18 @@ static __global__ void __launch_bounds__(kBlock) k_bicg_p(int n, const double* _
 }
 
 // v = A y; alpha = rho / <rhat, v>
-static __global__ void __launch_bounds__(kBlock) k_bicg_v(SellView A, const double* __restrict__ val, BicgVecs V,
+template <class T>
+static __global__ void __launch_bounds__(kBlock) k_bicg_v(SellView A, const T* __restrict__ val, BicgVecsT<T> V,
                                                   KrylovState* st, double* partials, unsigned int* ticket) {
     if (st->done) return;
     const int lane = threadIdx.x & 31;
-    double acc[2] = {0.0, 0.0};
+    T acc[2] = {T(0), T(0)};
     CGP_SLICE_LOOP(A, sl) {
         const int i = sl * 32 + lane;
-        double ax[2];
+        T ax[2];
         spmv2_row(A, val, V.y, sl, lane, ax);
         if (i < A.n) {
-            double rh[2];
+            T rh[2];
             ldv<2>(V.rhat, i, rh);
             acc[0] += rh[0] * ax[0];
             acc[1] += rh[1] * ax[1];
@@ -418,15 +457,16 @@ static __global__ void __launch_bounds__(kBlock) k_bicg_v(SellView A, const doub
 }
 
 // s = r - alpha v; z = D^{-1} s
-static __global__ void __launch_bounds__(kBlock) k_bicg_s(int n, const double* __restrict__ dinv, BicgVecs V,
+template <class T>
+static __global__ void __launch_bounds__(kBlock) k_bicg_s(int n, const T* __restrict__ dinv, BicgVecsT<T> V,
                                                   const KrylovState* st) {
     if (st->done) return;
-    const double alpha[2] = {st->alpha[0], st->alpha[1]};
+    const T alpha[2] = {(T)st->alpha[0], (T)st->alpha[1]};
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        double rv[2], vv[2], sv[2], zv[2];
+        T rv[2], vv[2], sv[2], zv[2];
         ldv<2>(V.r, i, rv);
         ldv<2>(V.v, i, vv);
-        const double d = dinv[i];
+        const T d = dinv[i];
         for (int c = 0; c < 2; ++c) {
             sv[c] = rv[c] - alpha[c] * vv[c];
             zv[c] = d * sv[c];
@@ -437,17 +477,18 @@ static __global__ void __launch_bounds__(kBlock) k_bicg_s(int n, const double* _
 }
 
 // t = A z; omega = <t,s>/<t,t>
-static __global__ void __launch_bounds__(kBlock) k_bicg_t(SellView A, const double* __restrict__ val, BicgVecs V,
+template <class T>
+static __global__ void __launch_bounds__(kBlock) k_bicg_t(SellView A, const T* __restrict__ val, BicgVecsT<T> V,
                                                   KrylovState* st, double* partials, unsigned int* ticket) {
     if (st->done) return;
     const int lane = threadIdx.x & 31;
-    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    T acc[4] = {T(0), T(0), T(0), T(0)};
     CGP_SLICE_LOOP(A, sl) {
         const int i = sl * 32 + lane;
-        double ax[2];
+        T ax[2];
         spmv2_row(A, val, V.z, sl, lane, ax);
         if (i < A.n) {
-            double sv[2];
+            T sv[2];
             ldv<2>(V.s, i, sv);
             for (int c = 0; c < 2; ++c) {
                 acc[c] += ax[c] * sv[c];
@@ -471,16 +512,17 @@ static __global__ void __launch_bounds__(kBlock) k_bicg_t(SellView A, const doub
 }
 
 // x += alpha y + omega z; r = s - omega t; rho' = <rhat, r>; beta; convergence test
-static __global__ void __launch_bounds__(kBlock) k_bicg_x(int n, BicgVecs V, KrylovState* st, double* partials,
+template <class T>
+static __global__ void __launch_bounds__(kBlock) k_bicg_x(int n, BicgVecsT<T> V, KrylovState* st, double* partials,
                                                   unsigned int* ticket, unsigned long long cond) {
     if (st->done) {
         if (blockIdx.x == 0 && threadIdx.x == 0) set_loop_condition(cond, 0);
         return;
     }
-    const double alpha[2] = {st->alpha[0], st->alpha[1]}, omega[2] = {st->omega[0], st->omega[1]};
-    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    const T alpha[2] = {(T)st->alpha[0], (T)st->alpha[1]}, omega[2] = {(T)st->omega[0], (T)st->omega[1]};
+    T acc[4] = {T(0), T(0), T(0), T(0)};
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        double xv[2], yv[2], zv[2], sv[2], tv[2], rh[2], rv[2];
+        T xv[2], yv[2], zv[2], sv[2], tv[2], rh[2], rv[2];
         ldv<2>(V.x, i, xv);
         ldv<2>(V.y, i, yv);
         ldv<2>(V.z, i, zv);

@@ -84,6 +84,11 @@ struct Solver {
     double *g = nullptr, *delta = nullptr;                                                           // 2*nf
     BicgVecs bv{};
     double *kr = nullptr, *kz = nullptr, *kp0 = nullptr, *kp1 = nullptr, *kq = nullptr;             // 2*nf each
+    // mixed form, fine-level FP32 inner solves: FP32 copies of the matrices and Jacobi
+    // diagonals (A refreshed every step), the right-hand side and the inner vectors
+    float *Af = nullptr, *dinvAf = nullptr, *M0f = nullptr, *dinvM0f = nullptr, *Mf = nullptr, *dinvMf = nullptr;
+    float* frhs = nullptr;        // 2*nf: FP32 residual of the current refinement sweep
+    float* fv[9] = {};            // 2*nf each: inner PCG (r, z, p0, p1, q, e) / BiCGStab (x..t)
     double* partials = nullptr;
     unsigned int* tickets = nullptr;
     KrylovState* ks = nullptr;    // KS_COUNT states

@@ -240,12 +240,15 @@ __global__ void k_finish(int nf, double* __restrict__ U, double* __restrict__ Up
         int64_t l = fixed_launches + 5 * (int64_t)ks[KS_MOM].iter;
         for (int k = KS_POIS; k < KS_COUNT; ++k)
             if (k != KS_POIS || pois_loop) l += 4 * (int64_t)((ks[k].iter + 1) / 2);
+        // FP32 inner loops of the mixed form: 5 kernels per BiCGStab trip, 4 per PCG trip
+        l += 5 * (int64_t)ks[KS_MOM].trips + 4 * (int64_t)(ks[KS_CORR].trips + ks[KS_MASS].trips);
         stats->launches += l;
         if (ks[KS_POIS].pad[1]) stats->guess_used += 1;
         stats->sum_outer += ks[KS_POIS].pad[0];
         for (int k = 0; k < KS_COUNT; ++k) {
-            stats->last_it[k] = ks[k].iter;
-            stats->sum_it[k] += ks[k].iter;
+            const int it = ks[k].iter + (k != KS_POIS ? ks[k].inner : 0);   // FP64 + FP32 inner iterations
+            stats->last_it[k] = it;
+            stats->sum_it[k] += it;
             double r = 0.0;
             for (int c = 0; c < 2; ++c)
                 if (ks[k].bb[c] > 0.0) r = fmax(r, sqrt(ks[k].rr[c] / ks[k].bb[c]));
@@ -264,6 +267,7 @@ __global__ void k_ks_setup(KrylovState* st, double tol2, int maxit) {
     st->status = 0;
     st->pad[0] = 0;
     st->pad[1] = 0;
+    st->skip = 0;
 }
 
 // ---------------------------------------------------------------- loop control
@@ -312,7 +316,7 @@ static int krylov_loop(Ctx& c, KrylovState* ks, int max_trips, Init init, Body b
     if (!c.capture) {
         if (c.prof) k_spin<<<1, 32, 0, c.st>>>(40);
         CGP_TRY(init(c.st, 0ull));
-        const int chunk = 4;
+        const int chunk = c.prof ? 1 : 4;   // profiling: no trips after convergence
         for (int trip = 0; trip < max_trips; trip += chunk) {
             if (c.prof) k_spin<<<1, 32, 0, c.st>>>(40);
             for (int k = 0; k < chunk; ++k) CGP_TRY(body(c.st, 0ull));
@@ -402,6 +406,177 @@ static int bicgstab(Ctx& c, SellView A, const double* val, const double* dinv, c
         return CGP_OK;
     };
     return krylov_loop(c, ks, maxit + 1, init, body);
+}
+
+// ---------------------------------------------------------------- mixed form: FP32 inner solves
+// Iterative refinement for the fine-level systems of the mixed form (Eqs. 21, 25, 26): each
+// sweep forms the FP64 residual r = b - A x, solves A e = r in FP32 (PCG or BiCGStab, to a
+// reduction kIrInnerTol of its residual norm) and adds e to x in FP64.  The FP64 Krylov
+// loop that follows polishes x to the tolerance and stops at once (its init sees the
+// converged residual) when the sweeps already met it, so the result has the accuracy of
+// the FP64 solve.  A sweep whose residual already meets the tolerance skips its inner solve.
+constexpr int kIrSweeps = 3;
+constexpr double kIrInnerTol = 1e-4;
+constexpr int kIrInnerMaxit = 200;
+
+template <int NC>
+__global__ void __launch_bounds__(kBlock) k_ir_residual(SellView A, const double* __restrict__ val,
+                                                       const double* __restrict__ b, double* __restrict__ x,
+                                                       float* __restrict__ r32, KrylovState* st, KrylovState* in,
+                                                       double tol2, int sweep, int zero_x, double* partials,
+                                                       unsigned int* ticket) {
+    const int lane = threadIdx.x & 31;
+    double acc[2 * NC];
+#pragma unroll
+    for (int k = 0; k < 2 * NC; ++k) acc[k] = 0.0;
+    CGP_SLICE_LOOP(A, sl) {
+        const int i = sl * 32 + lane;
+        double ax[NC];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) ax[c] = 0.0;
+        if (!zero_x) sell_accum<NC>(A, val, sl, lane, [&](int j, double (&o)[NC]) { ldv<NC>(x, j, o); }, ax);
+        if (i < A.n) {
+            double bv[NC], zero[NC];
+            float rf[NC];
+            ldv<NC>(b, i, bv);
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+                const double r = bv[c] - ax[c];
+                rf[c] = (float)r;
+                zero[c] = 0.0;
+                acc[c] += r * r;
+                acc[NC + c] += bv[c] * bv[c];
+            }
+            stv<NC>(r32, i, rf);
+            if (zero_x) stv<NC>(x, i, zero);
+        }
+    }
+    double tot[2 * NC];
+    if (grid_sum<2 * NC>(acc, partials, ticket, tot) && threadIdx.x == 0) {
+        if (sweep == 0) {
+            for (int c = 0; c < NC; ++c) st->bb[c] = tot[NC + c];
+            st->inner = 0;
+            st->trips = 0;
+        }
+        bool all = true, ok = true;
+        for (int c = 0; c < NC; ++c) {
+            st->rr[c] = tot[c];
+            all &= tot[c] <= tol2 * st->bb[c];
+            ok &= finite(tot[c]);
+        }
+        in->skip = (all || !ok) ? 1 : 0;
+        in->tol2 = kIrInnerTol * kIrInnerTol;
+        in->maxit = kIrInnerMaxit;
+        in->iter = 0;
+        in->done = 0;
+        in->status = 0;
+    }
+}
+
+// x += e (FP64) after an inner solve; counts its iterations and loop trips
+template <int NC>
+__global__ void __launch_bounds__(kBlock) k_ir_update(int n, double* __restrict__ x, const float* __restrict__ e,
+                                                     KrylovState* st, const KrylovState* in, int iters_per_trip) {
+    if (in->skip) return;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        st->inner += in->iter;
+        st->trips += (in->iter + iters_per_trip - 1) / iters_per_trip;
+    }
+    if (in->status == CGP_ENONFINITE) return;   // keep x; the FP64 loop takes over
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        double xv[NC];
+        float ev[NC];
+        ldv<NC>(x, i, xv);
+        ldv<NC>(e, i, ev);
+#pragma unroll
+        for (int c = 0; c < NC; ++c) xv[c] += (double)ev[c];
+        stv<NC>(x, i, xv);
+    }
+}
+
+// FP32 copies of a matrix and its Jacobi diagonal
+__global__ void k_to_f32_pair(int64_t n1, const double* __restrict__ a1, float* __restrict__ b1, int64_t n2,
+                              const double* __restrict__ a2, float* __restrict__ b2) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n1; i += stride) b1[i] = (float)a1[i];
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n2; i += stride) b2[i] = (float)a2[i];
+}
+
+// PCG with FP32 inner solves (mixed form); same contract as pcg<NC> without the projection
+template <int NC>
+static int pcg_mixed(Ctx& c, SellView A, const double* val, const float* valf, const double* dinv, const float* dinvf,
+                     double* b, double* x, KrylovState* ks, double tol, int maxit, bool zero_x, int pid) {
+    Solver& s = *c.s;
+    KrylovState* in = s.ks + KS_COUNT;
+    const int gs = grid_rows(s, A.nslices * 32, 1), gv = grid_rows(s, A.n, 1);
+    float *fr = s.fv[0], *fz = s.fv[1], *fp0 = s.fv[2], *fp1 = s.fv[3], *fq = s.fv[4], *fe = s.fv[5];
+    for (int sw = 0; sw < kIrSweeps; ++sw) {
+        PL(c, CGP_PROF_IR_RESID,
+           k_ir_residual<NC><<<gs, kBlock, 0, c.st>>>(A, val, b, x, s.frhs, ks, in, tol * tol, sw, zero_x && sw == 0,
+                                                      s.partials, s.tickets));
+        CGP_LAUNCH_CHECK();
+        auto init = [&, gs](cudaStream_t st, unsigned long long h) -> int {
+            PL(c, CGP_PROF_F32_INIT,
+               k_pcg_init<NC, float><<<gs, kBlock, 0, st>>>(A, valf, dinvf, s.frhs, fe, fr, fz, fp0, in, s.partials,
+                                                            s.tickets, 1, 0, h));
+            CGP_LAUNCH_CHECK();
+            return CGP_OK;
+        };
+        auto body = [&, gs, gv](cudaStream_t st, unsigned long long h) -> int {
+            PL(c, CGP_PROF_F32_SPMV,
+               k_pcg_spmv<NC, float><<<gs, kBlock, 0, st>>>(A, valf, fz, fp0, fp1, fq, in, s.partials, s.tickets));
+            PL(c, CGP_PROF_F32_UPDATE,
+               k_pcg_update<NC, float><<<gv, kBlock, 0, st>>>(A.n, dinvf, fe, fr, fz, fp1, fq, in, s.partials,
+                                                              s.tickets, h));
+            PL(c, CGP_PROF_F32_SPMV,
+               k_pcg_spmv<NC, float><<<gs, kBlock, 0, st>>>(A, valf, fz, fp1, fp0, fq, in, s.partials, s.tickets));
+            PL(c, CGP_PROF_F32_UPDATE,
+               k_pcg_update<NC, float><<<gv, kBlock, 0, st>>>(A.n, dinvf, fe, fr, fz, fp0, fq, in, s.partials,
+                                                              s.tickets, h));
+            CGP_LAUNCH_CHECK();
+            return CGP_OK;
+        };
+        CGP_TRY(krylov_loop(c, in, (kIrInnerMaxit + 1) / 2 + 1, init, body));
+        PL(c, CGP_PROF_IR_UPDATE, k_ir_update<NC><<<gv, kBlock, 0, c.st>>>(A.n, x, fe, ks, in, 2));
+        CGP_LAUNCH_CHECK();
+    }
+    return pcg<NC>(c, A, val, dinv, b, x, ks, tol, maxit, false, false, pid);
+}
+
+// BiCGStab with FP32 inner solves (mixed form); the FP32 matrix is refreshed first
+static int bicgstab_mixed(Ctx& c, SellView A, int64_t nnz, const double* val, const double* dinv, const double* b,
+                          KrylovState* ks, double tol, int maxit) {
+    Solver& s = *c.s;
+    KrylovState* in = s.ks + KS_COUNT;
+    const int gs = grid_rows(s, A.nslices * 32, 1), gv = grid_rows(s, A.n, 1);
+    PL(c, CGP_PROF_TO_F32, k_to_f32_pair<<<gv, kBlock, 0, c.st>>>(nnz, val, s.Af, A.n, dinv, s.dinvAf));
+    CGP_LAUNCH_CHECK();
+    const BicgVecsT<float> V{s.fv[0], s.fv[1], s.fv[2], s.fv[3], s.fv[4], s.fv[5], s.fv[6], s.fv[7], s.fv[8]};
+    for (int sw = 0; sw < kIrSweeps; ++sw) {
+        PL(c, CGP_PROF_IR_RESID,
+           k_ir_residual<2><<<gs, kBlock, 0, c.st>>>(A, val, b, s.bv.x, s.frhs, ks, in, tol * tol, sw, 0, s.partials,
+                                                     s.tickets));
+        CGP_LAUNCH_CHECK();
+        auto init = [&, gs, V](cudaStream_t st, unsigned long long h) -> int {
+            PL(c, CGP_PROF_F32_INIT,
+               k_bicg_init<float><<<gs, kBlock, 0, st>>>(A, s.Af, s.frhs, V, in, s.partials, s.tickets, h, 1));
+            CGP_LAUNCH_CHECK();
+            return CGP_OK;
+        };
+        auto body = [&, gs, gv, V](cudaStream_t st, unsigned long long h) -> int {
+            PL(c, CGP_PROF_F32_BICG_P, k_bicg_p<float><<<gv, kBlock, 0, st>>>(A.n, s.dinvAf, V, in));
+            PL(c, CGP_PROF_F32_BICG_V, k_bicg_v<float><<<gs, kBlock, 0, st>>>(A, s.Af, V, in, s.partials, s.tickets));
+            PL(c, CGP_PROF_F32_BICG_S, k_bicg_s<float><<<gv, kBlock, 0, st>>>(A.n, s.dinvAf, V, in));
+            PL(c, CGP_PROF_F32_BICG_T, k_bicg_t<float><<<gs, kBlock, 0, st>>>(A, s.Af, V, in, s.partials, s.tickets));
+            PL(c, CGP_PROF_F32_BICG_X, k_bicg_x<float><<<gv, kBlock, 0, st>>>(A.n, V, in, s.partials, s.tickets, h));
+            CGP_LAUNCH_CHECK();
+            return CGP_OK;
+        };
+        CGP_TRY(krylov_loop(c, in, kIrInnerMaxit + 1, init, body));
+        PL(c, CGP_PROF_IR_UPDATE, k_ir_update<2><<<gv, kBlock, 0, c.st>>>(A.n, s.bv.x, V.x, ks, in, 1));
+        CGP_LAUNCH_CHECK();
+    }
+    return bicgstab(c, A, val, dinv, b, ks, tol, maxit);
 }
 
 // ---------------------------------------------------------------- coarse solver choice
@@ -655,7 +830,10 @@ int step_pre(Ctx& c) {
                                                s.vtslot, s.S, s.M, s.CxT, s.CyT, s.P, s.w, s.h, F.tag, F.xy, bc,
                                                s.tdev, p.dt, s.A, s.dinvA, s.b, s.Ut));
     CGP_LAUNCH_CHECK();
-    CGP_TRY(bicgstab(c, Af, s.A, s.dinvA, s.b, &s.ks[KS_MOM], p.tol_mom, p.max_it_mom));
+    if (p.precision == CGP_MIXED)
+        CGP_TRY(bicgstab_mixed(c, Af, F.nnz_sell, s.A, s.dinvA, s.b, &s.ks[KS_MOM], p.tol_mom, p.max_it_mom));
+    else
+        CGP_TRY(bicgstab(c, Af, s.A, s.dinvA, s.b, &s.ks[KS_MOM], p.tol_mom, p.max_it_mom));
     // Eqs. 22-23: injection and coarse divergence
     PL(c, CGP_PROF_COARSE_RHS,
        k_coarse_rhs<<<grid_rows(s, C.nslices * 32, 1), kBlock, 0, c.st>>>(
@@ -679,7 +857,11 @@ int step_post(Ctx& c) {
        k_corr_rhs<<<gs, kBlock, 0, c.st>>>(Af, s.Cx, s.Cy, s.phi, F.tag, p.dt, s.g,
                                                    lumped ? s.mlumpF : nullptr, s.delta));
     CGP_LAUNCH_CHECK();
-    if (!lumped)
+    const bool mixed = p.precision == CGP_MIXED;
+    if (!lumped && mixed)
+        CGP_TRY(pcg_mixed<2>(c, Af, s.M0, s.M0f, s.dinvM0, s.dinvM0f, s.g, s.delta, &s.ks[KS_CORR], p.tol_mass,
+                             p.max_it_mass, true, CGP_PROF_CORR_SETUP));
+    else if (!lumped)
         CGP_TRY(pcg<2>(c, Af, s.M0, s.dinvM0, s.g, s.delta, &s.ks[KS_CORR], p.tol_mass, p.max_it_mass, true, false,
                        CGP_PROF_CORR_SETUP));
     // Eq. 26: pressure
@@ -687,14 +869,20 @@ int step_post(Ctx& c) {
         PL(c, CGP_PROF_DIV,
            k_div<<<gs, kBlock, 0, c.st>>>(Af, s.Cx, s.Cy, s.Ut, s.div, lumped ? s.mlumpF : nullptr, s.qrot));
         CGP_LAUNCH_CHECK();
-        if (!lumped)
+        if (!lumped && mixed)
+            CGP_TRY(pcg_mixed<1>(c, Af, s.M, s.Mf, s.dinvM, s.dinvMf, s.div, s.qrot, &s.ks[KS_MASS], p.tol_mass,
+                                 p.max_it_mass, true, CGP_PROF_MASS_SETUP));
+        else if (!lumped)
             CGP_TRY(pcg<1>(c, Af, s.M, s.dinvM, s.div, s.qrot, &s.ks[KS_MASS], p.tol_mass, p.max_it_mass, true, false,
                            CGP_PROF_MASS_SETUP));
     }
     const bool one_launch = s.coarse_kind != CGP_COARSE_KERNELS;
     const int coarse_fixed = (one_launch ? 1 : 2 + (s.pure_neumann ? 2 : 0)) +
                              ((p.guess == CGP_GUESS_LEARNED && s.guess_ready) ? 9 : 0);
-    const int fixed = 4 + 1 + coarse_fixed + (s.lf - s.lc) + 1 + (lumped ? 0 : 2) + (p.chi ? 1 + (lumped ? 0 : 2) : 0) + 1;
+    // mixed: per refinement solve kIrSweeps x (residual, inner init, update), + the FP32 copy of A
+    const int ir_fixed = mixed ? 1 + 3 * kIrSweeps * (1 + (lumped ? 0 : 1) + (p.chi && !lumped ? 1 : 0)) : 0;
+    const int fixed =
+        4 + 1 + coarse_fixed + (s.lf - s.lc) + 1 + (lumped ? 0 : 2) + (p.chi ? 1 + (lumped ? 0 : 2) : 0) + 1 + ir_fixed;
     PL(c, CGP_PROF_FINISH,
        k_finish<<<gv, kBlock, 0, c.st>>>(F.nv, s.U, s.Uprev, s.Ut, s.delta, s.P, s.phi, s.qrot, p.chi, 1.0 / p.Re,
                                          s.tdev, p.dt, s.stats, s.ks, fixed, one_launch ? 0 : 1));
