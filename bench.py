@@ -163,6 +163,11 @@ def kernel_bytes(name, n, z, t=0):
                         + 16 * n + n,
         "mom_prep": 64 * n, "finish": 112 * n, "corr_rhs": 20 * z + 4 * n + 8 * n + n + 16 * n,
         "div": 20 * z + 4 * n + 16 * n + 8 * n,
+        # FP32 inner kernels of the mixed form: 4-byte values, vectors and Jacobi diagonal
+        "f32_corr_spmv": 8 * z + 4 * n + 32 * n, "f32_corr_update": 60 * n,
+        "f32_mass_spmv": 8 * z + 4 * n + 16 * n, "f32_mass_update": 32 * n,
+        "f32_bicg_v": 8 * z + 4 * n + 24 * n, "f32_bicg_t": 8 * z + 4 * n + 24 * n,
+        "f32_bicg_p": 44 * n, "f32_bicg_s": 36 * n, "f32_bicg_x": 64 * n, "to_f32": 12 * z + 12 * n,
     }
     return table.get(name)
 
@@ -200,7 +205,9 @@ def run_gpu(args, rank, world):
         torch.cuda.synchronize()
         t_asm = time.time() - t0
         s.step(warmup)
-        _, _, _, st0, _ = s.fields()
+        U0, P0, t0_sim, st0, _ = s.fields()
+        # state at the start of the timed region (fields and the previous increment the coarse guess uses)
+        start = (U0, s.vector(cg.CGP_VEC_UPREV), P0, t0_sim, s.vector(cg.CGP_VEC_PHI_C))
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         if world > 1:
             torch.distributed.barrier()
@@ -219,7 +226,7 @@ def run_gpu(args, rank, world):
         return s, {"ms": ms, "ms_per_step": ms / steps, "steps_per_s": 1000.0 * steps / ms, "iters": its,
                    "guess_used": st1["guess_used"] - st0["guess_used"],
                    "launches": st1["launches"] - st0["launches"], "status": rc,
-                   "res_poisson": st1["res_poisson"], "res_mom": st1["res_mom"], "assemble_s": t_asm,
+                   "res_poisson": st1["res_poisson"], "res_mom": st1["res_mom"], "assemble_s": t_asm, "start": start,
                    "clocks": clk.summary()}
 
     head_form = args.form
@@ -235,13 +242,15 @@ def run_gpu(args, rank, world):
                 forms[other] = {k: res[k] for k in keys}
                 s2.close()
 
-    # end to end through the C ABI: pinned host state in, one step, state out, every step
+    # end to end through the C ABI: pinned host state in, one step, state out, every step;
+    # it replays the first steps of the timed region from the state they started from
     Uh = torch.empty((nv_f, 2), dtype=torch.float64, pin_memory=True)
     Uph = torch.empty((nv_f, 2), dtype=torch.float64, pin_memory=True)
     Ph = torch.empty(nv_f, dtype=torch.float64, pin_memory=True)
-    U, P, tcur, _, _ = s.fields()
+    U, Uprev, P, tcur, phic = head["start"]
+    cg.cgp_set_vector(s.handle, cg.CGP_VEC_PHI_C, phic)
     Uh.numpy()[:] = U
-    Uph.numpy()[:] = s.vector(cg.CGP_VEC_UPREV)
+    Uph.numpy()[:] = Uprev
     Ph.numpy()[:] = P
     e2e_steps = max(1, min(args.steps, 20))
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -268,19 +277,39 @@ def run_gpu(args, rank, world):
         avg = tot / cnt
         kern[name] = {"launches": cnt, "total_ms": round(tot, 4), "avg_us": round(1000 * avg, 2),
                       "GBps": round(b / (avg * 1e-3) / 1e9, 1) if b else None}
-    dom = max(kern, key=lambda k: kern[k]["total_ms"] if kern[k]["GBps"] is not None else -1)
-    n, z, t = (nv_c, nnz_c, nt_c) if level_of(dom) == "coarse" else (nv_f, nnz_f, nt_f)
-    traffic = None
+    traffic_tab = {}
     tr_path = os.path.join(ROOT, "profiles", "traffic.json")
     if os.path.exists(tr_path):
         try:
-            traffic = json.load(open(tr_path)).get(args.workload, {}).get(dom)
+            traffic_tab = json.load(open(tr_path)).get(args.workload, {})
         except Exception:
-            traffic = None
-    roof = {"kernel": dom, "bound": "hbm", "achieved": kern[dom]["GBps"], "peak": peak, "unit": "GB/s",
-            "frac": round(kern[dom]["GBps"] / peak, 4), "traffic": traffic,
-            "bytes_per_launch": kernel_bytes(dom, n, z, t), "avg_launch_us": kern[dom]["avg_us"],
-            "peak_source": peak_kind}
+            traffic_tab = {}
+    # the dominant kernel with an HBM byte model, against the measured copy bandwidth
+    dom = max(kern, key=lambda k: kern[k]["total_ms"] if kern[k]["GBps"] is not None else -1)
+    n, z, t = (nv_c, nnz_c, nt_c) if level_of(dom) == "coarse" else (nv_f, nnz_f, nt_f)
+    roof_hbm = {"kernel": dom, "bound": "hbm", "achieved": kern[dom]["GBps"], "peak": peak, "unit": "GB/s",
+                "frac": round(kern[dom]["GBps"] / peak, 4), "traffic": traffic_tab.get(dom),
+                "bytes_per_launch": kernel_bytes(dom, n, z, t), "avg_launch_us": kern[dom]["avg_us"],
+                "peak_source": peak_kind}
+    roof = roof_hbm
+    # the one-launch coarse solve, when it dominates and runs on chip: its data lives in
+    # shared memory, so its roofline is the shared-memory bandwidth of the cluster's SMs
+    kind, ctas, cl = s.coarse_info()
+    top = max(kern, key=lambda k: kern[k]["total_ms"])
+    if top == "pois_onelaunch" and kind == cg.CGP_COARSE_ONCHIP:
+        _, _, _, stp, _ = s.fields()
+        its = max(1, stp["it_poisson"])
+        smem_bytes = its * (12 * nnz_c + 4 * nv_c)       # per inner iteration: entry (addr, value, z) + z store
+        avg_s = kern[top]["avg_us"] * 1e-6
+        sm_mhz = head["clocks"].get("sm_mhz") or 2070.0
+        smem_peak = 128.0 * cl * sm_mhz * 1e6 / 1e9       # GB/s: 128 B per clock per SM
+        ach = smem_bytes / avg_s / 1e9
+        roof = {"kernel": "k_pcg_onchip", "bound": "smem", "achieved": round(ach, 1), "peak": round(smem_peak, 1),
+                "unit": "GB/s", "frac": round(ach / smem_peak, 4), "traffic": traffic_tab.get(top),
+                "bytes_per_launch": smem_bytes, "avg_launch_us": kern[top]["avg_us"], "inner_iterations": its,
+                "us_per_iteration": round(kern[top]["avg_us"] / its, 3), "cluster_ctas": cl,
+                "peak_source": "derived: 128 B/clock/SM x %d SMs x %.0f MHz (median SM clock, timed region)"
+                               % (cl, sm_mhz)}
 
     # PCG iteration bandwidth on a synthetic Poisson problem far larger than L2
     pcg = None
@@ -301,7 +330,7 @@ def run_gpu(args, rank, world):
                    "coarse_vertices": nv_c, "k": w.k, "chi": w.chi, "Re": w.Re, "dt": w.dt,
                    "tol": w.tol_poisson, "parallelism": "replicas" if world > 1 else "single",
                    "l2": "working set %.2f GB > 129 MB L2 (no flush)" % (1e-9 * ws_bytes)},
-        "e2e": e2e, "gpu_launches": int(head["launches"]), "clocks": head["clocks"], "roofline": roof,
+        "e2e": e2e, "gpu_launches": int(head["launches"]), "clocks": head["clocks"], "roofline": roof, "roofline_hbm": roof_hbm,
         "forms": forms, "kernels": kern, "setup_s": {"mesh": round(t_mesh, 3), "assemble": round(head["assemble_s"], 3)},
         "pcg_hbm": pcg, "batch": batch,
     }
@@ -323,7 +352,8 @@ def pcg_bandwidth(cg, torch, n_side, peak):
     mesh = cg.Mesh(base.xy, base.tri, base.tag, lv)
     # the two-kernels-per-iteration PCG: the bandwidth-oriented path for coarse meshes far beyond L2
     prm = cg.make_params(1.0, 1.0, k=0, tol_poisson=1e-30, max_it_poisson=200, guess=cg.CGP_GUESS_ZERO,
-                         bc_kind=cg.CGP_BC_CAVITY, coarse_mode=cg.CGP_COARSE_KERNELS)
+                         bc_kind=cg.CGP_BC_CAVITY, coarse_mode=cg.CGP_COARSE_KERNELS, max_it_mom=20,
+                         max_it_mass=20)
     s = cg.Solver(mesh, prm)
     nf, nc, zf, zc = cg.cgp_solver_info(s.handle)
     rhs = np.random.default_rng(0).standard_normal(nc)
@@ -332,7 +362,11 @@ def pcg_bandwidth(cg, torch, n_side, peak):
     t0 = time.time()
     phi, it, rc = cg.cgp_poisson_solve(s.handle, rhs)
     wall = time.time() - t0
-    # per-kernel times of the same solve come from a profiled step of this solver
+    # per-kernel times come from a profiled step of this solver; a seeded random velocity
+    # field gives its Poisson problem a nonzero right-hand side, so all 200 iterations run
+    rng = np.random.default_rng(1)
+    U = rng.standard_normal((nf, 2))
+    cg.cgp_set_fields(s.handle, U, U, np.zeros(nf), 0.0)
     prof = cg.cgp_profile_step(s.handle)
     sp, up = prof.get("pois_spmv"), prof.get("pois_update")
     out = {"n": nc, "nnz": zc, "iters": it, "wall_ms_per_iter": round(1000 * wall / max(it, 1), 4)}

@@ -171,6 +171,7 @@ static int layout(Solver& s, void* base, size_t* bytes) {
         s.oc_ebase = cv.take<int32_t>(C.nslices);
         s.oc_soff = cv.take<int32_t>(kOnchipMaxCluster + 1);
         s.oc_send_off = cv.take<int32_t>(kOnchipMaxCluster + 1);
+        s.oc_halo_n = cv.take<int32_t>(kOnchipMaxCluster);
         s.oc_li = cv.take<int32_t>(nnzc);
         s.oc_src = cv.take<int32_t>(nnzc);
         s.oc_send_lr = cv.take<int32_t>(nnzc);     // sends <= entries with a remote column

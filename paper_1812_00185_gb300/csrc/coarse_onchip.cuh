@@ -53,6 +53,34 @@ __device__ __forceinline__ void oc_barrier() {
     asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
 
+// ---- mbarrier signalling of the FP32 reductions: remote st.async stores complete bytes on
+// the receiving CTA's mbarrier, so no fence or cluster barrier is needed per reduction
+__device__ __forceinline__ void oc_mbar_init(uint64_t* mb, int count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"((uint32_t)__cvta_generic_to_shared(mb)), "r"(count)
+                 : "memory");
+}
+__device__ __forceinline__ void oc_mbar_arrive_expect(uint64_t* mb, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(
+                     (uint32_t)__cvta_generic_to_shared(mb)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool oc_mbar_try(uint64_t* mb, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"((uint32_t)__cvta_generic_to_shared(mb)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ void oc_st_async(uint32_t addr, float v, uint32_t mbar) {
+    asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.b32 [%0], %1, [%2];" ::"r"(addr),
+                 "r"(__float_as_uint(v)), "r"(mbar)
+                 : "memory");
+}
+constexpr long long kOnchipWaitCycles = 4000000000LL;   // ~2 s: a wait this long means a lost signal
+
 // what warp 0 tells its CTA after an FP64 reduction
 struct OnchipScalars {
     int act;
@@ -67,6 +95,10 @@ static __global__ void __launch_bounds__(kOnchipThreads, 1) k_pcg_onchip(CoarseP
     __shared__ double wsum[kOnchipThreads / 32][4];
     __shared__ float wsum32[kOnchipThreads / 32][4];
     __shared__ OnchipScalars sc;
+    __shared__ __align__(8) uint64_t mbar[2];     // FP32 reductions, alternating
+    __shared__ uint32_t mbar_remote[kOnchipMaxCluster][2];
+    __shared__ float tot32[4];
+    __shared__ int abort_flag;
     const int rank = (int)cluster.block_rank(), ncl = (int)cluster.num_blocks();
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const SellView& A = a.A;
@@ -111,9 +143,21 @@ static __global__ void __launch_bounds__(kOnchipThreads, 1) k_pcg_onchip(CoarseP
     auto lrow_of = [&](int t) { return 32 * (wid + nw * t) + lane; };
     const int ns0 = __ldg(pl.send_off + rank), nsend = __ldg(pl.send_off + rank + 1) - ns0;
     for (int i = threadIdx.x; i < nsend; i += blockDim.x) {
-        const int d = __ldg(pl.send_dst + ns0 + i);
-        send[i] = make_uint2((uint32_t)__ldg(pl.send_lr + ns0 + i), oc_map(zl + rows_max + (d & 0xFFFF), d >> 16));
+        const int d = __ldg(pl.send_dst + ns0 + i);   // x: local row | destination rank << 16
+        send[i] = make_uint2((uint32_t)__ldg(pl.send_lr + ns0 + i) | ((uint32_t)(d >> 16) << 16),
+                             oc_map(zl + rows_max + (d & 0xFFFF), d >> 16));
     }
+    if (threadIdx.x == 0) {
+        oc_mbar_init(&mbar[0], 1);
+        oc_mbar_init(&mbar[1], 1);
+        abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (threadIdx.x < ncl) {
+        mbar_remote[threadIdx.x][0] = oc_map(&mbar[0], threadIdx.x);
+        mbar_remote[threadIdx.x][1] = oc_map(&mbar[1], threadIdx.x);
+    }
+    const int halo_self = __ldg(pl.halo_n + rank);
     // remote slot addresses of the reductions: lane l < ncl stores into CTA l
     const uint32_t red64_remote = oc_map(red64, lane < ncl ? lane : 0);
     const uint32_t red32_remote = oc_map(red32, lane < ncl ? lane : 0);
@@ -121,7 +165,7 @@ static __global__ void __launch_bounds__(kOnchipThreads, 1) k_pcg_onchip(CoarseP
     auto push = [&]() {
         for (int i = threadIdx.x; i < nsend; i += blockDim.x) {
             const uint2 sd = send[i];
-            oc_st32(sd.y, zl[sd.x]);
+            oc_st32(sd.y, zl[sd.x & 0xFFFF]);
         }
     };
     // Cluster sums.  Partial sums go warp -> CTA (warp 0) -> every CTA's slot array, one
@@ -154,25 +198,57 @@ static __global__ void __launch_bounds__(kOnchipThreads, 1) k_pcg_onchip(CoarseP
         }
         slot ^= 1;
     };
-    // FP32 (inner iterations): totals in every thread, each warp adding the slots itself;
-    // with `publish`, the CTA's new z also goes to the neighbours' halos before the barrier
-    auto cred32 = [&](float (&v)[2], int nr, float (&tot)[2], bool publish) {
+    // FP32 (inner iterations): the CTA partials travel as st.async stores into every CTA's
+    // slots, each completing bytes on that CTA's mbarrier (two, used alternately: data for
+    // reduction m+2 can only be sent once every CTA has contributed to m+1, that is after this
+    // CTA finished m); warp 0 waits (bounded) and adds the slots, the CTA reads the totals
+    // after a __syncthreads.  With `publish`, the CTA's new z goes to the neighbours' halos the
+    // same way (every CTA expects its halo size in bytes).  A wait that runs out sets the
+    // abort flag of every CTA; the solve then stops with CGP_ETIMEOUT.
+    int mred = 0;
+    auto cred32 = [&](float (&v)[2], int nr, float (&tot)[2], bool publish) -> bool {
         for (int k = 0; k < nr; ++k) {
             const float s = warp_sum(v[k]);
             if (lane == 0) wsum32[wid][k] = s;
         }
         __syncthreads();
-        if (publish) push();
-        if (wid == 0) {
-            for (int k = 0; k < nr; ++k) {
-                const float s = __shfl_sync(0xffffffffu, warp_sum(lane < nw ? wsum32[lane][k] : 0.0f), 0);
-                if (lane < ncl) oc_st32(red32_remote + (uint32_t)(4 * ((slot * 16 + rank) * 4 + k)), s);
+        const int par = mred & 1;
+        const uint32_t phase = (uint32_t)(mred >> 1) & 1u;
+        ++mred;
+        const bool live = abort_flag == 0;
+        if (publish && live) {
+            for (int i = threadIdx.x; i < nsend; i += blockDim.x) {
+                const uint2 sd = send[i];
+                oc_st_async(sd.y, zl[sd.x & 0xFFFF], mbar_remote[sd.x >> 16][par]);
             }
         }
-        oc_barrier();
-        for (int k = 0; k < nr; ++k)
-            tot[k] = __shfl_sync(0xffffffffu, warp_sum(lane < ncl ? red32[(slot * 16 + lane) * 4 + k] : 0.0f), 0);
-        slot ^= 1;
+        if (wid == 0) {
+            float cs[2] = {0.0f, 0.0f};
+            for (int k = 0; k < nr; ++k) cs[k] = __shfl_sync(0xffffffffu, warp_sum(lane < nw ? wsum32[lane][k] : 0.0f), 0);
+            if (live && lane < ncl)
+                for (int k = 0; k < nr; ++k)
+                    oc_st_async(red32_remote + (uint32_t)(4 * ((par * 16 + rank) * 4 + k)), cs[k], mbar_remote[lane][par]);
+            if (lane == 0) oc_mbar_arrive_expect(&mbar[par], (uint32_t)(4 * (nr * ncl + (publish ? halo_self : 0))));
+            bool ok = live;
+            if (ok) {
+                const long long t0 = clock64();
+                while (!oc_mbar_try(&mbar[par], phase)) {
+                    if (abort_flag || clock64() - t0 > kOnchipWaitCycles) {
+                        ok = false;
+                        break;
+                    }
+                }
+            }
+            ok = __all_sync(0xffffffffu, ok);
+            for (int k = 0; k < nr; ++k) {
+                const float t = __shfl_sync(0xffffffffu, warp_sum(lane < ncl ? red32[(par * 16 + lane) * 4 + k] : 0.0f), 0);
+                if (lane == 0) tot32[k] = t;
+            }
+            if (!ok && lane < ncl) asm volatile("st.shared::cluster.u32 [%0], 1;" ::"r"(oc_map(&abort_flag, lane)) : "memory");
+        }
+        __syncthreads();
+        for (int k = 0; k < nr; ++k) tot[k] = tot32[k];
+        return abort_flag == 0;
     };
     const double mean = a.project ? a.st->mean : 0.0;
     const double tol2 = a.tol2;
@@ -300,7 +376,7 @@ static __global__ void __launch_bounds__(kOnchipThreads, 1) k_pcg_onchip(CoarseP
         float rz = sc.rz0, beta = 0.0f, rr_best = INFINITY;
         const float stop2 = sc.stop2;
         int best_k = 0;
-        bool drift = false;
+        bool drift = false, aborted = false;
         for (int k = 0; iters < a.maxit; ++k) {
             // phase A: w = A z (local gathers), p = z + beta p, q = w + beta q, <p, q>
             const float be = beta;
@@ -332,7 +408,10 @@ static __global__ void __launch_bounds__(kOnchipThreads, 1) k_pcg_onchip(CoarseP
                 }
             }
             float pq[2];
-            cred32(pq_acc, 1, pq, false);
+            if (!cred32(pq_acc, 1, pq, false)) {
+                aborted = true;
+                break;
+            }
             if (!(pq[0] != 0.0f) || !isfinite(pq[0])) break;   // restart from the true residual
             const float al = rz / pq[0];
             // phase B (own rows): e += alpha p, r -= alpha q, z = D^{-1} r
@@ -349,7 +428,10 @@ static __global__ void __launch_bounds__(kOnchipThreads, 1) k_pcg_onchip(CoarseP
                 }
             }
             float t2[2];
-            cred32(acc2, 2, t2, true);
+            if (!cred32(acc2, 2, t2, true)) {
+                aborted = true;
+                break;
+            }
             ++iters;
             if (!isfinite(t2[0]) || !isfinite(t2[1])) {
                 drift = true;
@@ -368,6 +450,10 @@ static __global__ void __launch_bounds__(kOnchipThreads, 1) k_pcg_onchip(CoarseP
                 break;
             }
         }
+        if (aborted) {
+            status = CGP_ETIMEOUT;
+            break;
+        }
         // ---- x += ||r|| e (FP64) unless the FP32 recurrence drifted away
         if (!drift) {
             const double norm = sc.norm;
@@ -385,7 +471,7 @@ static __global__ void __launch_bounds__(kOnchipThreads, 1) k_pcg_onchip(CoarseP
         }
     }
     // ---- pure-Neumann mean fix
-    if (a.mlump) {
+    if (a.mlump && status != CGP_ETIMEOUT) {
         double acc[2] = {0.0, 0.0};
 #pragma unroll
         for (int t = 0; t < kOnchipRows; ++t) {

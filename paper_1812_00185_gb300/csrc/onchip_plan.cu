@@ -111,6 +111,7 @@ bool onchip_plan(int n, const std::vector<int32_t>& ptr, const std::vector<int32
         }
         P.ent_max = std::max<int64_t>(P.ent_max, eb - eb0);
         P.halo_max = std::max(P.halo_max, (int)halo.size());
+        P.halo_n.push_back((int32_t)halo.size());
     }
     if (P.halo_max >= (1 << 16)) return false;
     // ---- entry order of every slice (bank-aware) and the local index of each entry

@@ -23,6 +23,7 @@ struct OnchipPlan {
     const int32_t* send_lr;    // per send: own local row whose z goes out
     const int32_t* send_dst;   // per send: (destination rank << 16) | halo slot there
     const int32_t* send_off;   // ncl+1
+    const int32_t* halo_n;     // ncl: halo values each CTA receives per push
     int rows_max, halo_max, send_max, ent_max;
 };
 
@@ -30,7 +31,7 @@ struct OnchipHostPlan {
     int ncl = 0, rows_max = 0, halo_max = 0, send_max = 0;
     int64_t ent_max = 0;
     size_t bytes = 0;          // dynamic shared memory per CTA
-    std::vector<int32_t> slist, soff, ebase, li, src, send_lr, send_dst, send_off;
+    std::vector<int32_t> slist, soff, ebase, li, src, send_lr, send_dst, send_off, halo_n;
 };
 
 // Shared-memory layout of one CTA (byte offsets identical in every CTA):

@@ -68,7 +68,7 @@ struct Solver {
     size_t onchip_bytes = 0;      // mixed: shared memory per CTA of the on-chip cluster solve (0 = not used)
     // mixed: workspace arrays of the on-chip plan (sized for the coarse level) and its device view
     int32_t *oc_slist = nullptr, *oc_soff = nullptr, *oc_ebase = nullptr, *oc_li = nullptr, *oc_src = nullptr;
-    int32_t *oc_send_lr = nullptr, *oc_send_dst = nullptr, *oc_send_off = nullptr;
+    int32_t *oc_send_lr = nullptr, *oc_send_dst = nullptr, *oc_send_off = nullptr, *oc_halo_n = nullptr;
     OnchipPlan onchip{};
     unsigned int* bar_count = nullptr;   // grid barrier counter, followed by the error word
     int* bar_err = nullptr;

@@ -505,7 +505,8 @@ __global__ void k_to_f32_pair(int64_t n1, const double* __restrict__ a1, float* 
 // PCG with FP32 inner solves (mixed form); same contract as pcg<NC> without the projection
 template <int NC>
 static int pcg_mixed(Ctx& c, SellView A, const double* val, const float* valf, const double* dinv, const float* dinvf,
-                     double* b, double* x, KrylovState* ks, double tol, int maxit, bool zero_x, int pid) {
+                     double* b, double* x, KrylovState* ks, double tol, int maxit, bool zero_x, int pid, int spmv_id,
+                     int update_id) {
     Solver& s = *c.s;
     KrylovState* in = s.ks + KS_COUNT;
     const int gs = grid_rows(s, A.nslices * 32, 1), gv = grid_rows(s, A.n, 1);
@@ -523,14 +524,14 @@ static int pcg_mixed(Ctx& c, SellView A, const double* val, const float* valf, c
             return CGP_OK;
         };
         auto body = [&, gs, gv](cudaStream_t st, unsigned long long h) -> int {
-            PL(c, CGP_PROF_F32_SPMV,
+            PL(c, spmv_id,
                k_pcg_spmv<NC, float><<<gs, kBlock, 0, st>>>(A, valf, fz, fp0, fp1, fq, in, s.partials, s.tickets));
-            PL(c, CGP_PROF_F32_UPDATE,
+            PL(c, update_id,
                k_pcg_update<NC, float><<<gv, kBlock, 0, st>>>(A.n, dinvf, fe, fr, fz, fp1, fq, in, s.partials,
                                                               s.tickets, h));
-            PL(c, CGP_PROF_F32_SPMV,
+            PL(c, spmv_id,
                k_pcg_spmv<NC, float><<<gs, kBlock, 0, st>>>(A, valf, fz, fp1, fp0, fq, in, s.partials, s.tickets));
-            PL(c, CGP_PROF_F32_UPDATE,
+            PL(c, update_id,
                k_pcg_update<NC, float><<<gv, kBlock, 0, st>>>(A.n, dinvf, fe, fr, fz, fp0, fq, in, s.partials,
                                                               s.tickets, h));
             CGP_LAUNCH_CHECK();
@@ -671,9 +672,10 @@ int choose_coarse_solver(Solver& s) {
                 CGP_CUDA(up(s.oc_send_lr, P.send_lr));
                 CGP_CUDA(up(s.oc_send_dst, P.send_dst));
                 CGP_CUDA(up(s.oc_send_off, P.send_off));
+                CGP_CUDA(up(s.oc_halo_n, P.halo_n));
                 s.onchip = OnchipPlan{s.oc_slist, s.oc_soff, s.oc_ebase, s.oc_li, s.oc_src, s.oc_send_lr,
-                                      s.oc_send_dst, s.oc_send_off, P.rows_max, P.halo_max, P.send_max,
-                                      (int)P.ent_max};
+                                      s.oc_send_dst, s.oc_send_off, s.oc_halo_n, P.rows_max, P.halo_max,
+                                      P.send_max, (int)P.ent_max};
                 s.onchip_bytes = P.bytes;
                 s.cluster_size = cs;
                 break;
@@ -860,7 +862,7 @@ int step_post(Ctx& c) {
     const bool mixed = p.precision == CGP_MIXED;
     if (!lumped && mixed)
         CGP_TRY(pcg_mixed<2>(c, Af, s.M0, s.M0f, s.dinvM0, s.dinvM0f, s.g, s.delta, &s.ks[KS_CORR], p.tol_mass,
-                             p.max_it_mass, true, CGP_PROF_CORR_SETUP));
+                             p.max_it_mass, true, CGP_PROF_CORR_SETUP, CGP_PROF_F32_CORR_SPMV, CGP_PROF_F32_CORR_UPDATE));
     else if (!lumped)
         CGP_TRY(pcg<2>(c, Af, s.M0, s.dinvM0, s.g, s.delta, &s.ks[KS_CORR], p.tol_mass, p.max_it_mass, true, false,
                        CGP_PROF_CORR_SETUP));
@@ -871,7 +873,8 @@ int step_post(Ctx& c) {
         CGP_LAUNCH_CHECK();
         if (!lumped && mixed)
             CGP_TRY(pcg_mixed<1>(c, Af, s.M, s.Mf, s.dinvM, s.dinvMf, s.div, s.qrot, &s.ks[KS_MASS], p.tol_mass,
-                                 p.max_it_mass, true, CGP_PROF_MASS_SETUP));
+                                 p.max_it_mass, true, CGP_PROF_MASS_SETUP, CGP_PROF_F32_MASS_SPMV,
+                                 CGP_PROF_F32_MASS_UPDATE));
         else if (!lumped)
             CGP_TRY(pcg<1>(c, Af, s.M, s.dinvM, s.div, s.qrot, &s.ks[KS_MASS], p.tol_mass, p.max_it_mass, true, false,
                            CGP_PROF_MASS_SETUP));
