@@ -609,6 +609,7 @@ int choose_coarse_solver(Solver& s) {
     const bool allow_rr = mode == CGP_COARSE_PERSISTENT;
     if (mode == CGP_COARSE_PERSISTENT_MEM) mode = CGP_COARSE_PERSISTENT;
     s.coarse_kind = mode;
+    s.coarse_fp64 = p.precision == CGP_FP64;
     s.cluster_size = 0;
     s.coarse_grid = 0;
     if (mode == CGP_COARSE_KERNELS) {
@@ -696,6 +697,11 @@ int choose_coarse_solver(Solver& s) {
             CGP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_rr, k_pcg_grid_rr, kGridThreads, 0));
             s.coarse_rr = wmax <= kRRWidth && per_sm_rr > 0 && rr_ctas_needed(C.nslices) <= sms * per_sm_rr;
         }
+        // mixed form, AUTO, no room on chip: the grid-wide FP64 solve (one reduction per
+        // iteration) is faster on this GPU than the FP32 inner solve (two) with the same grid
+        // barriers; the fine-level solves stay FP32-inner.  An explicit PERSISTENT request
+        // keeps the FP32 inner solve.
+        s.coarse_fp64 = p.precision == CGP_FP64 || (p.coarse_mode == CGP_COARSE_AUTO && !s.onchip_bytes);
         return CGP_OK;
     }
     CGP_CUDA(cudaFuncSetAttribute(k_pcg_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
@@ -740,7 +746,7 @@ CoarsePcgArgs coarse_args(Solver& s) {
     a.maxit = s.prm.max_it_poisson;
     a.zero_x = s.prm.guess == CGP_GUESS_ZERO;
     a.project = s.pure_neumann;
-    a.mixed = s.prm.precision == CGP_MIXED;
+    a.mixed = !s.coarse_fp64;
     a.max_outer = 50;
     a.bar_count = s.bar_count;
     a.bar_err = s.bar_err;
@@ -781,7 +787,7 @@ static int coarse_solve(Ctx& c) {
         }
         CGP_CUDA(cudaMemsetAsync(s.bar_count, 0, 2 * sizeof(unsigned int), c.st));   // counter + error word
         cudaLaunchConfig_t cfg = {};
-        const bool rr = s.coarse_rr && s.prm.precision == CGP_FP64;
+        const bool rr = s.coarse_rr && s.coarse_fp64;
         cfg.gridDim = dim3(rr ? rr_ctas_needed(C.nslices) : s.coarse_grid, 1, 1);
         cfg.blockDim = dim3(kGridThreads, 1, 1);
         cfg.stream = c.st;
@@ -1179,7 +1185,7 @@ extern "C" int cgp_coarse_info(const cgp_solver* h, int32_t* kind, int32_t* ctas
         if (s.onchip_bytes) {
             k = CGP_COARSE_ONCHIP;
             n = cl = s.cluster_size;
-        } else if (s.coarse_rr && s.prm.precision == CGP_FP64) {
+        } else if (s.coarse_rr && s.coarse_fp64) {
             n = rr_ctas_needed(s.mesh->lev[s.lc].nslices);
         } else {
             k = CGP_COARSE_PERSISTENT_MEM;

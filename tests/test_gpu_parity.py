@@ -255,8 +255,28 @@ def test_coarse_solver_choice(cg):
     assert k == cg.CGP_COARSE_PERSISTENT_MEM and n > 0 and c == 0
     k, n, c = info(precision=cg.CGP_MIXED)              # mixed default: on-chip cluster solve
     assert k == cg.CGP_COARSE_ONCHIP and n == c and c in (8, 16)
+    k, n, c = info(precision=cg.CGP_MIXED, coarse_mode=cg.CGP_COARSE_PERSISTENT)   # FP32 inner in memory
+    assert k == cg.CGP_COARSE_PERSISTENT_MEM and n > 0 and c == 0
     with pytest.raises(RuntimeError):
         info(coarse_mode=cg.CGP_COARSE_ONCHIP)          # the on-chip solve is FP32: mixed form only
     with pytest.raises(RuntimeError):
         info(precision=cg.CGP_MIXED, coarse_mode=cg.CGP_COARSE_KERNELS)
     m.close()
+
+
+def test_mixed_falls_back_to_fp64_coarse_when_off_chip(cg):
+    # a coarse system larger than one cluster can hold: AUTO keeps the mixed form's FP32-inner
+    # fine solves and runs the grid-wide FP64 coarse solve
+    w = WORKLOADS["cavity512_k1"]
+    base = w.base_mesh()
+    m = cg.Mesh(base.xy, base.tri, base.tag, w.n_levels)
+    s = cg.Solver(m, cg.make_params(w.Re, w.dt, chi=w.chi, k=w.k, precision=cg.CGP_MIXED))
+    assert s.coarse_info()[0] in (cg.CGP_COARSE_PERSISTENT, cg.CGP_COARSE_PERSISTENT_MEM)
+    ref = cg.Solver(m, cg.make_params(w.Re, w.dt, chi=w.chi, k=w.k, precision=cg.CGP_MIXED,
+                                      coarse_mode=cg.CGP_COARSE_PERSISTENT))
+    assert ref.coarse_info()[0] == cg.CGP_COARSE_PERSISTENT_MEM
+    ref.close()
+    s.step(2)
+    U, P, t, st, rc = s.fields()
+    assert rc == 0 and np.isfinite(U).all() and st["res_poisson"] <= 1.0001e-8
+    s.close(); m.close()
