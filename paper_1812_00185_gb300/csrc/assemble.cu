@@ -172,8 +172,8 @@ static int layout(Solver& s, void* base, size_t* bytes) {
         s.oc_soff = cv.take<int32_t>(kOnchipMaxCluster + 1);
         s.oc_send_off = cv.take<int32_t>(kOnchipMaxCluster + 1);
         s.oc_halo_n = cv.take<int32_t>(kOnchipMaxCluster);
-        s.oc_li = cv.take<int32_t>(nnzc);
-        s.oc_src = cv.take<int32_t>(nnzc);
+        s.oc_li = cv.take<int32_t>(nnzc + (size_t)96 * C.nslices);   // + padding to 4-entry steps
+        s.oc_src = cv.take<int32_t>(nnzc + (size_t)96 * C.nslices);
         s.oc_send_lr = cv.take<int32_t>(nnzc);     // sends <= entries with a remote column
         s.oc_send_dst = cv.take<int32_t>(nnzc);
         s.Af = cv.take<float>(nnzf);

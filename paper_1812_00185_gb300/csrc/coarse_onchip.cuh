@@ -7,7 +7,8 @@
 // (onchip_plan.cu) gives each CTA a spatially compact set of SELL-32 slices.  Each CTA keeps
 // in its shared memory:
 //   * z for its own rows followed by a halo: z of the other CTAs' rows that its rows use;
-//   * its slices of the FP32 matrix, each entry's column as the shared address of that z;
+//   * its slices of the FP32 matrix, each entry as (index of its column's z, value), widths
+//     padded to whole 4-entry steps;
 //   * a send list: after z changes, every CTA stores the z its neighbours need straight
 //     into their halos (remote shared-memory stores), before the barrier of the reduction
 //     that follows, so every gather of the SpMV is a local shared-memory load;
@@ -42,11 +43,6 @@ __device__ __forceinline__ void oc_st(uint32_t addr, double v) {
 }
 __device__ __forceinline__ void oc_st32(uint32_t addr, float v) {
     asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(addr), "f"(v) : "memory");
-}
-__device__ __forceinline__ float oc_lds(uint32_t addr) {
-    float v;
-    asm volatile("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(addr) : "memory");
-    return v;
 }
 // all threads of all CTAs of the cluster; orders shared and global memory at cluster scope
 __device__ __forceinline__ void oc_barrier() {
@@ -107,11 +103,9 @@ static __global__ void __launch_bounds__(kOnchipThreads, 1) k_pcg_onchip(CoarseP
     double* red64 = reinterpret_cast<double*>(smem + onchip_z_bytes(rows_max, pl.halo_max));
     float* red32 = reinterpret_cast<float*>(red64 + 128);
     uint2* send = reinterpret_cast<uint2*>(red32 + 128);
-    uint32_t* caddr = reinterpret_cast<uint32_t*>(send + pl.send_max);
+    uint2* cent = reinterpret_cast<uint2*>(send + pl.send_max);   // (local index of z, value bits)
     const int q0 = __ldg(pl.soff + rank), nsl = __ldg(pl.soff + rank + 1) - q0;
     const int eb0 = nsl > 0 ? __ldg(pl.ebase + q0) : 0;
-    float* cval = reinterpret_cast<float*>(caddr + pl.ent_max);
-    const uint32_t z_sh = (uint32_t)__cvta_generic_to_shared(zl);
     for (int i = threadIdx.x; i < zn; i += blockDim.x) zl[i] = 0.0f;
     // ---- rows of this thread: list positions wid + nw * t of its CTA (a warp owns whole
     // slices); their matrix entries are copied to shared memory by the owning warp
@@ -128,11 +122,11 @@ static __global__ void __launch_bounds__(kOnchipThreads, 1) k_pcg_onchip(CoarseP
             const int sl = __ldg(pl.slist + q0 + q);
             slice_[t] = sl;
             base_[t] = __ldg(pl.ebase + q0 + q) - eb0;
-            width_[t] = (__ldg(A.ptr + sl + 1) - __ldg(A.ptr + sl)) >> 5;
+            width_[t] = onchip_width4((__ldg(A.ptr + sl + 1) - __ldg(A.ptr + sl)) >> 5);
             for (int k = 0; k < width_[t]; ++k) {
                 const int el = base_[t] + 32 * k + lane;
-                caddr[el] = z_sh + 4u * (uint32_t)__ldg(pl.li + eb0 + el);
-                cval[el] = __ldg(a.valf + __ldg(pl.src + eb0 + el));
+                const int src = __ldg(pl.src + eb0 + el);
+                cent[el] = make_uint2((uint32_t)__ldg(pl.li + eb0 + el), src >= 0 ? __float_as_uint(__ldg(a.valf + src)) : 0u);
             }
         }
     }
@@ -384,22 +378,16 @@ static __global__ void __launch_bounds__(kOnchipThreads, 1) k_pcg_onchip(CoarseP
 #pragma unroll
             for (int t = 0; t < kOnchipRows; ++t) {
                 if (t >= nrow) break;
-                const int b = base_[t] + lane, w = width_[t];
+                const uint2* ce = cent + base_[t] + lane;
+                const int w = width_[t];
                 float s = 0.0f;
-                for (int k0 = 0; k0 < w; k0 += 8) {
-                    uint32_t ad[8];
-                    float v[8];
-#pragma unroll
-                    for (int u = 0; u < 8; ++u) {
-                        const bool in = k0 + u < w;
-                        ad[u] = in ? caddr[b + 32 * (k0 + u)] : z_sh;
-                        v[u] = in ? cval[b + 32 * (k0 + u)] : 0.0f;
-                    }
-                    float g[8];
-#pragma unroll
-                    for (int u = 0; u < 8; ++u) g[u] = oc_lds(ad[u]);
-#pragma unroll
-                    for (int u = 0; u < 8; ++u) s = fmaf(v[u], g[u], s);
+                for (int k = 0; k < w; k += 4) {
+                    const uint2 e0 = ce[32 * k], e1 = ce[32 * (k + 1)], e2 = ce[32 * (k + 2)], e3 = ce[32 * (k + 3)];
+                    const float g0 = zl[e0.x], g1 = zl[e1.x], g2 = zl[e2.x], g3 = zl[e3.x];
+                    s = fmaf(__uint_as_float(e0.y), g0, s);
+                    s = fmaf(__uint_as_float(e1.y), g1, s);
+                    s = fmaf(__uint_as_float(e2.y), g2, s);
+                    s = fmaf(__uint_as_float(e3.y), g3, s);
                 }
                 if (row_of(t) >= 0) {
                     p_[t] = fmaf(be, p_[t], z_[t]);

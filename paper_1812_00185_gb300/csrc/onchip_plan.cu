@@ -8,7 +8,9 @@
 // their centroids into equal-count groups: each CTA owns a compact region and only values
 // along region boundaries cross the cluster.  Within a slice, the order of each row's
 // entries is chosen so that the 32 lanes of a gather step hit distinct shared-memory banks
-// where possible (the sum a row forms is the same up to FP32 rounding order).
+// where possible (the sum a row forms is the same up to FP32 rounding order), and each
+// slice's width is padded to a multiple of 4 (padding entries read the row's own z with a
+// zero value), so the SpMV runs in 4-entry steps without bounds tests.
 #include <algorithm>
 #include <numeric>
 #include <unordered_map>
@@ -80,12 +82,9 @@ bool onchip_plan(int n, const std::vector<int32_t>& ptr, const std::vector<int32
     P.ncl = ncl;
     P.rows_max = 32 * smax;
     // ---- local indices, halos, sends
-    const int64_t E = ptr[S];
     P.ebase.resize(S);
-    P.li.assign(E, 0);
-    P.src.assign(E, 0);
     std::vector<std::vector<std::pair<int, int>>> sends(ncl);   // per owner: (local row, dest rank << 16 | slot)
-    std::vector<int> halo_of(E, -1);
+    std::vector<int> halo_of(ptr[S], -1);
     int64_t eb = 0;
     for (int c = 0; c < ncl; ++c) {
         std::unordered_map<int, int> halo;
@@ -93,7 +92,7 @@ bool onchip_plan(int n, const std::vector<int32_t>& ptr, const std::vector<int32
         for (int q = P.soff[c]; q < P.soff[c + 1]; ++q) {
             const int s = P.slist[q];
             P.ebase[q] = (int32_t)eb;
-            eb += ptr[s + 1] - ptr[s];
+            eb += 32 * onchip_width4((ptr[s + 1] - ptr[s]) >> 5);
             for (int64_t e = ptr[s]; e < ptr[s + 1]; ++e) {
                 const int j = col[e], o = part[j >> 5];
                 if (o == c) continue;
@@ -114,6 +113,8 @@ bool onchip_plan(int n, const std::vector<int32_t>& ptr, const std::vector<int32
         P.halo_n.push_back((int32_t)halo.size());
     }
     if (P.halo_max >= (1 << 16)) return false;
+    P.li.assign(eb, 0);
+    P.src.assign(eb, -1);
     // ---- entry order of every slice (bank-aware) and the local index of each entry
     std::vector<int> lidx(32 * 64), order(32 * 64);
     for (int q = 0; q < S; ++q) {
@@ -150,13 +151,19 @@ bool onchip_plan(int n, const std::vector<int32_t>& ptr, const std::vector<int32
                 if (bank_addr[a & 31] < 0) bank_addr[a & 31] = a;
             }
         }
-        for (int lane = 0; lane < 32; ++lane)
+        for (int lane = 0; lane < 32; ++lane) {
             for (int k = 0; k < w; ++k) {
                 const int m = order[lane * w + k];
                 const int64_t dst = P.ebase[q] + 32 * k + lane;
                 P.src[dst] = (int32_t)(ptr[s] + 32 * m + lane);
                 P.li[dst] = lidx[lane * w + m];
             }
+            for (int k = w; k < onchip_width4(w); ++k) {   // padding: own row, value 0
+                const int64_t dst = P.ebase[q] + 32 * k + lane;
+                P.src[dst] = -1;
+                P.li[dst] = 32 * pos[s] + lane;
+            }
+        }
     }
     P.send_off.assign(ncl + 1, 0);
     for (int c = 0; c < ncl; ++c) {

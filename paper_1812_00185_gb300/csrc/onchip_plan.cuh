@@ -12,6 +12,9 @@ constexpr int kOnchipThreads = 512;       // 16 warps, up to 128 registers a thr
 constexpr int kOnchipRows = 6;            // most slices (rows) a warp (thread) may own
 constexpr int kOnchipMaxCluster = 16;
 
+// slice width rounded up to whole 4-entry SpMV steps
+__host__ __device__ __forceinline__ int onchip_width4(int w) { return (w + 3) & ~3; }
+
 // Device copy of the plan (arrays in the solver workspace).  Slices are listed CTA by CTA;
 // "list position" q indexes slist / ebase, and local entries are numbered over all CTAs.
 struct OnchipPlan {
@@ -19,7 +22,7 @@ struct OnchipPlan {
     const int32_t* soff;       // ncl+1: list positions of CTA c are soff[c] .. soff[c+1]-1
     const int32_t* ebase;      // per list position: first local entry of the slice
     const int32_t* li;         // per local entry: index into the CTA's z (own rows, then halo)
-    const int32_t* src;        // per local entry: the SELL entry it holds
+    const int32_t* src;        // per local entry: the SELL entry it holds, -1 for padding
     const int32_t* send_lr;    // per send: own local row whose z goes out
     const int32_t* send_dst;   // per send: (destination rank << 16) | halo slot there
     const int32_t* send_off;   // ncl+1
@@ -36,7 +39,8 @@ struct OnchipHostPlan {
 
 // Shared-memory layout of one CTA (byte offsets identical in every CTA):
 //   z[rows_max + halo_max] (float, padded to 16 bytes) | red64[2][16][4] double |
-//   red32[2][16][4] float | send[send_max] (local row, cluster address) | addr[ent] | val[ent]
+//   red32[2][16][4] float | send[send_max] (local row, cluster address) | entry[ent] (local
+//   index of the column's z, FP32 value bits)
 __host__ __device__ __forceinline__ size_t onchip_z_bytes(int rows_max, int halo_max) {
     return (size_t)4 * (((size_t)rows_max + halo_max + 3) & ~(size_t)3);
 }
