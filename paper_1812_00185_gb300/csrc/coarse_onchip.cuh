@@ -272,30 +272,56 @@ static __global__ void __launch_bounds__(kOnchipThreads, 1) k_pcg_onchip(CoarseP
     bool converged = false;
     double tot[4];
     if (a.x_alt && !a.zero_x) {
-        double acc[2] = {0.0, 0.0};
+        // second initial guess y (the learned prediction): start from the combination
+        // c1 x + c2 y that minimises the A-norm of the error over span{x, y} (a 2x2 Galerkin
+        // system), which is what CG's work depends on; never worse than x or y alone
+        double g[3] = {0.0, 0.0, 0.0}, f[2] = {0.0, 0.0};   // xAx, xAy, yAy; x.b, y.b
 #pragma unroll
         for (int t = 0; t < kOnchipRows; ++t) {
             if (t >= nrow) break;
-            const double ax = row_a(t, xv, false), aa = row_a(t, a.x_alt, true);
+            const double ax = row_a(t, xv, false), ay = row_a(t, a.x_alt, true);
             const int i = row_of(t);
             if (i >= 0) {
-                const double bi = ldcg(a.b + i);
-                acc[0] += (bi - ax) * (bi - ax);
-                acc[1] += (bi - aa) * (bi - aa);
+                const double xi = ldcg(xv + i), yi = __ldg(a.x_alt + i), bi = ldcg(a.b + i);
+                g[0] += xi * ax;
+                g[1] += xi * ay;
+                g[2] += yi * ay;
+                f[0] += xi * bi;
+                f[1] += yi * bi;
             }
         }
-        cred64(acc, tot);
-        if (threadIdx.x == 0) sc.act = tot[1] < tot[0];
+        cred64(g, tot);
+        double gt[3] = {tot[0], tot[1], tot[2]};
+        cred64(f, tot);
+        if (threadIdx.x == 0) {
+            const double a11 = gt[0], a12 = gt[1], a22 = gt[2], f1 = tot[0], f2 = tot[1];
+            const double det = a11 * a22 - a12 * a12;
+            double c1 = 1.0, c2 = 0.0;
+            if (isfinite(det) && det > 1e-12 * fabs(a11 * a22) && a11 > 0.0 && a22 > 0.0) {
+                c1 = (f1 * a22 - f2 * a12) / det;
+                c2 = (a11 * f2 - a12 * f1) / det;
+            } else if (a22 > 0.0 && isfinite(f2) && (!(a11 > 0.0) || f2 * f2 / a22 > f1 * f1 / a11)) {
+                c1 = 0.0;                        // x and y (nearly) parallel, or x = 0: the better one, scaled
+                c2 = f2 / a22;
+            } else if (a11 > 0.0 && isfinite(f1)) {
+                c1 = f1 / a11;
+            }
+            if (!isfinite(c1) || !isfinite(c2)) {
+                c1 = 1.0;
+                c2 = 0.0;
+            }
+            sc.inv = c1;
+            sc.norm = c2;
+        }
         __syncthreads();
-        if (sc.act) {
-            used_alt = 1;
+        const double c1 = sc.inv, c2 = sc.norm;
+        used_alt = c2 != 0.0;
 #pragma unroll
-            for (int t = 0; t < kOnchipRows; ++t) {
-                const int i = row_of(t);
-                if (i >= 0) __stcg(xv + i, __ldg(a.x_alt + i));
-            }
-            oc_barrier();
+        for (int t = 0; t < kOnchipRows; ++t) {
+            const int i = row_of(t);
+            if (i >= 0) __stcg(xv + i, c1 * ldcg(xv + i) + c2 * __ldg(a.x_alt + i));
         }
+        oc_barrier();
     }
     double bb = 0.0, rr_final = 0.0;   // meaningful in warp 0
     enum { kInner = 0, kConverged, kNonfinite, kNotconv };

@@ -21,12 +21,13 @@
 namespace cgp {
 
 // ---------------------------------------------------------------- forward kernels
-// per-sample RMS of r and q (one block per sample)
+// per-sample RMS of r and q: kScaleBlocks blocks per sample write partial sums of squares,
+// then one warp per sample adds them in block order (deterministic)
 __global__ void __launch_bounds__(kBlock) k_mlp_scales(int n, const double* __restrict__ r, const double* __restrict__ q,
-                                                     float* __restrict__ scale) {
-    const int b = blockIdx.x;
+                                                     double* __restrict__ spart) {
+    const int b = blockIdx.y;
     double a0 = 0.0, a1 = 0.0;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const double rv = r[(size_t)b * n + i], qv = q[(size_t)b * n + i];
         a0 += rv * rv;
         a1 += qv * qv;
@@ -46,6 +47,21 @@ __global__ void __launch_bounds__(kBlock) k_mlp_scales(int n, const double* __re
             s0 += sm[w][0];
             s1 += sm[w][1];
         }
+        spart[((size_t)b * gridDim.x + blockIdx.x) * 2] = s0;
+        spart[((size_t)b * gridDim.x + blockIdx.x) * 2 + 1] = s1;
+    }
+}
+
+__global__ void k_mlp_scales_fin(int n, int nblk, const double* __restrict__ spart, float* __restrict__ scale) {
+    const int b = blockIdx.x, lane = threadIdx.x;
+    double s0 = 0.0, s1 = 0.0;
+    for (int k = lane; k < nblk; k += 32) {
+        s0 += spart[((size_t)b * nblk + k) * 2];
+        s1 += spart[((size_t)b * nblk + k) * 2 + 1];
+    }
+    s0 = warp_sum(s0);
+    s1 = warp_sum(s1);
+    if (lane == 0) {
         const double sr = sqrt(s0 / n), sq = sqrt(s1 / n);
         scale[2 * b] = sr > 0.0 ? (float)sr : 1.0f;
         scale[2 * b + 1] = sq > 0.0 ? (float)sq : 1.0f;
@@ -324,6 +340,7 @@ void MlpBuffers::carve(Carve& cv, int n_, int batch) {
     maxb = batch;
     const size_t nb = (size_t)n * batch;
     scale = cv.take<float>(2 * (size_t)batch);
+    spart = cv.take<double>(2 * (size_t)kScaleBlocks * batch);
     h0 = cv.take<float>(4 * nb);
     m0 = cv.take<float>(4 * nb);
     a1 = cv.take<float>(kHid * nb);
@@ -340,7 +357,8 @@ int mlp_forward(const MlpBuffers& B, const Level& L, const double* r, const doub
     const int n = B.n;
     const int64_t nb = (int64_t)n * batch;
     const int g = blocks_for(nb), g128 = blocks_for(nb, 128);
-    k_mlp_scales<<<batch, kBlock, 0, st>>>(n, r, q, B.scale);
+    k_mlp_scales<<<dim3(kScaleBlocks, batch), kBlock, 0, st>>>(n, r, q, B.spart);
+    k_mlp_scales_fin<<<batch, 32, 0, st>>>(n, kScaleBlocks, B.spart, B.scale);
     k_mlp_features<<<g, kBlock, 0, st>>>(n, batch, r, q, L.xy, B.scale, B.h0);
     k_mlp_nmean<4, false><<<g, kBlock, 0, st>>>(n, batch, L.rowptr, L.col, B.h0, B.m0);
     k_mlp_dense<4, kHid, false><<<g128, 128, 0, st>>>(n, batch, B.params_bf + kOffW1, B.params + kOffB1, B.h0, B.m0,

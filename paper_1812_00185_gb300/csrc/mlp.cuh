@@ -19,9 +19,12 @@ constexpr int kOffW3 = kOffB2 + kHid;
 constexpr int kOffB3 = kOffW3 + 2 * kHid;
 constexpr int kMlpParams = kOffB3 + 1;
 
+constexpr int kScaleBlocks = 64;   // blocks per sample of the RMS reduction
+
 struct MlpBuffers {
     int n = 0, maxb = 0;
     float* scale = nullptr;                     // [batch][2]: RMS of r and q
+    double* spart = nullptr;                    // [batch][kScaleBlocks][2]: block partial sums of r^2, q^2
     float *h0 = nullptr, *m0 = nullptr;         // [batch][4][n]
     float *a1 = nullptr, *m1 = nullptr;         // [batch][64][n] pre-activations / neighbour means
     float *a2 = nullptr, *m2 = nullptr;

@@ -887,7 +887,7 @@ int step_post(Ctx& c) {
     }
     const bool one_launch = s.coarse_kind != CGP_COARSE_KERNELS;
     const int coarse_fixed = (one_launch ? 1 : 2 + (s.pure_neumann ? 2 : 0)) +
-                             ((p.guess == CGP_GUESS_LEARNED && s.guess_ready) ? 9 : 0);
+                             ((p.guess == CGP_GUESS_LEARNED && s.guess_ready) ? 10 : 0);
     // mixed: per refinement solve kIrSweeps x (residual, inner init, update), + the FP32 copy of A
     const int ir_fixed = mixed ? 1 + 3 * kIrSweeps * (1 + (lumped ? 0 : 1) + (p.chi && !lumped ? 1 : 0)) : 0;
     const int fixed =
