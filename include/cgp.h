@@ -55,7 +55,10 @@ enum {
     CGP_BC_CAVITY = 0,       /* [0,1]^2, u=(bc_param[0],0) on y=1 with 0<x<1, u=0 on the rest of the boundary */
     CGP_BC_CHANNEL = 1,      /* u=(4 Umax y(H-y)/H^2, 0) on x=0 (Umax=bc_param[0], H=bc_param[1]), u=0 elsewhere on VEL_DIR */
     CGP_BC_TG = 2,           /* Taylor-Green vortex, paper Eqs. 28-30 */
-    CGP_BC_TG_PERIODIC = 3   /* Taylor-Green with amplitude cos(2 pi t) and the body force that makes it exact */
+    CGP_BC_TG_PERIODIC = 3,  /* Taylor-Green with amplitude cos(2 pi t) and the body force that makes it exact */
+    CGP_BC_USER = 4          /* caller's data: the Dirichlet velocity of every VEL_DIR vertex and the body force
+                                f of Eq. 21 at t^{n+1}, given by cgp_set_dirichlet / cgp_set_forcing before
+                                each step (both zero until set; they keep their values between steps) */
 };
 enum { CGP_FP64 = 0, CGP_MIXED = 1 };                   /* precision of the coarse Poisson solve */
 /* initial guess of the coarse Poisson solve: zero, the previous step's increment, or the
@@ -153,6 +156,12 @@ int cgp_workspace_size(const cgp_mesh* mesh, const cgp_params* params, size_t* b
  * cgp_workspace_size bytes that must outlive the solver.  The mesh must outlive it too. */
 int cgp_assemble(const cgp_mesh* mesh, const cgp_params* params, void* workspace, size_t ws_bytes,
                  cgp_stream_t stream, cgp_solver** out);
+/* CGP_BC_USER only (CGP_EINVAL otherwise): the velocity imposed on the VEL_DIR vertices
+ * and the nodal body force used by the next steps, each 2*N_f doubles (u, v interleaved,
+ * fine-level vertex order; entries of non-VEL_DIR vertices of uD are ignored).  Host
+ * arrays synchronise; device arrays are copied on `stream`. */
+int cgp_set_dirichlet(cgp_solver* s, const double* uD, int32_t where, cgp_stream_t stream);
+int cgp_set_forcing(cgp_solver* s, const double* F, int32_t where, cgp_stream_t stream);
 /* Replace the state: U (2*N_f), Uprev (2*N_f, may be NULL = U), P (N_f), time t. */
 int cgp_set_fields(cgp_solver* s, const double* U, const double* Uprev, const double* P, double t,
                    int32_t where, cgp_stream_t stream);
@@ -275,6 +284,13 @@ int cgp_mlp_train_step(cgp_mlp* m, const double* r, const double* q, const doubl
 /* Copy the network's weights into a solver assembled with guess = CGP_GUESS_LEARNED whose
  * pressure-increment level is the network's level.  Synchronises. */
 int cgp_guess_set(cgp_solver* s, const cgp_mlp* m, cgp_stream_t stream);
+/* Training data for the learned guess, generated by the solver itself: advances n_steps
+ * steps (as cgp_step) and stores, for step k, row k (N_c values) of rhs = the right-hand
+ * side of Eq. 23, prev = the increment Phi_c before the step (the network's second input)
+ * and target = the increment Phi_c the coarse solve produced.  Arrays of n_steps * N_c
+ * doubles, host or device (where); host: synchronises, device: asynchronous on stream. */
+int cgp_record_pairs(cgp_solver* s, int32_t n_steps, double* rhs, double* prev, double* target, int32_t where,
+                     cgp_stream_t stream);
 void cgp_mlp_destroy(cgp_mlp* m);
 
 /* ---- allocation-free solve (the paper has no counterpart) ----

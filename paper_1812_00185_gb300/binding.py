@@ -17,7 +17,7 @@ from . import build as _build
 CGP_OK, CGP_EINVAL, CGP_ENOTCONV, CGP_EBREAKDOWN, CGP_ENONFINITE, CGP_ETIMEOUT, CGP_ECUDA, CGP_ENOMEM = \
     0, -1, -2, -3, -4, -5, -6, -7
 CGP_VEL_DIR, CGP_PHI_ZERO = 1, 2
-CGP_BC_CAVITY, CGP_BC_CHANNEL, CGP_BC_TG, CGP_BC_TG_PERIODIC = 0, 1, 2, 3
+CGP_BC_CAVITY, CGP_BC_CHANNEL, CGP_BC_TG, CGP_BC_TG_PERIODIC, CGP_BC_USER = 0, 1, 2, 3, 4
 CGP_FP64, CGP_MIXED = 0, 1
 CGP_GUESS_ZERO, CGP_GUESS_PREV, CGP_GUESS_LEARNED = 0, 1, 2
 CGP_MASS_CONSISTENT, CGP_MASS_LUMPED = 0, 1
@@ -82,6 +82,9 @@ _SIGS = {
     "cgp_get_matrix": (c_int32, [c_void_p, c_int32, c_void_p, c_int32, c_void_p]),
     "cgp_solver_info": (c_int32, [c_void_p, POINTER(c_int32), POINTER(c_int32), POINTER(c_int64),
                                   POINTER(c_int64)]),
+    "cgp_set_dirichlet": (c_int32, [c_void_p, c_void_p, c_int32, c_void_p]),
+    "cgp_set_forcing": (c_int32, [c_void_p, c_void_p, c_int32, c_void_p]),
+    "cgp_record_pairs": (c_int32, [c_void_p, c_int32, c_void_p, c_void_p, c_void_p, c_int32, c_void_p]),
     "cgp_coarse_info": (c_int32, [c_void_p, POINTER(c_int32), POINTER(c_int32), POINTER(c_int32)]),
     "cgp_poisson_solve": (c_int32, [c_void_p, c_void_p, c_void_p, POINTER(c_int32), c_int32, c_void_p]),
     "cgp_prolong": (c_int32, [c_void_p, c_void_p, c_void_p, c_int32, c_void_p]),
@@ -257,6 +260,25 @@ def cgp_get_fields(solver, U=None, P=None, where=CGP_HOST, stream=None, allow=(C
         _check(rc)
     _check(rc, allow=allow)
     return U, P, t.value, st.as_dict(), rc
+
+
+def cgp_set_dirichlet(solver, uD, stream=None):
+    uD = np.ascontiguousarray(uD, dtype=np.float64)
+    _check(load().cgp_set_dirichlet(solver, _ptr(uD), CGP_HOST, _stream(stream)))
+
+
+def cgp_set_forcing(solver, F, stream=None):
+    F = np.ascontiguousarray(F, dtype=np.float64)
+    _check(load().cgp_set_forcing(solver, _ptr(F), CGP_HOST, _stream(stream)))
+
+
+def cgp_record_pairs(solver, n_steps, rhs, prev, target, where=None, stream=None):
+    """Advance n_steps steps, storing (rhs, previous increment, increment) per step into the
+    given arrays (n_steps x N_c; torch CUDA tensors, or numpy arrays for the host form)."""
+    if where is None:
+        where = CGP_DEVICE if hasattr(rhs, "is_cuda") and rhs.is_cuda else CGP_HOST
+    _check(load().cgp_record_pairs(solver, int(n_steps), _ptr(rhs), _ptr(prev), _ptr(target), where,
+                                   _stream(stream)))
 
 
 def cgp_coarse_info(solver):

@@ -198,6 +198,10 @@ static int layout(Solver& s, void* base, size_t* bytes) {
     s.rc = cv.take<double>(nc);
     s.div = cv.take<double>(nf);
     s.qrot = cv.take<double>(nf);
+    if (s.prm.bc_kind == CGP_BC_USER) {
+        s.user_ud = cv.take<double>(2 * nf);
+        s.user_f = cv.take<double>(2 * nf);
+    }
     s.partials = cv.take<double>((size_t)s.max_grid * 8);
     s.tickets = cv.take<unsigned int>(64);
     s.bar_count = cv.take<unsigned int>(2);
@@ -218,7 +222,7 @@ static int check_params(const cgp_mesh* m, const cgp_params* p) {
     }
     if (p->k < 0 || p->k > m->n_levels || !(p->Re > 0) || !(p->dt > 0) || (p->chi != 0 && p->chi != 1) ||
         !(p->tol_mom > 0) || !(p->tol_poisson > 0) || !(p->tol_mass > 0) || p->max_it_mom < 1 ||
-        p->max_it_poisson < 1 || p->max_it_mass < 1 || p->bc_kind < 0 || p->bc_kind > CGP_BC_TG_PERIODIC ||
+        p->max_it_poisson < 1 || p->max_it_mass < 1 || p->bc_kind < 0 || p->bc_kind > CGP_BC_USER ||
         (p->precision != CGP_FP64 && p->precision != CGP_MIXED) || p->guess < 0 || p->guess > 2 ||
         (p->mass_mode != CGP_MASS_CONSISTENT && p->mass_mode != CGP_MASS_LUMPED) || p->coarse_mode < 0 ||
         p->coarse_mode > CGP_COARSE_ONCHIP || p->cluster_size < 0 || p->cluster_size > 16 || p->tol_inner < 0 ||
@@ -346,6 +350,8 @@ extern "C" int cgp_assemble(const cgp_mesh* mesh, const cgp_params* params, void
         cudaMemsetAsync(s.ks, 0, (KS_COUNT + 1) * sizeof(KrylovState), st) != cudaSuccess ||
         cudaMemsetAsync(s.stats, 0, sizeof(DeviceStats), st) != cudaSuccess ||
         cudaMemsetAsync(s.phi, 0, sizeof(double) * s.nf, st) != cudaSuccess ||
+        (s.user_ud && cudaMemsetAsync(s.user_ud, 0, sizeof(double) * 2 * s.nf, st) != cudaSuccess) ||
+        (s.user_f && cudaMemsetAsync(s.user_f, 0, sizeof(double) * 2 * s.nf, st) != cudaSuccess) ||
         cudaMemsetAsync(s.scal, 0, sizeof(double) * 16, st) != cudaSuccess) {
         set_error("workspace initialisation failed");
         return fail(CGP_ECUDA);

@@ -10,6 +10,8 @@ struct BcParams {
     int kind;
     double p0, p1, p2, p3;
     double Re;
+    const double* ud = nullptr;   // CGP_BC_USER: caller's Dirichlet values (2 per vertex)
+    const double* fu = nullptr;   // CGP_BC_USER: caller's body force (2 per vertex)
 };
 
 __device__ __forceinline__ void tg_shape(double x, double y, double& u, double& v, double& p) {
@@ -44,11 +46,16 @@ __device__ __forceinline__ bool exact_field(const BcParams& bc, double x, double
     return false;
 }
 
-// prescribed velocity at a VEL_DIR vertex
-__device__ __forceinline__ void dirichlet_value(const BcParams& bc, double x, double y, double t, double& u,
+// prescribed velocity at VEL_DIR vertex i
+__device__ __forceinline__ void dirichlet_value(const BcParams& bc, int i, double x, double y, double t, double& u,
                                                 double& v) {
     u = 0.0;
     v = 0.0;
+    if (bc.kind == CGP_BC_USER) {
+        u = bc.ud[2 * i];
+        v = bc.ud[2 * i + 1];
+        return;
+    }
     if (bc.kind == CGP_BC_CAVITY) {
         if (y == 1.0 && x > 0.0 && x < 1.0) u = bc.p0;
         return;
@@ -62,9 +69,15 @@ __device__ __forceinline__ void dirichlet_value(const BcParams& bc, double x, do
     exact_field(bc, x, y, t, u, v, p);
 }
 
-__device__ __forceinline__ void body_force(const BcParams& bc, double x, double y, double t, double& fx, double& fy) {
+__device__ __forceinline__ void body_force(const BcParams& bc, int i, double x, double y, double t, double& fx,
+                                           double& fy) {
     fx = 0.0;
     fy = 0.0;
+    if (bc.kind == CGP_BC_USER) {
+        fx = bc.fu[2 * i];
+        fy = bc.fu[2 * i + 1];
+        return;
+    }
     if (bc.kind == CGP_BC_TG_PERIODIC) {
         double u, v, p;
         tg_shape(x, y, u, v, p);

@@ -65,6 +65,7 @@ struct Solver {
     int cluster_size = 0;         // CTAs of the one-cluster solver
     int coarse_grid = 0;          // CTAs of the persistent (cooperative) solver
     bool coarse_rr = false;       // the persistent FP64 solve may keep its rows in registers
+    double *user_ud = nullptr, *user_f = nullptr;   // CGP_BC_USER: 2*nf each
     bool coarse_fp64 = true;      // the coarse solve's inner iterations run in FP64
     size_t onchip_bytes = 0;      // mixed: shared memory per CTA of the on-chip cluster solve (0 = not used)
     // mixed: workspace arrays of the on-chip plan (sized for the coarse level) and its device view

@@ -13,6 +13,14 @@
 namespace cgp {
 
 
+// problem data of the solver's kind, with the caller's arrays for CGP_BC_USER
+static BcParams bc_of(const Solver& s) {
+    BcParams b = bc_from(s.prm);
+    b.ud = s.user_ud;
+    b.fu = s.user_f;
+    return b;
+}
+
 // ---------------------------------------------------------------- per-vertex kernels
 __global__ void k_init_state(int nf, const double* __restrict__ xy, const uint8_t* __restrict__ tag, BcParams bc,
                              double dt, double* __restrict__ U, double* __restrict__ Uprev, double* __restrict__ P,
@@ -32,7 +40,7 @@ __global__ void k_init_state(int nf, const double* __restrict__ xy, const uint8_
         return;
     }
     u = v = 0.0;
-    if (tag[i] & CGP_VEL_DIR) dirichlet_value(bc, x, y, 0.0, u, v);
+    if (tag[i] & CGP_VEL_DIR) dirichlet_value(bc, i, x, y, 0.0, u, v);
     U[2 * i] = Uprev[2 * i] = u;
     U[2 * i + 1] = Uprev[2 * i + 1] = v;
     P[i] = 0.0;
@@ -47,7 +55,7 @@ __global__ void k_mom_prep(int nf, const double* __restrict__ U, const double* _
         double2 u = reinterpret_cast<const double2*>(U)[i];
         double2 up = reinterpret_cast<const double2*>(Uprev)[i];
         double fx = 0.0, fy = 0.0;
-        if (bc.kind == CGP_BC_TG_PERIODIC) body_force(bc, xy[2 * i], xy[2 * i + 1], tn, fx, fy);
+        if (bc.kind == CGP_BC_TG_PERIODIC || bc.kind == CGP_BC_USER) body_force(bc, i, xy[2 * i], xy[2 * i + 1], tn, fx, fy);
         reinterpret_cast<double2*>(w)[i] = make_double2(2.0 * u.x - up.x, 2.0 * u.y - up.y);
         reinterpret_cast<double2*>(h)[i] =
             make_double2(dt * fx + (2.0 * u.x - 0.5 * up.x), dt * fy + (2.0 * u.y - 0.5 * up.y));
@@ -76,7 +84,7 @@ __global__ void k_mom_assemble(int nf, const int32_t* __restrict__ rowptr, const
             for (int q = rb; q < re; ++q) A[e0 + 32 * (q - rb)] = col[q] == i ? 1.0 : 0.0;
             dinv[i] = 1.0;
             double u, v;
-            dirichlet_value(bc, xy[2 * i], xy[2 * i + 1], tn, u, v);
+            dirichlet_value(bc, i, xy[2 * i], xy[2 * i + 1], tn, u, v);
             reinterpret_cast<double2*>(b)[i] = make_double2(u, v);
             reinterpret_cast<double2*>(x0)[i] = make_double2(u, v);
             continue;
@@ -829,7 +837,7 @@ int step_pre(Ctx& c) {
     const cgp_params& p = s.prm;
     const Level& F = s.mesh->lev[s.lf];
     const Level& C = s.mesh->lev[s.lc];
-    const BcParams bc = bc_from(p);
+    const BcParams bc = bc_of(s);
     SellView Af = sell_of(F), Ac = sell_of(C);
     const int gv = grid_rows(s, F.nv, 1);
     PL(c, CGP_PROF_MOM_PREP, k_mom_prep<<<gv, kBlock, 0, c.st>>>(F.nv, s.U, s.Uprev, F.xy, bc, s.tdev, p.dt, s.w, s.h));
@@ -907,7 +915,7 @@ static int step_body(Ctx& c) {
 
 int init_state(Solver* s, cudaStream_t st) {
     const Level& F = s->mesh->lev[s->lf];
-    k_init_state<<<blocks_for(F.nv), kBlock, 0, st>>>(F.nv, F.xy, F.tag, bc_from(s->prm), s->prm.dt, s->U, s->Uprev,
+    k_init_state<<<blocks_for(F.nv), kBlock, 0, st>>>(F.nv, F.xy, F.tag, bc_of(*s), s->prm.dt, s->U, s->Uprev,
                                                       s->P, s->tdev);
     CGP_LAUNCH_CHECK();
     return CGP_OK;
@@ -1028,6 +1036,51 @@ extern "C" int cgp_step(cgp_solver* h, int32_t n_steps, cgp_stream_t stream) {
         return CGP_OK;
     }
     for (int i = 0; i < n_steps; ++i) CGP_TRY(enqueue_step(&s, st, false));
+    return CGP_OK;
+}
+
+static int set_user_array(cgp_solver* h, double* dst, const double* src, int32_t where, cgp_stream_t stream,
+                          const char* name) {
+    clear_error();
+    if (!h || !src || (where != CGP_HOST && where != CGP_DEVICE)) {
+        set_error("%s: bad arguments", name);
+        return CGP_EINVAL;
+    }
+    if (h->s.prm.bc_kind != CGP_BC_USER || !dst) {
+        set_error("%s: the solver's bc_kind is not CGP_BC_USER", name);
+        return CGP_EINVAL;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    CGP_TRY(copy_in(dst, src, sizeof(double) * 2 * h->s.nf, where, st));
+    if (where == CGP_HOST) CGP_CUDA(cudaStreamSynchronize(st));
+    return CGP_OK;
+}
+
+extern "C" int cgp_set_dirichlet(cgp_solver* h, const double* uD, int32_t where, cgp_stream_t stream) {
+    return set_user_array(h, h ? h->s.user_ud : nullptr, uD, where, stream, "cgp_set_dirichlet");
+}
+
+extern "C" int cgp_set_forcing(cgp_solver* h, const double* F, int32_t where, cgp_stream_t stream) {
+    return set_user_array(h, h ? h->s.user_f : nullptr, F, where, stream, "cgp_set_forcing");
+}
+
+extern "C" int cgp_record_pairs(cgp_solver* h, int32_t n_steps, double* rhs, double* prev, double* target,
+                                int32_t where, cgp_stream_t stream) {
+    clear_error();
+    if (!h || n_steps < 0 || !rhs || !prev || !target || (where != CGP_HOST && where != CGP_DEVICE)) {
+        set_error("cgp_record_pairs: bad arguments");
+        return CGP_EINVAL;
+    }
+    Solver& s = h->s;
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t nc = s.nc, bytes = sizeof(double) * nc;
+    for (int k = 0; k < n_steps; ++k) {
+        CGP_TRY(copy_out(prev + k * nc, s.phi, bytes, where, st));
+        CGP_TRY(cgp_step(h, 1, stream));
+        CGP_TRY(copy_out(rhs + k * nc, s.rc, bytes, where, st));
+        CGP_TRY(copy_out(target + k * nc, s.phi, bytes, where, st));
+    }
+    if (where == CGP_HOST) CGP_CUDA(cudaStreamSynchronize(st));
     return CGP_OK;
 }
 

@@ -23,15 +23,11 @@ class PairStore:
 
     def record(self, solver, steps):
         """Advance `steps` steps of `solver` (a binding.Solver), storing one triple per step."""
-        for _ in range(steps):
-            if self.count >= self.cap:
-                break
-            k = self.count
-            cg.cgp_get_vector_device(solver.handle, cg.CGP_VEC_PHI_C, self.q[k])
-            solver.step(1)
-            cg.cgp_get_vector_device(solver.handle, cg.CGP_VEC_RHS_C, self.r[k])
-            cg.cgp_get_vector_device(solver.handle, cg.CGP_VEC_PHI_C, self.t[k])
-            self.count += 1
+        k = self.count
+        m = min(steps, self.cap - k)
+        if m > 0:
+            cg.cgp_record_pairs(solver.handle, m, self.r[k:k + m], self.q[k:k + m], self.t[k:k + m])
+            self.count += m
         return self.count
 
 

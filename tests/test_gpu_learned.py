@@ -116,3 +116,21 @@ def test_training_and_learned_guess_in_the_step(cg):
     assert sl["sum_it_poisson"] <= 1.1 * sp["sum_it_poisson"]
     cg.cgp_mlp_destroy(net)
     mesh.close()
+
+
+def test_record_pairs_matches_the_step_by_step_record(cg):
+    # the C ABI's pair recorder stores what reading the vectors around each step gives
+    base = channel_cylinder_mesh(seed=7, h=0.05)
+    mesh = cg.Mesh(base.xy, base.tri, base.tag, 2)
+    prm = cg.make_params(1000.0, 0.002, chi=1, k=1, bc_kind=cg.CGP_BC_CHANNEL, bc_param=(0.3, 0.41))
+    a, b = cg.Solver(mesh, prm), cg.Solver(mesh, prm)
+    n, nc = 4, a.nc
+    rh, pv, tg = (np.zeros((n, nc)) for _ in range(3))
+    cg.cgp_record_pairs(a.handle, n, rh, pv, tg)
+    for k in range(n):
+        q = b.vector(cg.CGP_VEC_PHI_C)[:nc]
+        b.step(1)
+        assert np.array_equal(pv[k], q)
+        assert np.array_equal(rh[k], b.vector(cg.CGP_VEC_RHS_C))
+        assert np.array_equal(tg[k], b.vector(cg.CGP_VEC_PHI_C)[:nc])
+    a.close(); b.close(); mesh.close()

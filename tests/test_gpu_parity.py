@@ -280,3 +280,40 @@ def test_mixed_falls_back_to_fp64_coarse_when_off_chip(cg):
     U, P, t, st, rc = s.fields()
     assert rc == 0 and np.isfinite(U).all() and st["res_poisson"] <= 1.0001e-8
     s.close(); m.close()
+
+
+def test_user_boundary_data_reproduce_the_built_in_kinds(cg):
+    # CGP_BC_USER with the caller's arrays: the cavity lid gives the cavity run bit for bit;
+    # per-step Taylor-Green-periodic data (Dirichlet values and body force at t^{n+1},
+    # evaluated on the host) give the built-in kind to rounding
+    base = square_mesh(8)
+    m = cg.Mesh(base.xy, base.tri, base.tag, 2)
+    F = m.level(2)
+    xy = F["xy"]
+    ref = cg.Solver(m, cg.make_params(100.0, 0.01, chi=1, k=1, **TIGHT))
+    usr = cg.Solver(m, cg.make_params(100.0, 0.01, chi=1, k=1, bc_kind=cg.CGP_BC_USER, **TIGHT))
+    U0, P0, t0, _, _ = ref.fields()
+    lid = flows.dirichlet_value(flows.BC_CAVITY, xy, 0.0, 100.0)
+    cg.cgp_set_dirichlet(usr.handle, lid)
+    usr.set_fields(U0, U0, P0, t0)
+    ref.step(5)
+    usr.step(5)
+    assert np.array_equal(ref.fields()[0], usr.fields()[0]) and np.array_equal(ref.fields()[1], usr.fields()[1])
+    ref.close(); usr.close()
+    Re, dt = 100.0, 0.005
+    ref = cg.Solver(m, cg.make_params(Re, dt, chi=1, k=1, bc_kind=cg.CGP_BC_TG_PERIODIC, **TIGHT))
+    usr = cg.Solver(m, cg.make_params(Re, dt, chi=1, k=1, bc_kind=cg.CGP_BC_USER, **TIGHT))
+    U0, P0, t0, _, _ = ref.fields()
+    usr.set_fields(U0, ref.vector(cg.CGP_VEC_UPREV), P0, t0)
+    for n in range(6):
+        t1 = (n + 1) * dt
+        cg.cgp_set_dirichlet(usr.handle, flows.dirichlet_value(flows.BC_TG_PERIODIC, xy, t1, Re))
+        cg.cgp_set_forcing(usr.handle, flows.body_force(flows.BC_TG_PERIODIC, xy, t1, Re))
+        usr.step(1)
+    ref.step(6)
+    Ur, Pr = ref.fields()[:2]
+    Uu, Pu = usr.fields()[:2]
+    assert rel(Uu, Ur) < 1e-10 and rel(Pu, Pr) < 1e-8, (rel(Uu, Ur), rel(Pu, Pr))
+    with pytest.raises(RuntimeError):
+        cg.cgp_set_forcing(ref.handle, np.zeros((xy.shape[0], 2)))     # not a CGP_BC_USER solver
+    ref.close(); usr.close(); m.close()
