@@ -99,7 +99,14 @@ typedef struct {
     double tol_inner;          /* CGP_MIXED: residual reduction asked of each FP32 inner solve (0 = 1e-3) */
     int32_t coarse_mode;       /* coarse Poisson solver: CGP_COARSE_* */
     int32_t cluster_size;      /* CTAs of the cluster solver (0 = largest that fits, else 2..16) */
+    int32_t restrict_mode;     /* CGP_RESTRICT_*: how the right-hand side of Eq. 23 reaches the coarse level */
 } cgp_params;
+
+/* INJECT (the paper, Eqs. 22-23): inject U~ at the coarse vertices, then the coarse
+ * divergence.  PT (a variant, not in the paper): the fine divergence Cx u~ + Cy v~
+ * restricted by the transpose of the prolongation of Eq. 24, the Galerkin-consistent
+ * right-hand side; the two agree when U~ is the prolongation of a coarse field. */
+enum { CGP_RESTRICT_INJECT = 0, CGP_RESTRICT_PT = 1 };
 
 /* Coarse Poisson solver kinds.  KERNELS: two kernel launches per PCG iteration (graph
  * WHILE loop).  PERSISTENT: the whole solve in one cooperative launch over the GPU with a

@@ -64,7 +64,7 @@ class CGPOracle:
     """
 
     def __init__(self, base, n_levels, k, Re, dt, chi, bc,
-                 bc_param=(1.0, 0.0, 0.0, 0.0), mass_mode="consistent", levels=None):
+                 bc_param=(1.0, 0.0, 0.0, 0.0), mass_mode="consistent", levels=None, restrict_mode="inject"):
         if not 0 <= k <= n_levels:
             raise ValueError("need 0 <= k <= n_levels")
         self.levels = levels if levels is not None else build_hierarchy(base.xy, base.tri, base.tag, n_levels)
@@ -72,6 +72,7 @@ class CGPOracle:
         self.fine, self.coarse = self.levels[self.lf], self.levels[self.lc]
         self.Re, self.dt, self.chi, self.bc = float(Re), float(dt), int(chi), int(bc)
         self.bc_param = tuple(bc_param)
+        self.restrict_mode = restrict_mode
         self.mass_mode = mass_mode
         f, c = self.fine, self.coarse
         self.ops_f = fem.static_operators(f.xy, f.tri)
@@ -116,9 +117,15 @@ class CGPOracle:
         return np.stack([lu.solve(bx), lu.solve(by)], 1)
 
     def coarse_rhs(self, Ut):
-        """Eqs. 22-23: inject U~ and form -3/(2 dt) (Cx_c u~_c + Cy_c v~_c)."""
-        Uc = fem.inject(Ut, self.coarse.n_vert)
-        r = -1.5 / self.dt * (self.ops_c["Cx"] @ Uc[:, 0] + self.ops_c["Cy"] @ Uc[:, 1])
+        """Eqs. 22-23: inject U~ and form -3/(2 dt) (Cx_c u~_c + Cy_c v~_c).  restrict_mode
+        "pt" (a variant, not the paper's): -3/(2 dt) P^T (Cx_f u~ + Cy_f v~), the fine
+        divergence restricted by the transpose of the prolongation."""
+        if self.restrict_mode == "pt":
+            g = self.ops_f["Cx"] @ Ut[:, 0] + self.ops_f["Cy"] @ Ut[:, 1]
+            r = -1.5 / self.dt * fem.restrict_t(g, self.levels, self.lf, self.lc)
+        else:
+            Uc = fem.inject(Ut, self.coarse.n_vert)
+            r = -1.5 / self.dt * (self.ops_c["Cx"] @ Uc[:, 0] + self.ops_c["Cy"] @ Uc[:, 1])
         r[self.phi0_mask] = 0.0
         if self.pure_neumann:
             r = r - r.sum() / r.size

@@ -108,6 +108,25 @@ def prolong_one(phi_c, parents):
     return np.concatenate([phi_c, mid])
 
 
+def restrict_t_one(y_f, parents, n_coarse):
+    """Transpose of one prolongation level: y_c[i] = y_f[i] + 1/2 (sum of y_f over the new
+    vertices that have i as an end point of their edge)."""
+    y_f = np.asarray(y_f, dtype=np.float64)
+    y_c = np.array(y_f[:n_coarse], copy=True)
+    new = y_f[n_coarse:]
+    np.add.at(y_c, parents[:, 0], 0.5 * new)
+    np.add.at(y_c, parents[:, 1], 0.5 * new)
+    return y_c
+
+
+def restrict_t(y_f, levels, l_from, l_to):
+    """P^T from level l_from down to level l_to (< l_from): the transposed composition."""
+    y = np.asarray(y_f, dtype=np.float64)
+    for l in range(l_from, l_to, -1):
+        y = restrict_t_one(y, levels[l].parents, levels[l - 1].n_vert)
+    return y
+
+
 def prolong(phi_c, levels, l_from, l_to):
     """Compose the one-level prolongations from level l_from up to level l_to."""
     phi = np.asarray(phi_c, dtype=np.float64)

@@ -18,6 +18,7 @@ CGP_OK, CGP_EINVAL, CGP_ENOTCONV, CGP_EBREAKDOWN, CGP_ENONFINITE, CGP_ETIMEOUT, 
     0, -1, -2, -3, -4, -5, -6, -7
 CGP_VEL_DIR, CGP_PHI_ZERO = 1, 2
 CGP_BC_CAVITY, CGP_BC_CHANNEL, CGP_BC_TG, CGP_BC_TG_PERIODIC, CGP_BC_USER = 0, 1, 2, 3, 4
+CGP_RESTRICT_INJECT, CGP_RESTRICT_PT = 0, 1
 CGP_FP64, CGP_MIXED = 0, 1
 CGP_GUESS_ZERO, CGP_GUESS_PREV, CGP_GUESS_LEARNED = 0, 1, 2
 CGP_MASS_CONSISTENT, CGP_MASS_LUMPED = 0, 1
@@ -50,7 +51,8 @@ class Params(ctypes.Structure):
                 ("max_it_mom", c_int32), ("max_it_poisson", c_int32), ("max_it_mass", c_int32),
                 ("precision", c_int32), ("guess", c_int32), ("mass_mode", c_int32), ("bc_kind", c_int32),
                 ("bc_param", c_double * 4), ("use_graph", c_int32), ("tol_inner", c_double),
-                ("coarse_mode", c_int32), ("cluster_size", c_int32)]
+                ("coarse_mode", c_int32), ("cluster_size", c_int32),
+                ("restrict_mode", c_int32)]
 
 
 class Stats(ctypes.Structure):
@@ -209,7 +211,7 @@ def cgp_mesh_destroy(mesh):
 def make_params(Re, dt, chi=0, k=1, tol_mom=1e-10, tol_poisson=1e-10, tol_mass=1e-12, max_it_mom=500,
                 max_it_poisson=20000, max_it_mass=500, precision=CGP_FP64, guess=CGP_GUESS_PREV,
                 mass_mode=CGP_MASS_CONSISTENT, bc_kind=CGP_BC_CAVITY, bc_param=(1.0, 0.0, 0.0, 0.0),
-                use_graph=1, tol_inner=0.0, coarse_mode=0, cluster_size=0):
+                use_graph=1, tol_inner=0.0, coarse_mode=0, cluster_size=0, restrict_mode=0):
     p = Params()
     p.Re, p.dt, p.chi, p.k = Re, dt, chi, k
     p.tol_mom, p.tol_poisson, p.tol_mass = tol_mom, tol_poisson, tol_mass
@@ -219,6 +221,7 @@ def make_params(Re, dt, chi=0, k=1, tol_mom=1e-10, tol_poisson=1e-10, tol_mass=1
         p.bc_param[i] = bc_param[i] if i < len(bc_param) else 0.0
     p.use_graph = use_graph
     p.tol_inner, p.coarse_mode, p.cluster_size = tol_inner, coarse_mode, cluster_size
+    p.restrict_mode = restrict_mode
     return p
 
 

@@ -222,7 +222,7 @@ static int check_params(const cgp_mesh* m, const cgp_params* p) {
     }
     if (p->k < 0 || p->k > m->n_levels || !(p->Re > 0) || !(p->dt > 0) || (p->chi != 0 && p->chi != 1) ||
         !(p->tol_mom > 0) || !(p->tol_poisson > 0) || !(p->tol_mass > 0) || p->max_it_mom < 1 ||
-        p->max_it_poisson < 1 || p->max_it_mass < 1 || p->bc_kind < 0 || p->bc_kind > CGP_BC_USER ||
+        p->max_it_poisson < 1 || p->max_it_mass < 1 || p->bc_kind < 0 || p->bc_kind > CGP_BC_USER || p->restrict_mode < 0 || p->restrict_mode > CGP_RESTRICT_PT ||
         (p->precision != CGP_FP64 && p->precision != CGP_MIXED) || p->guess < 0 || p->guess > 2 ||
         (p->mass_mode != CGP_MASS_CONSISTENT && p->mass_mode != CGP_MASS_LUMPED) || p->coarse_mode < 0 ||
         p->coarse_mode > CGP_COARSE_ONCHIP || p->cluster_size < 0 || p->cluster_size > 16 || p->tol_inner < 0 ||

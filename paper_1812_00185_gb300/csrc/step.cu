@@ -150,6 +150,37 @@ __global__ void __launch_bounds__(kBlock) k_coarse_rhs(SellView Ac, const double
     if (grid_sum<1>(acc, partials, ticket, tot) && threadIdx.x == 0) st->mean = pure_neumann ? tot[0] / Ac.n : 0.0;
 }
 
+// One level of P^T, the transposed prolongation (CGP_RESTRICT_PT).  On a red refinement the
+// neighbours of an old vertex on the finer level are exactly the midpoints of its incident
+// edges, each of which P sets to half of it, so y_c[i] = y_f[i] + 1/2 of the sum of y_f over
+// those neighbours: a gather over the finer level's adjacency (diagonal skipped).
+__global__ void k_restrict_t(int nc, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                             const double* __restrict__ yf, double* __restrict__ yc) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nc; i += gridDim.x * blockDim.x) {
+        double s = 0.0;
+        for (int q = rowptr[i]; q < rowptr[i + 1]; ++q) {
+            const int j = col[q];
+            if (j != i) s += yf[j];
+        }
+        yc[i] = yf[i] + 0.5 * s;
+    }
+}
+
+// right-hand side of Eq. 23 from the restricted fine divergence y (CGP_RESTRICT_PT)
+__global__ void __launch_bounds__(kBlock) k_coarse_rhs_pt(int nc, const double* __restrict__ y,
+                                                         const uint8_t* __restrict__ tag, double dt,
+                                                         double* __restrict__ rc, KrylovState* st, int pure_neumann,
+                                                         double* partials, unsigned int* ticket) {
+    double acc[1] = {0.0};
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nc; i += gridDim.x * blockDim.x) {
+        const double r = (tag[i] & CGP_PHI_ZERO) ? 0.0 : -1.5 / dt * y[i];
+        rc[i] = r;
+        acc[0] += r;
+    }
+    double tot[1];
+    if (grid_sum<1>(acc, partials, ticket, tot) && threadIdx.x == 0) st->mean = pure_neumann ? tot[0] / nc : 0.0;
+}
+
 // mean fix of a pure-Neumann solution: mu = sum m_i phi_i / sum m_i
 __global__ void __launch_bounds__(kBlock) k_phi_mean(int n, const double* __restrict__ m, const double* __restrict__ phi,
                                                     double* __restrict__ out, double* partials, unsigned int* ticket) {
@@ -851,9 +882,28 @@ int step_pre(Ctx& c) {
     else
         CGP_TRY(bicgstab(c, Af, s.A, s.dinvA, s.b, &s.ks[KS_MOM], p.tol_mom, p.max_it_mom));
     // Eqs. 22-23: injection and coarse divergence
-    PL(c, CGP_PROF_COARSE_RHS,
-       k_coarse_rhs<<<grid_rows(s, C.nslices * 32, 1), kBlock, 0, c.st>>>(
-           Ac, s.Cxc, s.Cyc, s.Ut, C.tag, p.dt, s.rc, &s.ks[KS_POIS], s.pure_neumann, s.partials, s.tickets));
+    if (p.restrict_mode == CGP_RESTRICT_PT) {
+        // fine divergence, then P^T level by level (ping-pong in two Krylov work vectors that
+        // are free until the coarse solve)
+        PL(c, CGP_PROF_COARSE_RHS,
+           k_div<<<grid_rows(s, F.nslices * 32, 1), kBlock, 0, c.st>>>(Af, s.Cx, s.Cy, s.Ut, s.div, nullptr, nullptr));
+        const double* y = s.div;
+        double* buf[2] = {s.kz, s.kq};
+        for (int l = s.lf, b = 0; l > s.lc; --l, b ^= 1) {
+            const Level& L = s.mesh->lev[l];
+            const int nc = s.mesh->lev[l - 1].nv;
+            PL(c, CGP_PROF_COARSE_RHS,
+               k_restrict_t<<<grid_rows(s, nc, 1), kBlock, 0, c.st>>>(nc, L.rowptr, L.col, y, buf[b]));
+            y = buf[b];
+        }
+        PL(c, CGP_PROF_COARSE_RHS,
+           k_coarse_rhs_pt<<<grid_rows(s, C.nv, 1), kBlock, 0, c.st>>>(C.nv, y, C.tag, p.dt, s.rc, &s.ks[KS_POIS],
+                                                                         s.pure_neumann, s.partials, s.tickets));
+    } else {
+        PL(c, CGP_PROF_COARSE_RHS,
+           k_coarse_rhs<<<grid_rows(s, C.nslices * 32, 1), kBlock, 0, c.st>>>(
+               Ac, s.Cxc, s.Cyc, s.Ut, C.tag, p.dt, s.rc, &s.ks[KS_POIS], s.pure_neumann, s.partials, s.tickets));
+    }
     CGP_LAUNCH_CHECK();
     return learned_guess(c);
 }
@@ -898,8 +948,10 @@ int step_post(Ctx& c) {
                              ((p.guess == CGP_GUESS_LEARNED && s.guess_ready) ? 10 : 0);
     // mixed: per refinement solve kIrSweeps x (residual, inner init, update), + the FP32 copy of A
     const int ir_fixed = mixed ? 1 + 3 * kIrSweeps * (1 + (lumped ? 0 : 1) + (p.chi && !lumped ? 1 : 0)) : 0;
+    const int pt_fixed = p.restrict_mode == CGP_RESTRICT_PT ? 1 + (s.lf - s.lc) : 0;   // k_div + the P^T levels
     const int fixed =
-        4 + 1 + coarse_fixed + (s.lf - s.lc) + 1 + (lumped ? 0 : 2) + (p.chi ? 1 + (lumped ? 0 : 2) : 0) + 1 + ir_fixed;
+        4 + 1 + coarse_fixed + (s.lf - s.lc) + 1 + (lumped ? 0 : 2) + (p.chi ? 1 + (lumped ? 0 : 2) : 0) + 1 + ir_fixed +
+        pt_fixed;
     PL(c, CGP_PROF_FINISH,
        k_finish<<<gv, kBlock, 0, c.st>>>(F.nv, s.U, s.Uprev, s.Ut, s.delta, s.P, s.phi, s.qrot, p.chi, 1.0 / p.Re,
                                          s.tdev, p.dt, s.stats, s.ks, fixed, one_launch ? 0 : 1));

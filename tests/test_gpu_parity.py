@@ -317,3 +317,24 @@ def test_user_boundary_data_reproduce_the_built_in_kinds(cg):
     with pytest.raises(RuntimeError):
         cg.cgp_set_forcing(ref.handle, np.zeros((xy.shape[0], 2)))     # not a CGP_BC_USER solver
     ref.close(); usr.close(); m.close()
+
+
+@pytest.mark.parametrize("case", ["cavity_k2", "channel_k1"])
+def test_pt_restriction_full_run(cg, case):
+    # restrict_mode PT (the fine divergence restricted by P^T) against the oracle's variant
+    if case == "cavity_k2":
+        base, lv, k, bc, bp = square_mesh(8), 2, 2, flows.BC_CAVITY, (1.0, 0, 0, 0)
+    else:
+        base, lv, k, bc, bp = _channel_small(), 2, 1, flows.BC_CHANNEL, (0.3, 0.41, 0, 0)
+    m = cg.Mesh(base.xy, base.tri, base.tag, lv)
+    s = cg.Solver(m, cg.make_params(100.0, 0.01, chi=1, k=k, bc_kind=bc, bc_param=bp,
+                                    restrict_mode=cg.CGP_RESTRICT_PT, **TIGHT))
+    o = CGPOracle(base, lv, k, 100.0, 0.01, 1, bc, bc_param=bp, restrict_mode="pt")
+    s.step(1)
+    out = o.step()
+    assert rel(s.vector(cg.CGP_VEC_RHS_C), out["rc"]) < 1e-10
+    s.step(4)
+    o.run(4)
+    U, P, t, st, rc = s.fields()
+    assert rc == 0 and rel(U, o.U) < 1e-6 and rel(P, o.P) < 1e-6, (rel(U, o.U), rel(P, o.P))
+    s.close(); m.close()

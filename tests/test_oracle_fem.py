@@ -146,3 +146,37 @@ def test_prolongation_exact_on_linear_and_injection_inverse():
                 rnd = np.random.default_rng(lc).standard_normal(xc.shape[0])
                 back = fem.inject(fem.prolong(rnd, levels, lc, lf), xc.shape[0])
                 assert np.array_equal(back, rnd)          # R P = I bit for bit
+
+
+@pytest.mark.parametrize("k", [1, 2, 3])
+def test_restriction_is_the_transpose_of_prolongation(k):
+    # <P x, y> = <x, P^T y> for random coarse x and fine y, over k levels
+    base = square_mesh(4)
+    levels = build_hierarchy(base.xy, base.tri, base.tag, 3)
+    rng = np.random.default_rng(k)
+    x = rng.standard_normal(levels[3 - k].n_vert)
+    y = rng.standard_normal(levels[3].n_vert)
+    lhs = fem.prolong(x, levels, 3 - k, 3) @ y
+    rhs = x @ fem.restrict_t(y, levels, 3, 3 - k)
+    assert abs(lhs - rhs) <= 1e-12 * (abs(lhs) + 1.0)
+
+
+@pytest.mark.parametrize("k", [1, 2])
+def test_pt_rhs_equals_injection_for_prolonged_velocity(k):
+    # nested P1 spaces: P^T Cx_f P = Cx_c (the coarse operators are the Galerkin products),
+    # so for a fine velocity that is the prolongation of a coarse one the two restrictions
+    # of Eq. 22 give the same coarse right-hand side
+    from oracle.cgp import CGPOracle
+    from oracle import flows
+    base = channel_cylinder_mesh(seed=3, h=0.08)
+    o_inj = CGPOracle(base, 2, k, 100.0, 0.01, 0, flows.BC_CHANNEL, bc_param=(0.3, 0.41, 0, 0))
+    o_pt = CGPOracle(base, 2, k, 100.0, 0.01, 0, flows.BC_CHANNEL, bc_param=(0.3, 0.41, 0, 0),
+                     levels=o_inj.levels, restrict_mode="pt")
+    rng = np.random.default_rng(5)
+    Uc = rng.standard_normal((o_inj.coarse.n_vert, 2))
+    Uf = np.stack([fem.prolong(Uc[:, c], o_inj.levels, 2 - k, 2) for c in range(2)], 1)
+    a, b = o_inj.coarse_rhs(Uf), o_pt.coarse_rhs(Uf)
+    assert np.abs(a - b).max() <= 1e-11 * np.abs(a).max()
+    # on a general fine field they differ (the variant is not the paper's restriction)
+    Ur = rng.standard_normal(Uf.shape)
+    assert np.abs(o_inj.coarse_rhs(Ur) - o_pt.coarse_rhs(Ur)).max() > 1e-3 * np.abs(o_inj.coarse_rhs(Ur)).max()
