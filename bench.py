@@ -11,8 +11,8 @@ CUDA graph).
 Printed: one JSON line (rank 0).  ``value`` = time steps per second of the headline
 form; ``e2e`` = the same through the C ABI with host buffers copied in and out every
 step; ``roofline`` = the step's dominant kernel against the measured HBM copy
-bandwidth; ``pcg_hbm`` = GB/s of the PCG iteration on a large synthetic Poisson
-problem; ``cpu_baseline`` = the FP64 CPU oracle on a bounded sample.
+bandwidth; ``pcg_hbm`` = GB/s of the PCG iteration on synthetic n^2 x 2 Poisson
+problems (n = 1024, 2048, 4096: 1.05M to 16.8M rows, all far beyond L2); ``cpu_baseline`` = the FP64 CPU oracle on a bounded sample.
 
 ``--impl reference`` times the FP64 CPU oracle itself on the same workload.
 Under torchrun (N > 1) every rank runs an independent replica (the method has no
@@ -108,12 +108,13 @@ def workload_problem(name):
 
 
 def make_params(cg, w, form, use_graph=1, tol_inner=0.0):
-    mixed = form in ("mixed", "mixed_learned")
+    mixed = form in ("mixed", "mixed_learned", "mixed_zero")
     learned = form in ("learned", "mixed_learned")
+    guess = cg.CGP_GUESS_LEARNED if learned else (cg.CGP_GUESS_ZERO if form == "mixed_zero" else cg.CGP_GUESS_PREV)
     return cg.make_params(w.Re, w.dt, chi=w.chi, k=w.k, tol_mom=w.tol_mom, tol_poisson=w.tol_poisson,
                           tol_mass=1e-10, max_it_mom=1000, max_it_poisson=20000, max_it_mass=1000,
                           precision=cg.CGP_MIXED if mixed else cg.CGP_FP64,
-                          guess=cg.CGP_GUESS_LEARNED if learned else cg.CGP_GUESS_PREV, bc_kind=w.bc,
+                          guess=guess, bc_kind=w.bc,
                           bc_param=w.bc_param, use_graph=use_graph, tol_inner=tol_inner)
 
 
@@ -154,9 +155,10 @@ def train_guess(cg, w, args):
 # n rows, z = CSR entries of the level the kernel works on, t = triangles
 def kernel_bytes(name, n, z, t=0):
     table = {
-        "pois_spmv": 12 * z + 4 * n + 32 * n, "pois_update": 64 * n,
-        "mass_spmv": 12 * z + 4 * n + 32 * n, "mass_update": 64 * n,
-        "corr_spmv": 12 * z + 4 * n + 64 * n, "corr_update": 120 * n,
+        # FP64 PCG, three kernels per iteration: p = z + beta p; q = A p (gathers p); update
+        "pois_pupd": 24 * n, "pois_spmv": 12 * z + 4 * n + 16 * n, "pois_update": 64 * n,
+        "mass_pupd": 24 * n, "mass_spmv": 12 * z + 4 * n + 16 * n, "mass_update": 64 * n,
+        "corr_pupd": 48 * n, "corr_spmv": 12 * z + 4 * n + 32 * n, "corr_update": 120 * n,
         "bicg_v": 12 * z + 4 * n + 48 * n, "bicg_t": 12 * z + 4 * n + 48 * n,
         "bicg_p": 88 * n, "bicg_s": 72 * n, "bicg_x": 128 * n,
         "mom_assemble": 44 * z + 4 * n + 16 * n + 8 * n + 8 * n + 32 * n + 4 * n + 24 * t + 56 * t + 12 * t
@@ -236,7 +238,8 @@ def run_gpu(args, rank, world):
     keys = ("steps_per_s", "ms_per_step", "iters", "status", "guess_used", "res_poisson")
     forms = {head_form: {k: head[k] for k in keys}}
     if not args.quick:
-        for other in ("fp64", "mixed"):
+        # the coarse initial guesses side by side: previous increment (mixed), zero, learned
+        for other in ("fp64", "mixed", "mixed_zero"):
             if other != head_form:
                 s2, res = run_form(other, args.steps, args.warmup)
                 forms[other] = {k: res[k] for k in keys}
@@ -314,7 +317,7 @@ def run_gpu(args, rank, world):
     # PCG iteration bandwidth on a synthetic Poisson problem far larger than L2
     pcg = None
     if not args.quick and rank == 0:
-        pcg = pcg_bandwidth(cg, torch, args.pcg_n, peak)
+        pcg = [pcg_bandwidth(cg, torch, n, peak) for n in args.pcg_n]
     batch = None
     if not args.quick and args.batch > 0:
         batch = batch_throughput(cg, torch, args.batch, args.batch_steps, 3)
@@ -368,15 +371,16 @@ def pcg_bandwidth(cg, torch, n_side, peak):
     U = rng.standard_normal((nf, 2))
     cg.cgp_set_fields(s.handle, U, U, np.zeros(nf), 0.0)
     prof = cg.cgp_profile_step(s.handle)
-    sp, up = prof.get("pois_spmv"), prof.get("pois_update")
+    sp, up, pu = prof.get("pois_spmv"), prof.get("pois_update"), prof.get("pois_pupd")
     out = {"n": nc, "nnz": zc, "iters": it, "wall_ms_per_iter": round(1000 * wall / max(it, 1), 4)}
-    if sp and up:
-        b_iter = kernel_bytes("pois_spmv", nc, zc) + kernel_bytes("pois_update", nc, zc)
-        t_iter = (sp[1] / sp[0] + up[1] / up[0]) * 1e-3
+    if sp and up and pu:
+        b_iter = kernel_bytes("pois_spmv", nc, zc) + kernel_bytes("pois_update", nc, zc) + kernel_bytes("pois_pupd", nc, zc)
+        t_iter = (sp[1] / sp[0] + up[1] / up[0] + pu[1] / pu[0]) * 1e-3
         out.update({"bytes_per_iter": b_iter, "us_per_iter": round(1e6 * t_iter, 2),
                     "GBps": round(b_iter / t_iter / 1e9, 1), "frac": round(b_iter / t_iter / 1e9 / peak, 4),
                     "spmv_GBps": round(kernel_bytes("pois_spmv", nc, zc) / (sp[1] / sp[0] * 1e-3) / 1e9, 1),
-                    "update_GBps": round(kernel_bytes("pois_update", nc, zc) / (up[1] / up[0] * 1e-3) / 1e9, 1)})
+                    "update_GBps": round(kernel_bytes("pois_update", nc, zc) / (up[1] / up[0] * 1e-3) / 1e9, 1),
+                    "pupd_GBps": round(kernel_bytes("pois_pupd", nc, zc) / (pu[1] / pu[0] * 1e-3) / 1e9, 1)})
     s.close()
     mesh.close()
     return out
@@ -464,7 +468,8 @@ def main():
     ap.add_argument("--batch-steps", type=int, default=10)
     ap.add_argument("--train-pairs", type=int, default=150)
     ap.add_argument("--train-iters", type=int, default=400)
-    ap.add_argument("--pcg-n", type=int, default=2048)
+    ap.add_argument("--pcg-n", type=int, nargs="+", default=[1024, 2048, 4096],
+                    help="sides of the structured Poisson problems of the PCG bandwidth sweep")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--tol-inner", type=float, default=0.0,
                     help="mixed form: residual reduction of each FP32 inner solve (0: library default)")

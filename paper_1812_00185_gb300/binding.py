@@ -119,7 +119,8 @@ PROF_NAMES = ["mom_prep", "mom_assemble", "mom_setup", "mom_init", "bicg_p", "bi
               "phi_sub", "prolong", "corr_rhs", "corr_setup", "corr_init", "corr_spmv", "corr_update", "div",
               "mass_setup", "mass_init", "mass_spmv", "mass_update", "finish", "pois_onelaunch", "mlp_forward",
               "ir_resid", "ir_update", "to_f32", "f32_init", "f32_corr_spmv", "f32_corr_update", "f32_mass_spmv",
-              "f32_mass_update", "f32_bicg_p", "f32_bicg_v", "f32_bicg_s", "f32_bicg_t", "f32_bicg_x"]
+              "f32_mass_update", "f32_bicg_p", "f32_bicg_v", "f32_bicg_s", "f32_bicg_t", "f32_bicg_x",
+              "pois_pupd", "corr_pupd", "mass_pupd"]
 
 _LIB = None
 

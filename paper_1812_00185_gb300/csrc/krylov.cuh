@@ -252,6 +252,68 @@ __global__ void __launch_bounds__(kBlock) k_pcg_spmv(SellView A, const T* __rest
     }
 }
 
+// Three-kernel form (the FP64 solves): p = z + beta p in place, then q = A p gathers p
+// alone.  The stored p_j is the value the fused form recomputes for every neighbour, so the
+// iterates are the same; the SpMV does one FMA per entry instead of two, which matters on a
+// GPU with few FP64 units.
+template <int NC, class T = double>
+__global__ void __launch_bounds__(kBlock) k_pcg_pupd(int n, const T* __restrict__ z, T* __restrict__ p,
+                                                    const KrylovState* st) {
+    if (st->done) return;
+    T beta[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) beta[c] = (T)st->beta[c];
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        T zv[NC], pv[NC];
+        ldv<NC>(z, i, zv);
+        ldv<NC>(p, i, pv);
+#pragma unroll
+        for (int c = 0; c < NC; ++c) pv[c] = zv[c] + beta[c] * pv[c];
+        stv<NC>(p, i, pv);
+    }
+}
+
+// q = A p; pq = <p, q> -> alpha (three-kernel form)
+template <int NC, class T = double>
+__global__ void __launch_bounds__(kBlock) k_pcg_spmv3(SellView A, const T* __restrict__ val, const T* __restrict__ p,
+                                                     T* __restrict__ q, KrylovState* st, double* partials,
+                                                     unsigned int* ticket) {
+    if (st->done) return;
+    const int lane = threadIdx.x & 31;
+    T acc[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) acc[c] = T(0);
+    CGP_SLICE_LOOP(A, sl) {
+        const int i = sl * 32 + lane;
+        T ax[NC];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) ax[c] = T(0);
+        sell_accum<NC>(A, val, sl, lane, [&](int j, T (&o)[NC]) { ldv<NC>(p, j, o); }, ax);
+        if (i < A.n) {
+            T pv[NC];
+            ldv<NC>(p, i, pv);
+#pragma unroll
+            for (int c = 0; c < NC; ++c) acc[c] += pv[c] * ax[c];
+            stv<NC>(q, i, ax);
+        }
+    }
+    double tot[NC];
+    if (grid_sum<NC>(acc, partials, ticket, tot) && threadIdx.x == 0) {
+        for (int c = 0; c < NC; ++c) {
+            st->pq[c] = tot[c];
+            if (st->compdone[c]) {
+                st->alpha[c] = 0.0;
+            } else if (tot[c] != 0.0 && finite(tot[c])) {
+                st->alpha[c] = st->rz[c] / tot[c];
+            } else {
+                st->alpha[c] = 0.0;
+                st->compdone[c] = 1;
+                st->status = finite(tot[c]) ? CGP_EBREAKDOWN : CGP_ENONFINITE;
+            }
+        }
+    }
+}
+
 // x += alpha p, r -= alpha q, z = D^{-1} r; rz = <r,z>, rr = <r,r>; convergence test.
 template <int NC, class T = double>
 __global__ void __launch_bounds__(kBlock) k_pcg_update(int n, const T* __restrict__ dinv,

@@ -274,11 +274,11 @@ __global__ void k_finish(int nf, double* __restrict__ U, double* __restrict__ Up
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         *tdev = *tdev + dt;
         stats->steps += 1;
-        // launches of a graph replay: the fixed kernels, 5 per BiCGStab iteration and 4 per
-        // trip of a PCG loop body (two iterations per trip)
+        // launches of a graph replay: the fixed kernels, 5 per BiCGStab iteration and 6 per
+        // trip of an FP64 PCG loop body (two iterations per trip)
         int64_t l = fixed_launches + 5 * (int64_t)ks[KS_MOM].iter;
         for (int k = KS_POIS; k < KS_COUNT; ++k)
-            if (k != KS_POIS || pois_loop) l += 4 * (int64_t)((ks[k].iter + 1) / 2);
+            if (k != KS_POIS || pois_loop) l += 6 * (int64_t)((ks[k].iter + 1) / 2);
         // FP32 inner loops of the mixed form: 5 kernels per BiCGStab trip, 4 per PCG trip
         l += 5 * (int64_t)ks[KS_MOM].trips + 4 * (int64_t)(ks[KS_CORR].trips + ks[KS_MASS].trips);
         stats->launches += l;
@@ -395,13 +395,20 @@ static int krylov_loop(Ctx& c, KrylovState* ks, int max_trips, Init init, Body b
     return CGP_OK;
 }
 
-// PCG on (pattern A, values val, Jacobi dinv): b, x; NC components.  Body = two iterations
-// (the search direction alternates between two buffers).
+// profile id of the p update of the PCG whose setup id is pid
+static int pupd_id(int pid) {
+    return pid == CGP_PROF_POIS_SETUP ? CGP_PROF_POIS_PUPD : pid == CGP_PROF_CORR_SETUP ? CGP_PROF_CORR_PUPD
+                                                                                       : CGP_PROF_MASS_PUPD;
+}
+
+// PCG on (pattern A, values val, Jacobi dinv): b, x; NC components.  Three kernels per
+// iteration (p update, SpMV, update); body = two iterations.
 template <int NC>
 static int pcg(Ctx& c, SellView A, const double* val, const double* dinv, double* b, double* x, KrylovState* ks,
                double tol, int maxit, bool zero_x, bool project, int pid) {
     Solver& s = *c.s;
     const int gs = grid_rows(s, A.nslices * 32, 1), gv = grid_rows(s, A.n, 1);
+    const int pu = pupd_id(pid);
     auto init = [&, gs](cudaStream_t st, unsigned long long h) -> int {
         PL(c, pid, k_ks_setup<<<1, 1, 0, st>>>(ks, tol * tol, maxit));
         PL(c, pid + 1, k_pcg_init<NC><<<gs, kBlock, 0, st>>>(A, val, dinv, b, x, s.kr, s.kz, s.kp0, ks,
@@ -409,15 +416,13 @@ static int pcg(Ctx& c, SellView A, const double* val, const double* dinv, double
         CGP_LAUNCH_CHECK();
         return CGP_OK;
     };
-    auto body = [&, gs, gv](cudaStream_t st, unsigned long long h) -> int {
-        PL(c, pid + 2, k_pcg_spmv<NC><<<gs, kBlock, 0, st>>>(A, val, s.kz, s.kp0, s.kp1, s.kq, ks, s.partials,
-                                                                     s.tickets));
-        PL(c, pid + 3, k_pcg_update<NC><<<gv, kBlock, 0, st>>>(A.n, dinv, x, s.kr, s.kz, s.kp1, s.kq, ks, s.partials,
-                                                               s.tickets, h));
-        PL(c, pid + 2, k_pcg_spmv<NC><<<gs, kBlock, 0, st>>>(A, val, s.kz, s.kp1, s.kp0, s.kq, ks, s.partials,
-                                                                     s.tickets));
-        PL(c, pid + 3, k_pcg_update<NC><<<gv, kBlock, 0, st>>>(A.n, dinv, x, s.kr, s.kz, s.kp0, s.kq, ks, s.partials,
-                                                               s.tickets, h));
+    auto body = [&, gs, gv, pu](cudaStream_t st, unsigned long long h) -> int {
+        for (int it = 0; it < 2; ++it) {
+            PL(c, pu, k_pcg_pupd<NC><<<gv, kBlock, 0, st>>>(A.n, s.kz, s.kp0, ks));
+            PL(c, pid + 2, k_pcg_spmv3<NC><<<gs, kBlock, 0, st>>>(A, val, s.kp0, s.kq, ks, s.partials, s.tickets));
+            PL(c, pid + 3, k_pcg_update<NC><<<gv, kBlock, 0, st>>>(A.n, dinv, x, s.kr, s.kz, s.kp0, s.kq, ks,
+                                                                   s.partials, s.tickets, h));
+        }
         CGP_LAUNCH_CHECK();
         return CGP_OK;
     };
@@ -1240,9 +1245,9 @@ extern "C" int cgp_profile_step(cgp_solver* h, cgp_stream_t stream, int32_t n_id
         // first `iter` launches of each loop kernel (they run in order)
         auto solve_of = [](int id) {
             if (id >= CGP_PROF_BICG_P && id <= CGP_PROF_BICG_X) return (int)KS_MOM;
-            if (id == CGP_PROF_POIS_SPMV || id == CGP_PROF_POIS_UPDATE) return (int)KS_POIS;
-            if (id == CGP_PROF_CORR_SPMV || id == CGP_PROF_CORR_UPDATE) return (int)KS_CORR;
-            if (id == CGP_PROF_MASS_SPMV || id == CGP_PROF_MASS_UPDATE) return (int)KS_MASS;
+            if (id == CGP_PROF_POIS_SPMV || id == CGP_PROF_POIS_UPDATE || id == CGP_PROF_POIS_PUPD) return (int)KS_POIS;
+            if (id == CGP_PROF_CORR_SPMV || id == CGP_PROF_CORR_UPDATE || id == CGP_PROF_CORR_PUPD) return (int)KS_CORR;
+            if (id == CGP_PROF_MASS_SPMV || id == CGP_PROF_MASS_UPDATE || id == CGP_PROF_MASS_PUPD) return (int)KS_MASS;
             return -1;
         };
         for (int k = 0; k < pr.n; ++k) {
