@@ -359,6 +359,9 @@ extern "C" int cgp_assemble(const cgp_mesh* mesh, const cgp_params* params, void
     int rc = init_state(&s, st);
     if (rc != CGP_OK) return fail(rc);
     if (cudaStreamCreateWithFlags(&s.side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&s.branch, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&s.ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&s.ev_join, cudaEventDisableTiming) != cudaSuccess ||
         cudaMallocHost(&s.h_flag, sizeof(int)) != cudaSuccess) {
         set_error("stream / pinned flag creation failed");
         return fail(CGP_ECUDA);
@@ -421,6 +424,9 @@ extern "C" void cgp_solver_destroy(cgp_solver* h) {
     if (s.step_exec) cudaGraphExecDestroy(s.step_exec);
     if (s.step_graph) cudaGraphDestroy(s.step_graph);
     if (s.side) cudaStreamDestroy(s.side);
+    if (s.branch) cudaStreamDestroy(s.branch);
+    if (s.ev_fork) cudaEventDestroy(s.ev_fork);
+    if (s.ev_join) cudaEventDestroy(s.ev_join);
     if (s.h_flag) cudaFreeHost(s.h_flag);
     delete h;
 }

@@ -66,7 +66,9 @@ struct Solver {
     int coarse_grid = 0;          // CTAs of the persistent (cooperative) solver
     bool coarse_rr = false;       // the persistent FP64 solve may keep its rows in registers
     double *user_ud = nullptr, *user_f = nullptr;   // CGP_BC_USER: 2*nf each
-    bool coarse_fp64 = true;      // the coarse solve's inner iterations run in FP64
+    bool coarse_fp64 = true;
+    cudaStream_t branch = nullptr;                 // second stream of a step (work beside the coarse solve)
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;      // the coarse solve's inner iterations run in FP64
     size_t onchip_bytes = 0;      // mixed: shared memory per CTA of the on-chip cluster solve (0 = not used)
     // mixed: workspace arrays of the on-chip plan (sized for the coarse level) and its device view
     int32_t *oc_slist = nullptr, *oc_soff = nullptr, *oc_ebase = nullptr, *oc_li = nullptr, *oc_src = nullptr;
@@ -123,7 +125,7 @@ struct Ctx {
 // helpers implemented in step.cu / assemble.cu
 int enqueue_step(Solver* s, cudaStream_t st, bool capture);
 int step_pre(Ctx& c);             // Eq. 21, Eqs. 22-23 right-hand side, learned prediction
-int step_post(Ctx& c);            // Eqs. 24-26 and the end of the step
+int step_post(Ctx& c, bool mass_done = false);   // Eqs. 24-26 and the end of the step
 size_t coarse_args_size();
 void fill_coarse_args(Solver& s, void* dst);
 int batch_clusters(int csize, int threads, int* nclusters);

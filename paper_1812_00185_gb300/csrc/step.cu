@@ -913,8 +913,30 @@ int step_pre(Ctx& c) {
     return learned_guess(c);
 }
 
-// Eqs. 24-26 and the end of the step
-int step_post(Ctx& c) {
+// The rotational term of Eq. 26: M q = Cx u~ + Cy v~ (consistent M), or its lumped form.
+// It needs only U~, so it may run beside the coarse solve.
+static int rotational_term(Ctx& c) {
+    Solver& s = *c.s;
+    const cgp_params& p = s.prm;
+    const Level& F = s.mesh->lev[s.lf];
+    SellView Af = sell_of(F);
+    const int gs = grid_rows(s, F.nslices * 32, 1);
+    const bool lumped = p.mass_mode == CGP_MASS_LUMPED, mixed = p.precision == CGP_MIXED;
+    PL(c, CGP_PROF_DIV,
+       k_div<<<gs, kBlock, 0, c.st>>>(Af, s.Cx, s.Cy, s.Ut, s.div, lumped ? s.mlumpF : nullptr, s.qrot));
+    CGP_LAUNCH_CHECK();
+    if (!lumped && mixed)
+        CGP_TRY(pcg_mixed<1>(c, Af, s.M, s.Mf, s.dinvM, s.dinvMf, s.div, s.qrot, &s.ks[KS_MASS], p.tol_mass,
+                             p.max_it_mass, true, CGP_PROF_MASS_SETUP, CGP_PROF_F32_MASS_SPMV,
+                             CGP_PROF_F32_MASS_UPDATE));
+    else if (!lumped)
+        CGP_TRY(pcg<1>(c, Af, s.M, s.dinvM, s.div, s.qrot, &s.ks[KS_MASS], p.tol_mass, p.max_it_mass, true, false,
+                       CGP_PROF_MASS_SETUP));
+    return CGP_OK;
+}
+
+// Eqs. 24-26 and the end of the step (mass_done: the rotational term was formed already)
+int step_post(Ctx& c, bool mass_done) {
     Solver& s = *c.s;
     const cgp_params& p = s.prm;
     const Level& F = s.mesh->lev[s.lf];
@@ -936,18 +958,7 @@ int step_post(Ctx& c) {
         CGP_TRY(pcg<2>(c, Af, s.M0, s.dinvM0, s.g, s.delta, &s.ks[KS_CORR], p.tol_mass, p.max_it_mass, true, false,
                        CGP_PROF_CORR_SETUP));
     // Eq. 26: pressure
-    if (p.chi) {
-        PL(c, CGP_PROF_DIV,
-           k_div<<<gs, kBlock, 0, c.st>>>(Af, s.Cx, s.Cy, s.Ut, s.div, lumped ? s.mlumpF : nullptr, s.qrot));
-        CGP_LAUNCH_CHECK();
-        if (!lumped && mixed)
-            CGP_TRY(pcg_mixed<1>(c, Af, s.M, s.Mf, s.dinvM, s.dinvMf, s.div, s.qrot, &s.ks[KS_MASS], p.tol_mass,
-                                 p.max_it_mass, true, CGP_PROF_MASS_SETUP, CGP_PROF_F32_MASS_SPMV,
-                                 CGP_PROF_F32_MASS_UPDATE));
-        else if (!lumped)
-            CGP_TRY(pcg<1>(c, Af, s.M, s.dinvM, s.div, s.qrot, &s.ks[KS_MASS], p.tol_mass, p.max_it_mass, true, false,
-                           CGP_PROF_MASS_SETUP));
-    }
+    if (p.chi && !mass_done) CGP_TRY(rotational_term(c));
     const bool one_launch = s.coarse_kind != CGP_COARSE_KERNELS;
     const int coarse_fixed = (one_launch ? 1 : 2 + (s.pure_neumann ? 2 : 0)) +
                              ((p.guess == CGP_GUESS_LEARNED && s.guess_ready) ? 10 : 0);
@@ -965,9 +976,26 @@ int step_post(Ctx& c) {
 }
 
 static int step_body(Ctx& c) {
+    Solver& s = *c.s;
+    const cgp_params& p = s.prm;
     CGP_TRY(step_pre(c));
+    // The on-chip coarse solve holds 16 SMs for most of the step; the rotational term of
+    // Eq. 26 (its own mass solve) depends only on U~, so it runs on the other SMs meanwhile,
+    // on a second stream.  Nothing on the main stream reduces into the shared scratch until
+    // the branches join, before Eq. 24 (the velocity correction solve uses the same scratch).
+    const bool overlap = !c.prof && s.onchip_bytes && p.chi && p.mass_mode != CGP_MASS_LUMPED && s.branch;
+    if (!overlap) {
+        CGP_TRY(coarse_solve(c));
+        return step_post(c, false);
+    }
+    CGP_CUDA(cudaEventRecord(s.ev_fork, c.st));
+    CGP_CUDA(cudaStreamWaitEvent(s.branch, s.ev_fork, 0));
     CGP_TRY(coarse_solve(c));
-    return step_post(c);
+    Ctx b{c.s, s.branch, c.capture, nullptr};
+    CGP_TRY(rotational_term(b));
+    CGP_CUDA(cudaEventRecord(s.ev_join, s.branch));
+    CGP_CUDA(cudaStreamWaitEvent(c.st, s.ev_join, 0));
+    return step_post(c, true);
 }
 
 int init_state(Solver* s, cudaStream_t st) {
