@@ -108,14 +108,15 @@ def workload_problem(name):
 
 
 def make_params(cg, w, form, use_graph=1, tol_inner=0.0):
-    mixed = form in ("mixed", "mixed_learned", "mixed_zero")
+    mixed = form in ("mixed", "mixed_learned", "mixed_zero", "mixed_jacobi")
     learned = form in ("learned", "mixed_learned")
     guess = cg.CGP_GUESS_LEARNED if learned else (cg.CGP_GUESS_ZERO if form == "mixed_zero" else cg.CGP_GUESS_PREV)
     return cg.make_params(w.Re, w.dt, chi=w.chi, k=w.k, tol_mom=w.tol_mom, tol_poisson=w.tol_poisson,
                           tol_mass=1e-10, max_it_mom=1000, max_it_poisson=20000, max_it_mass=1000,
                           precision=cg.CGP_MIXED if mixed else cg.CGP_FP64,
                           guess=guess, bc_kind=w.bc,
-                          bc_param=w.bc_param, use_graph=use_graph, tol_inner=tol_inner)
+                          bc_param=w.bc_param, use_graph=use_graph, tol_inner=tol_inner,
+                          precond=cg.CGP_PRECOND_JACOBI if form == "mixed_jacobi" else cg.CGP_PRECOND_AUTO)
 
 
 def train_guess(cg, w, args):
@@ -238,8 +239,9 @@ def run_gpu(args, rank, world):
     keys = ("steps_per_s", "ms_per_step", "iters", "status", "guess_used", "res_poisson")
     forms = {head_form: {k: head[k] for k in keys}}
     if not args.quick:
-        # the coarse initial guesses side by side: previous increment (mixed), zero, learned
-        for other in ("fp64", "mixed", "mixed_zero"):
+        # the coarse initial guesses side by side: previous increment (mixed), zero, learned;
+        # and the on-chip solve with Jacobi alone instead of Jacobi + the subdomain correction
+        for other in ("fp64", "mixed", "mixed_zero", "mixed_jacobi"):
             if other != head_form:
                 s2, res = run_form(other, args.steps, args.warmup)
                 forms[other] = {k: res[k] for k in keys}
@@ -463,7 +465,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--workload", default="channel1m_k2")
-    ap.add_argument("--form", default="mixed_learned", choices=["fp64", "mixed", "learned", "mixed_learned"])
+    ap.add_argument("--form", default="mixed_learned",
+                    choices=["fp64", "mixed", "learned", "mixed_learned", "mixed_zero", "mixed_jacobi"])
     ap.add_argument("--batch", type=int, default=256, help="instances of the batched form (0: skip)")
     ap.add_argument("--batch-steps", type=int, default=10)
     ap.add_argument("--train-pairs", type=int, default=150)
@@ -476,6 +479,8 @@ def main():
     ap.add_argument("--quick", action="store_true", help="skip the secondary measurements")
     ap.add_argument("--graph", type=int, default=1, choices=[0, 1],
                     help="1: replay steps as CUDA graphs; 0: eager launches (what ncu can profile)")
+    ap.add_argument("--pcg-only", action="store_true",
+                    help="print only the PCG bandwidth sweep (one JSON line per problem size)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "gpu":
         args.warmup = 3
@@ -495,6 +500,16 @@ def main():
             "cpu_baseline": res,
             "e2e": {"value": res["value"], "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
         }))
+        return 0
+
+    if args.pcg_only:
+        if rank != 0:
+            return 0
+        import torch
+        from paper_1812_00185_gb300 import binding as cg
+        peak, _ = _peaks()
+        for n in args.pcg_n:
+            print(json.dumps(pcg_bandwidth(cg, torch, n, peak)), flush=True)
         return 0
 
     if world > 1:

@@ -100,6 +100,7 @@ typedef struct {
     int32_t coarse_mode;       /* coarse Poisson solver: CGP_COARSE_* */
     int32_t cluster_size;      /* CTAs of the cluster solver (0 = largest that fits, else 2..16) */
     int32_t restrict_mode;     /* CGP_RESTRICT_*: how the right-hand side of Eq. 23 reaches the coarse level */
+    int32_t precond;           /* CGP_PRECOND_*: preconditioner of the coarse Poisson PCG */
 } cgp_params;
 
 /* INJECT (the paper, Eqs. 22-23): inject U~ at the coarse vertices, then the coarse
@@ -107,6 +108,15 @@ typedef struct {
  * restricted by the transpose of the prolongation of Eq. 24, the Galerkin-consistent
  * right-hand side; the two agree when U~ is the prolongation of a coarse field. */
 enum { CGP_RESTRICT_INJECT = 0, CGP_RESTRICT_PT = 1 };
+
+/* Preconditioner of the coarse Poisson PCG (Eq. 23).  JACOBI: M^{-1} = D^{-1}.  COARSE
+ * (a variant, not in the paper): Jacobi plus an additive subdomain coarse correction,
+ * M^{-1} = D^{-1} + Z E^+ Z^T with Z the indicator vectors of up to 128 compact vertex
+ * subdomains (phi = 0 vertices in none) and E^+ the pseudo-inverse of E = Z^T K_c Z, built
+ * once at cgp_assemble; only the ONCHIP coarse solver has it (cgp_assemble fails with
+ * CGP_EINVAL otherwise).  AUTO: COARSE where the ONCHIP solver runs, JACOBI elsewhere.
+ * The solution is the same to the solve's tolerance; only the iteration count changes. */
+enum { CGP_PRECOND_AUTO = 0, CGP_PRECOND_JACOBI = 1, CGP_PRECOND_COARSE = 2 };
 
 /* Coarse Poisson solver kinds.  KERNELS: two kernel launches per PCG iteration (graph
  * WHILE loop).  PERSISTENT: the whole solve in one cooperative launch over the GPU with a
@@ -209,6 +219,9 @@ int cgp_solver_info(const cgp_solver* s, int32_t* n_fine, int32_t* n_coarse, int
  * *ctas = CTAs of its launch (0 for KERNELS), *cluster = CTAs per cluster (0 if none).
  * Any output pointer may be NULL.  CGP_EINVAL before cgp_assemble. */
 int cgp_coarse_info(const cgp_solver* s, int32_t* kind, int32_t* ctas, int32_t* cluster);
+/* Subdomains of the coarse solve's coarse correction (0: Jacobi alone), through *nsub.
+ * CGP_EINVAL before cgp_assemble. */
+int cgp_coarse_subdomains(const cgp_solver* s, int32_t* nsub);
 
 /* Eq. 23 alone: solve K_c phi = rhs (N_c values; phi=0 rows and the pure-Neumann
  * projection/mean fix as in a step) with the configured precision and tolerance.

@@ -19,6 +19,7 @@ CGP_OK, CGP_EINVAL, CGP_ENOTCONV, CGP_EBREAKDOWN, CGP_ENONFINITE, CGP_ETIMEOUT, 
 CGP_VEL_DIR, CGP_PHI_ZERO = 1, 2
 CGP_BC_CAVITY, CGP_BC_CHANNEL, CGP_BC_TG, CGP_BC_TG_PERIODIC, CGP_BC_USER = 0, 1, 2, 3, 4
 CGP_RESTRICT_INJECT, CGP_RESTRICT_PT = 0, 1
+CGP_PRECOND_AUTO, CGP_PRECOND_JACOBI, CGP_PRECOND_COARSE = 0, 1, 2
 CGP_FP64, CGP_MIXED = 0, 1
 CGP_GUESS_ZERO, CGP_GUESS_PREV, CGP_GUESS_LEARNED = 0, 1, 2
 CGP_MASS_CONSISTENT, CGP_MASS_LUMPED = 0, 1
@@ -52,7 +53,7 @@ class Params(ctypes.Structure):
                 ("precision", c_int32), ("guess", c_int32), ("mass_mode", c_int32), ("bc_kind", c_int32),
                 ("bc_param", c_double * 4), ("use_graph", c_int32), ("tol_inner", c_double),
                 ("coarse_mode", c_int32), ("cluster_size", c_int32),
-                ("restrict_mode", c_int32)]
+                ("restrict_mode", c_int32), ("precond", c_int32)]
 
 
 class Stats(ctypes.Structure):
@@ -88,6 +89,7 @@ _SIGS = {
     "cgp_set_forcing": (c_int32, [c_void_p, c_void_p, c_int32, c_void_p]),
     "cgp_record_pairs": (c_int32, [c_void_p, c_int32, c_void_p, c_void_p, c_void_p, c_int32, c_void_p]),
     "cgp_coarse_info": (c_int32, [c_void_p, POINTER(c_int32), POINTER(c_int32), POINTER(c_int32)]),
+    "cgp_coarse_subdomains": (c_int32, [c_void_p, POINTER(c_int32)]),
     "cgp_poisson_solve": (c_int32, [c_void_p, c_void_p, c_void_p, POINTER(c_int32), c_int32, c_void_p]),
     "cgp_prolong": (c_int32, [c_void_p, c_void_p, c_void_p, c_int32, c_void_p]),
     "cgp_profile_step": (c_int32, [c_void_p, c_void_p, c_int32, c_void_p, c_void_p]),
@@ -212,7 +214,7 @@ def cgp_mesh_destroy(mesh):
 def make_params(Re, dt, chi=0, k=1, tol_mom=1e-10, tol_poisson=1e-10, tol_mass=1e-12, max_it_mom=500,
                 max_it_poisson=20000, max_it_mass=500, precision=CGP_FP64, guess=CGP_GUESS_PREV,
                 mass_mode=CGP_MASS_CONSISTENT, bc_kind=CGP_BC_CAVITY, bc_param=(1.0, 0.0, 0.0, 0.0),
-                use_graph=1, tol_inner=0.0, coarse_mode=0, cluster_size=0, restrict_mode=0):
+                use_graph=1, tol_inner=0.0, coarse_mode=0, cluster_size=0, restrict_mode=0, precond=0):
     p = Params()
     p.Re, p.dt, p.chi, p.k = Re, dt, chi, k
     p.tol_mom, p.tol_poisson, p.tol_mass = tol_mom, tol_poisson, tol_mass
@@ -223,6 +225,7 @@ def make_params(Re, dt, chi=0, k=1, tol_mom=1e-10, tol_poisson=1e-10, tol_mass=1
     p.use_graph = use_graph
     p.tol_inner, p.coarse_mode, p.cluster_size = tol_inner, coarse_mode, cluster_size
     p.restrict_mode = restrict_mode
+    p.precond = precond
     return p
 
 
@@ -290,6 +293,13 @@ def cgp_coarse_info(solver):
     k, n, c = c_int32(), c_int32(), c_int32()
     _check(load().cgp_coarse_info(solver, byref(k), byref(n), byref(c)))
     return k.value, n.value, c.value
+
+
+def cgp_coarse_subdomains(solver):
+    """Subdomains of the coarse solve's coarse correction (0: Jacobi alone)."""
+    m = c_int32()
+    _check(load().cgp_coarse_subdomains(solver, byref(m)))
+    return m.value
 
 
 def cgp_solver_info(solver):
@@ -486,6 +496,9 @@ class Solver:
 
     def coarse_info(self):
         return cgp_coarse_info(self.handle)
+
+    def coarse_subdomains(self):
+        return cgp_coarse_subdomains(self.handle)
 
     def matrix(self, which):
         return cgp_get_matrix(self.handle, which)

@@ -167,15 +167,23 @@ static int layout(Solver& s, void* base, size_t* bytes) {
     }
     s.cw32 = cv.take<float>(9 * nc);
     if (s.prm.precision == CGP_MIXED) {
-        s.oc_slist = cv.take<int32_t>(C.nslices);
-        s.oc_ebase = cv.take<int32_t>(C.nslices);
+        // on-chip plan: at most kOnchipMaxCluster x 16 warps x kOnchipRows slices; entries: the
+        // matrix, plus per leaf (rows sorted by length) one slice of the longest row (<= 64),
+        // plus padding to 4-entry steps
+        const size_t npos = (size_t)kOnchipMaxCluster * kOnchipWarps * kOnchipRows;
+        const size_t nent = nnzc + (size_t)kOnchipMaxCluster * kOnchipWarps * 32 * 64 + 96 * npos;
+        s.oc_grow = cv.take<int32_t>(32 * npos);
+        s.oc_ebase = cv.take<int32_t>(npos);
+        s.oc_width = cv.take<int32_t>(npos);
         s.oc_soff = cv.take<int32_t>(kOnchipMaxCluster + 1);
         s.oc_send_off = cv.take<int32_t>(kOnchipMaxCluster + 1);
         s.oc_halo_n = cv.take<int32_t>(kOnchipMaxCluster);
-        s.oc_li = cv.take<int32_t>(nnzc + (size_t)96 * C.nslices);   // + padding to 4-entry steps
-        s.oc_src = cv.take<int32_t>(nnzc + (size_t)96 * C.nslices);
+        s.oc_li = cv.take<int32_t>(nent);
+        s.oc_src = cv.take<int32_t>(nent);
         s.oc_send_lr = cv.take<int32_t>(nnzc);     // sends <= entries with a remote column
         s.oc_send_dst = cv.take<int32_t>(nnzc);
+        s.oc_hsub = cv.take<uint8_t>((size_t)kOnchipMaxCluster * (nc < 65535 ? nc : 65535));
+        s.oc_einv = cv.take<float>((size_t)kOnchipMaxCluster * kOnchipMaxSubPerCta * kOnchipMaxCluster * kOnchipMaxSubPerCta);
         s.Af = cv.take<float>(nnzf);
         s.M0f = cv.take<float>(nnzf);
         s.Mf = cv.take<float>(nnzf);
@@ -222,7 +230,7 @@ static int check_params(const cgp_mesh* m, const cgp_params* p) {
     }
     if (p->k < 0 || p->k > m->n_levels || !(p->Re > 0) || !(p->dt > 0) || (p->chi != 0 && p->chi != 1) ||
         !(p->tol_mom > 0) || !(p->tol_poisson > 0) || !(p->tol_mass > 0) || p->max_it_mom < 1 ||
-        p->max_it_poisson < 1 || p->max_it_mass < 1 || p->bc_kind < 0 || p->bc_kind > CGP_BC_USER || p->restrict_mode < 0 || p->restrict_mode > CGP_RESTRICT_PT ||
+        p->max_it_poisson < 1 || p->max_it_mass < 1 || p->bc_kind < 0 || p->bc_kind > CGP_BC_USER || p->restrict_mode < 0 || p->restrict_mode > CGP_RESTRICT_PT || p->precond < 0 || p->precond > CGP_PRECOND_COARSE ||
         (p->precision != CGP_FP64 && p->precision != CGP_MIXED) || p->guess < 0 || p->guess > 2 ||
         (p->mass_mode != CGP_MASS_CONSISTENT && p->mass_mode != CGP_MASS_LUMPED) || p->coarse_mode < 0 ||
         p->coarse_mode > CGP_COARSE_ONCHIP || p->cluster_size < 0 || p->cluster_size > 16 || p->tol_inner < 0 ||
@@ -343,7 +351,7 @@ extern "C" int cgp_assemble(const cgp_mesh* mesh, const cgp_params* params, void
         return fail(CGP_ECUDA);
     }
     {
-        int rc = choose_coarse_solver(s);
+        int rc = choose_coarse_solver(s, st);
         if (rc != CGP_OK) return fail(rc);
     }
     if (cudaMemsetAsync(s.tickets, 0, 64 * sizeof(unsigned int), st) != cudaSuccess ||

@@ -4,17 +4,18 @@
 // The coarse systems of CGP are small (tens of thousands of rows), and on this GPU the FP64
 // pipe is narrow while a cluster barrier is far cheaper than a grid-wide one, so the FP32
 // inner PCG of the mixed form runs on a single cluster of 8 or 16 CTAs.  A host-side plan
-// (onchip_plan.cu) gives each CTA a spatially compact set of SELL-32 slices.  Each CTA keeps
-// in its shared memory:
+// (onchip_plan.cu) gives each warp a spatially compact patch of rows (each CTA the patches
+// of one region).  Each CTA keeps in its shared memory:
 //   * z for its own rows followed by a halo: z of the other CTAs' rows that its rows use;
-//   * its slices of the FP32 matrix, each entry as (index of its column's z, value), widths
-//     padded to whole 4-entry steps;
+//   * its rows of the FP32 matrix, 32-row slices, each entry as (index of its column's z,
+//     value), widths padded to whole 4-entry steps;
 //   * a send list: after z changes, every CTA stores the z its neighbours need straight
-//     into their halos (remote shared-memory stores), before the barrier of the reduction
-//     that follows, so every gather of the SpMV is a local shared-memory load;
+//     into their halos (remote shared-memory stores) with the reduction that follows, so
+//     every gather of the SpMV is a local shared-memory load;
 //   * the slots of the cluster reductions: every CTA stores its partial sums into every
-//     other CTA's slot array, then one hardware cluster barrier makes them visible and each
-//     CTA adds the slots in the same fixed order (identical scalars everywhere).
+//     other CTA's slot array and each CTA adds the slots in the same fixed order (identical
+//     scalars everywhere);
+//   * E^+ of the preconditioner's coarse space (below).
 // The inner iteration is classical PCG with the SpMV applied to z: w = A z, p = z + beta p,
 // q = w + beta q (= A p), so z is the only vector that travels; the other vectors (e, r, z,
 // p, q, D^{-1}) live in registers.  Two reductions per iteration (<p, q>, then <r, z> and
@@ -22,6 +23,17 @@
 // inside the FP32 range.  The FP64 outer loop (true residual, its norm, the convergence
 // test, x += ||r|| e) reads the FP64 matrix and x from global memory a few times per solve;
 // only warp 0 of each CTA does its FP64 scalar work.
+//
+// Preconditioner: Jacobi, or Jacobi plus an additive subdomain coarse correction,
+//     z = D^{-1} r + Z E^+ Z^T r,   E = Z^T A Z,
+// where column j of Z is the indicator of subdomain j (a group of sibling warp patches; phi =
+// 0 rows belong to none) and E^+ is the pseudo-inverse of the small Galerkin matrix, held by
+// every CTA.  M^{-1} stays symmetric positive definite, so the iteration is still PCG; the
+// coarse space removes the smooth error components Jacobi damps slowest (the iteration
+// count drops several-fold on the coarse Poisson systems of CGP).  Its cost rides on the
+// existing reductions: Z^T r is a set of warp sums that travels with <r, D^{-1} r>, every
+// CTA forms mu = E^+ Z^T r, and <r, z> = <r, D^{-1} r> + (Z^T r)^T mu needs no extra
+// exchange; z of the halo rows is corrected by the receiver (mu is identical everywhere).
 #pragma once
 
 #include <cooperative_groups.h>
@@ -80,7 +92,7 @@ constexpr long long kOnchipWaitCycles = 4000000000LL;   // ~2 s: a wait this lon
 // what warp 0 tells its CTA after an FP64 reduction
 struct OnchipScalars {
     int act;
-    float rz0, stop2;          // scaled inner problem: <r, z> and the stop threshold on <r, r>
+    float stop2;               // stop threshold of the scaled inner problem on <r, r>
     double inv, norm, mu;      // 1 / ||r||, ||r|| of the outer residual; mean of the Neumann fix
 };
 
@@ -88,41 +100,48 @@ static __global__ void __launch_bounds__(kOnchipThreads, 1) k_pcg_onchip(CoarseP
     namespace cg = cooperative_groups;
     cg::cluster_group cluster = cg::this_cluster();
     extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ double wsum[kOnchipThreads / 32][4];
-    __shared__ float wsum32[kOnchipThreads / 32][4];
+    __shared__ double wsum[kOnchipWarps][4];
+    __shared__ float wsum32[kOnchipWarps][4];
     __shared__ OnchipScalars sc;
     __shared__ __align__(8) uint64_t mbar[2];     // FP32 reductions, alternating
     __shared__ uint32_t mbar_remote[kOnchipMaxCluster][2];
     __shared__ float tot32[4];
     __shared__ int abort_flag;
     const int rank = (int)cluster.block_rank(), ncl = (int)cluster.num_blocks();
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = kOnchipWarps;
     const SellView& A = a.A;
-    const int rows_max = pl.rows_max, zn = rows_max + pl.halo_max;
+    const int rows_max = pl.rows_max, zn = rows_max + pl.halo_max, m = pl.nsub;
     float* zl = reinterpret_cast<float*>(smem);
     double* red64 = reinterpret_cast<double*>(smem + onchip_z_bytes(rows_max, pl.halo_max));
     float* red32 = reinterpret_cast<float*>(red64 + 128);
-    uint2* send = reinterpret_cast<uint2*>(red32 + 128);
-    uint2* cent = reinterpret_cast<uint2*>(send + pl.send_max);   // (local index of z, value bits)
-    const int q0 = __ldg(pl.soff + rank), nsl = __ldg(pl.soff + rank + 1) - q0;
-    const int eb0 = nsl > 0 ? __ldg(pl.ebase + q0) : 0;
+    float* einv = red32 + 2 * 16 * kOnchipSlot;
+    float* mu = einv + m * m;                     // mu[m] = 0: rows outside the coarse space
+    float* qf = mu + ((m + 4) & ~3);
+    uint8_t* hsub = reinterpret_cast<uint8_t*>(qf + 16);
+    uint2* send = reinterpret_cast<uint2*>(hsub + ((pl.halo_max + 15) & ~15));
+    uint2* cent = send + pl.send_max;             // (local index of z, value bits)
+    const int q0 = __ldg(pl.soff + rank), npos = __ldg(pl.soff + rank + 1) - q0;
+    const int eb0 = npos > 0 ? __ldg(pl.ebase + q0) : 0;
+    const int halo_self = __ldg(pl.halo_n + rank);
     for (int i = threadIdx.x; i < zn; i += blockDim.x) zl[i] = 0.0f;
-    // ---- rows of this thread: list positions wid + nw * t of its CTA (a warp owns whole
-    // slices); their matrix entries are copied to shared memory by the owning warp
+    for (int i = threadIdx.x; i < m * m; i += blockDim.x) einv[i] = __ldg(pl.einv + i);
+    for (int i = threadIdx.x; i < ((m + 4) & ~3); i += blockDim.x) mu[i] = 0.0f;
+    for (int h = threadIdx.x; h < halo_self; h += blockDim.x) hsub[h] = __ldg(pl.hsub + (size_t)rank * pl.halo_max + h);
+    // ---- rows of this thread: slice t of its warp is list position wid + nw * t of its CTA;
+    // their matrix entries are copied to shared memory by the owning warp
     int nrow = 0;
-    int base_[kOnchipRows], width_[kOnchipRows], slice_[kOnchipRows];
+    int base_[kOnchipRows], width_[kOnchipRows], grow_[kOnchipRows];
 #pragma unroll
     for (int t = 0; t < kOnchipRows; ++t) {
         const int q = wid + nw * t;
         base_[t] = 0;
         width_[t] = 0;
-        slice_[t] = -1;
-        if (q < nsl) {
+        grow_[t] = -1;
+        if (q < npos) {
             nrow = t + 1;
-            const int sl = __ldg(pl.slist + q0 + q);
-            slice_[t] = sl;
             base_[t] = __ldg(pl.ebase + q0 + q) - eb0;
-            width_[t] = onchip_width4((__ldg(A.ptr + sl + 1) - __ldg(A.ptr + sl)) >> 5);
+            width_[t] = __ldg(pl.width + q0 + q);
+            grow_[t] = __ldg(pl.grow + 32 * (size_t)(q0 + q) + lane);
             for (int k = 0; k < width_[t]; ++k) {
                 const int el = base_[t] + 32 * k + lane;
                 const int src = __ldg(pl.src + eb0 + el);
@@ -131,10 +150,13 @@ static __global__ void __launch_bounds__(kOnchipThreads, 1) k_pcg_onchip(CoarseP
         }
     }
     auto row_of = [&](int t) {   // global row of slot t, or -1
-        const int i = 32 * slice_[t] + lane;
-        return (slice_[t] >= 0 && i < A.n) ? i : -1;
+        const int g = grow_[t];
+        return g >= 0 ? g : (g == -1 ? -1 : -2 - g);
     };
+    auto in_space = [&](int t) { return grow_[t] >= 0; };
     auto lrow_of = [&](int t) { return 32 * (wid + nw * t) + lane; };
+    const int spc = m ? nw / pl.wpg : 0;                       // subdomains per CTA
+    const int my_sub = m ? (rank * nw + wid) / pl.wpg : m;     // this warp's subdomain
     const int ns0 = __ldg(pl.send_off + rank), nsend = __ldg(pl.send_off + rank + 1) - ns0;
     for (int i = threadIdx.x; i < nsend; i += blockDim.x) {
         const int d = __ldg(pl.send_dst + ns0 + i);   // x: local row | destination rank << 16
@@ -151,17 +173,9 @@ static __global__ void __launch_bounds__(kOnchipThreads, 1) k_pcg_onchip(CoarseP
         mbar_remote[threadIdx.x][0] = oc_map(&mbar[0], threadIdx.x);
         mbar_remote[threadIdx.x][1] = oc_map(&mbar[1], threadIdx.x);
     }
-    const int halo_self = __ldg(pl.halo_n + rank);
     // remote slot addresses of the reductions: lane l < ncl stores into CTA l
     const uint32_t red64_remote = oc_map(red64, lane < ncl ? lane : 0);
     const uint32_t red32_remote = oc_map(red32, lane < ncl ? lane : 0);
-    // z of the own rows to the neighbours' halos (after a __syncthreads, before a barrier)
-    auto push = [&]() {
-        for (int i = threadIdx.x; i < nsend; i += blockDim.x) {
-            const uint2 sd = send[i];
-            oc_st32(sd.y, zl[sd.x & 0xFFFF]);
-        }
-    };
     // Cluster sums.  Partial sums go warp -> CTA (warp 0) -> every CTA's slot array, one
     // hardware cluster barrier, then the ncl slots are added; all in a fixed order, so every
     // CTA gets the same totals.  Consecutive reductions alternate between two slot sets, so a
@@ -197,18 +211,26 @@ static __global__ void __launch_bounds__(kOnchipThreads, 1) k_pcg_onchip(CoarseP
     // reduction m+2 can only be sent once every CTA has contributed to m+1, that is after this
     // CTA finished m); warp 0 waits (bounded) and adds the slots, the CTA reads the totals
     // after a __syncthreads.  With `publish`, the CTA's new z goes to the neighbours' halos the
-    // same way (every CTA expects its halo size in bytes).  A wait that runs out sets the
-    // abort flag of every CTA; the solve then stops with CGP_ETIMEOUT.
-    int mred = 0;
-    auto cred32 = [&](float (&v)[2], int nr, float (&tot)[2], bool publish) -> bool {
+    // same way (every CTA expects its halo size in bytes).  With `subs`, the warp sums of
+    // `subv` are added per subdomain and the spc subdomain sums of every CTA travel too; they
+    // stay in the slots (set `last_par`) for the coarse correction.  A wait that runs out sets
+    // the abort flag of every CTA; the solve then stops with CGP_ETIMEOUT.
+    int mred = 0, last_par = 0;
+    auto cred32 = [&](float (&v)[2], int nr, float subv, float (&tot)[2], bool publish, bool subs) -> bool {
+        const int ns = subs ? spc : 0;
         for (int k = 0; k < nr; ++k) {
             const float s = warp_sum(v[k]);
             if (lane == 0) wsum32[wid][k] = s;
+        }
+        if (ns) {
+            const float s = warp_sum(subv);
+            if (lane == 0) wsum32[wid][nr] = s;
         }
         __syncthreads();
         const int par = mred & 1;
         const uint32_t phase = (uint32_t)(mred >> 1) & 1u;
         ++mred;
+        last_par = par;
         const bool live = abort_flag == 0;
         if (publish && live) {
             for (int i = threadIdx.x; i < nsend; i += blockDim.x) {
@@ -219,10 +241,19 @@ static __global__ void __launch_bounds__(kOnchipThreads, 1) k_pcg_onchip(CoarseP
         if (wid == 0) {
             float cs[2] = {0.0f, 0.0f};
             for (int k = 0; k < nr; ++k) cs[k] = __shfl_sync(0xffffffffu, warp_sum(lane < nw ? wsum32[lane][k] : 0.0f), 0);
-            if (live && lane < ncl)
-                for (int k = 0; k < nr; ++k)
-                    oc_st_async(red32_remote + (uint32_t)(4 * ((par * 16 + rank) * 4 + k)), cs[k], mbar_remote[lane][par]);
-            if (lane == 0) oc_mbar_arrive_expect(&mbar[par], (uint32_t)(4 * (nr * ncl + (publish ? halo_self : 0))));
+            // subdomain g of this CTA = warps g * wpg .. g * wpg + wpg - 1
+            float gs = (ns && lane < nw) ? wsum32[lane][nr] : 0.0f;
+            for (int o = 1; o < (ns ? pl.wpg : 1); o <<= 1) gs += __shfl_down_sync(0xffffffffu, gs, o);
+            const bool sender = live && lane < ncl;
+            const uint32_t dst = red32_remote + (uint32_t)(4 * ((par * 16 + rank) * kOnchipSlot));
+            if (sender)
+                for (int k = 0; k < nr; ++k) oc_st_async(dst + 4 * k, cs[k], mbar_remote[lane][par]);
+            for (int g = 0; g < ns; ++g) {
+                const float x = __shfl_sync(0xffffffffu, gs, g * pl.wpg);
+                if (sender) oc_st_async(dst + 4 * (nr + g), x, mbar_remote[lane][par]);
+            }
+            if (lane == 0)
+                oc_mbar_arrive_expect(&mbar[par], (uint32_t)(4 * ((nr + ns) * ncl + (publish ? halo_self : 0))));
             bool ok = live;
             if (ok) {
                 const long long t0 = clock64();
@@ -235,7 +266,7 @@ static __global__ void __launch_bounds__(kOnchipThreads, 1) k_pcg_onchip(CoarseP
             }
             ok = __all_sync(0xffffffffu, ok);
             for (int k = 0; k < nr; ++k) {
-                const float t = __shfl_sync(0xffffffffu, warp_sum(lane < ncl ? red32[(par * 16 + lane) * 4 + k] : 0.0f), 0);
+                const float t = __shfl_sync(0xffffffffu, warp_sum(lane < ncl ? red32[(par * 16 + lane) * kOnchipSlot + k] : 0.0f), 0);
                 if (lane == 0) tot32[k] = t;
             }
             if (!ok && lane < ncl) asm volatile("st.shared::cluster.u32 [%0], 1;" ::"r"(oc_map(&abort_flag, lane)) : "memory");
@@ -244,10 +275,50 @@ static __global__ void __launch_bounds__(kOnchipThreads, 1) k_pcg_onchip(CoarseP
         for (int k = 0; k < nr; ++k) tot[k] = tot32[k];
         return abort_flag == 0;
     };
+    // Coarse correction after a reduction that carried the subdomain sums s = Z^T r (slot set
+    // `par`, after `nr` scalars): every warp forms mu_j = (E^+ s)_j for j = wid, wid + nw, ...
+    // (lanes split the columns), then z += mu[subdomain] in the own rows and the halo.
+    // Returns s^T mu, the coarse part of <r, z>; identical in every CTA.
+    float z_[kOnchipRows];
+    auto coarse_fix = [&](int par, int nr) -> float {
+        const float* sl = red32 + par * 16 * kOnchipSlot + nr;
+        const int sh = __ffs(spc) - 1;
+        auto s_at = [&](int j) { return sl[(j >> sh) * kOnchipSlot + (j & (spc - 1))]; };
+        float sv[4];   // m <= 128
+#pragma unroll
+        for (int i = 0; i < 4; ++i) sv[i] = lane + 32 * i < m ? s_at(lane + 32 * i) : 0.0f;
+        float qp = 0.0f;
+        for (int j = wid; j < m; j += nw) {
+            const float* er = einv + j * m;
+            float acc = 0.0f;
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+                if (lane + 32 * i < m) acc = fmaf(er[lane + 32 * i], sv[i], acc);
+            acc = warp_sum(acc);
+            if (lane == 0) {
+                mu[j] = acc;
+                qp = fmaf(s_at(j), acc, qp);
+            }
+        }
+        if (lane == 0) qf[wid] = qp;
+        __syncthreads();
+        float q = 0.0f;
+        for (int w = 0; w < nw; ++w) q += qf[w];
+        const float mw = mu[my_sub];
+#pragma unroll
+        for (int t = 0; t < kOnchipRows; ++t) {
+            if (t >= nrow) break;
+            if (in_space(t)) z_[t] += mw;
+            zl[lrow_of(t)] = z_[t];
+        }
+        for (int h = threadIdx.x; h < halo_self; h += blockDim.x) zl[rows_max + h] += mu[hsub[h]];
+        __syncthreads();
+        return q;
+    };
     const double mean = a.project ? a.st->mean : 0.0;
     const double tol2 = a.tol2;
     double* xv = a.x;
-    float e_[kOnchipRows], r_[kOnchipRows], z_[kOnchipRows], p_[kOnchipRows], q_[kOnchipRows], d_[kOnchipRows];
+    float e_[kOnchipRows], r_[kOnchipRows], p_[kOnchipRows], q_[kOnchipRows], d_[kOnchipRows];
 #pragma unroll
     for (int t = 0; t < kOnchipRows; ++t) {
         e_[t] = r_[t] = z_[t] = p_[t] = q_[t] = d_[t] = 0.0f;
@@ -259,14 +330,20 @@ static __global__ void __launch_bounds__(kOnchipThreads, 1) k_pcg_onchip(CoarseP
         }
     }
     oc_barrier();   // matrix and sends loaded, z zeroed, b projected and x zeroed where asked
-    // FP64 row of A times a global vector (`ro`: v is read-only during the launch)
+    // FP64 row of A times a global vector (`ro`: v is read-only during the launch), from the
+    // SELL-32 arrays: entry k of row i sits at ptr[i / 32] + 32 k + i % 32 (padding: value 0)
     auto row_a = [&](int t, const double* v, bool ro) {
-        double ax[1] = {0.0};
-        if (ro)
-            sell_accum<1>(A, a.val, slice_[t], lane, [&](int j, double (&o)[1]) { o[0] = __ldg(v + j); }, ax);
-        else
-            sell_accum<1>(A, a.val, slice_[t], lane, [&](int j, double (&o)[1]) { o[0] = ldcg(v + j); }, ax);
-        return ax[0];
+        const int i = row_of(t);
+        double acc = 0.0;
+        if (i >= 0) {
+            const int e0 = __ldg(A.ptr + (i >> 5)), w = (__ldg(A.ptr + (i >> 5) + 1) - e0) >> 5;
+            for (int k = 0; k < w; ++k) {
+                const int e = e0 + 32 * k + (i & 31);
+                const int j = __ldg(A.col + e);
+                acc = fma(__ldg(a.val + e), ro ? __ldg(v + j) : ldcg(v + j), acc);
+            }
+        }
+        return acc;
     };
     int iters = 0, status = 0, outer = 0, used_alt = 0;
     bool converged = false;
@@ -327,7 +404,7 @@ static __global__ void __launch_bounds__(kOnchipThreads, 1) k_pcg_onchip(CoarseP
     enum { kInner = 0, kConverged, kNonfinite, kNotconv };
     for (;;) {
         // ---- outer: r = b - A x in FP64 (global memory); the inner problem A e = r / ||r||
-        double acc[3] = {0.0, 0.0, 0.0};
+        double acc[2] = {0.0, 0.0};
 #pragma unroll
         for (int t = 0; t < kOnchipRows; ++t) {
             if (t >= nrow) break;
@@ -339,7 +416,6 @@ static __global__ void __launch_bounds__(kOnchipThreads, 1) k_pcg_onchip(CoarseP
                 r_[t] = (float)ri;
                 acc[0] += ri * ri;
                 acc[1] += bi * bi;
-                acc[2] += ri * ri * (double)d_[t];
             }
         }
         cred64(acc, tot);
@@ -355,7 +431,6 @@ static __global__ void __launch_bounds__(kOnchipThreads, 1) k_pcg_onchip(CoarseP
                 if (act == kInner) {
                     sc.norm = sqrt(tot[0]);
                     sc.inv = 1.0 / sc.norm;
-                    sc.rz0 = (float)(tot[2] / tot[0]);
                     sc.stop2 = (float)fmax(a.inner_tol * a.inner_tol, 0.25 * tol2 * bb / tot[0]);
                 }
             }
@@ -377,6 +452,7 @@ static __global__ void __launch_bounds__(kOnchipThreads, 1) k_pcg_onchip(CoarseP
             }
         }
         const float inv = (float)sc.inv;
+        float a1[2] = {0.0f, 0.0f}, s1 = 0.0f;
 #pragma unroll
         for (int t = 0; t < kOnchipRows; ++t) {
             if (row_of(t) >= 0) {
@@ -386,14 +462,21 @@ static __global__ void __launch_bounds__(kOnchipThreads, 1) k_pcg_onchip(CoarseP
                 p_[t] = 0.0f;
                 q_[t] = 0.0f;
                 zl[lrow_of(t)] = z_[t];
+                a1[0] = fmaf(r_[t], z_[t], a1[0]);
+                if (in_space(t)) s1 += r_[t];
             }
         }
-        __syncthreads();
-        push();
-        oc_barrier();   // the first z in every halo
+        // <r, D^{-1} r> and Z^T r; the first z goes to every halo with it
+        float t1[2];
+        if (!cred32(a1, 1, s1, t1, true, m > 0)) {
+            status = CGP_ETIMEOUT;
+            break;
+        }
+        float rz = t1[0];
+        if (m) rz += coarse_fix(last_par, 1);
         // ---- inner classical PCG in FP32 on the scaled residual; every warp carries the same
         // scalars (rz, beta, rr_best), computed from the same totals
-        float rz = sc.rz0, beta = 0.0f, rr_best = INFINITY;
+        float beta = 0.0f, rr_best = INFINITY;
         const float stop2 = sc.stop2;
         int best_k = 0;
         bool drift = false, aborted = false;
@@ -422,14 +505,15 @@ static __global__ void __launch_bounds__(kOnchipThreads, 1) k_pcg_onchip(CoarseP
                 }
             }
             float pq[2];
-            if (!cred32(pq_acc, 1, pq, false)) {
+            if (!cred32(pq_acc, 1, 0.0f, pq, false, false)) {
                 aborted = true;
                 break;
             }
             if (!(pq[0] != 0.0f) || !isfinite(pq[0])) break;   // restart from the true residual
             const float al = rz / pq[0];
-            // phase B (own rows): e += alpha p, r -= alpha q, z = D^{-1} r
-            float acc2[2] = {0.0f, 0.0f};
+            // phase B (own rows): e += alpha p, r -= alpha q, z = D^{-1} r (+ the coarse
+            // correction once Z^T r is known)
+            float acc2[2] = {0.0f, 0.0f}, s2 = 0.0f;
 #pragma unroll
             for (int t = 0; t < kOnchipRows; ++t) {
                 if (row_of(t) >= 0) {
@@ -439,10 +523,11 @@ static __global__ void __launch_bounds__(kOnchipThreads, 1) k_pcg_onchip(CoarseP
                     zl[lrow_of(t)] = z_[t];
                     acc2[0] = fmaf(r_[t], z_[t], acc2[0]);
                     acc2[1] = fmaf(r_[t], r_[t], acc2[1]);
+                    if (in_space(t)) s2 += r_[t];
                 }
             }
             float t2[2];
-            if (!cred32(acc2, 2, t2, true)) {
+            if (!cred32(acc2, 2, s2, t2, true, m > 0)) {
                 aborted = true;
                 break;
             }
@@ -451,9 +536,12 @@ static __global__ void __launch_bounds__(kOnchipThreads, 1) k_pcg_onchip(CoarseP
                 drift = true;
                 break;
             }
-            if (t2[1] <= stop2 || t2[0] == 0.0f || t2[1] == 0.0f) break;
-            beta = t2[0] / rz;
-            rz = t2[0];
+            if (t2[1] <= stop2 || t2[1] == 0.0f) break;
+            float rzn = t2[0];
+            if (m) rzn += coarse_fix(last_par, 2);
+            if (!(rzn > 0.0f)) break;   // restart from the true residual
+            beta = rzn / rz;
+            rz = rzn;
             if (t2[1] < 0.5f * rr_best) {
                 rr_best = t2[1];
                 best_k = k;

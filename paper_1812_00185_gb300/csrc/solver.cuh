@@ -71,8 +71,10 @@ struct Solver {
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;      // the coarse solve's inner iterations run in FP64
     size_t onchip_bytes = 0;      // mixed: shared memory per CTA of the on-chip cluster solve (0 = not used)
     // mixed: workspace arrays of the on-chip plan (sized for the coarse level) and its device view
-    int32_t *oc_slist = nullptr, *oc_soff = nullptr, *oc_ebase = nullptr, *oc_li = nullptr, *oc_src = nullptr;
-    int32_t *oc_send_lr = nullptr, *oc_send_dst = nullptr, *oc_send_off = nullptr, *oc_halo_n = nullptr;
+    int32_t *oc_grow = nullptr, *oc_soff = nullptr, *oc_ebase = nullptr, *oc_width = nullptr, *oc_li = nullptr;
+    int32_t *oc_src = nullptr, *oc_send_lr = nullptr, *oc_send_dst = nullptr, *oc_send_off = nullptr, *oc_halo_n = nullptr;
+    uint8_t* oc_hsub = nullptr;
+    float* oc_einv = nullptr;
     OnchipPlan onchip{};
     unsigned int* bar_count = nullptr;   // grid barrier counter, followed by the error word
     int* bar_err = nullptr;
@@ -131,7 +133,7 @@ void fill_coarse_args(Solver& s, void* dst);
 int batch_clusters(int csize, int threads, int* nclusters);
 int launch_batch_coarse(const void* d_args, int ninst, unsigned int* queue, int csize, int threads, int nclusters,
                         cudaStream_t st);
-int choose_coarse_solver(Solver& s);
+int choose_coarse_solver(Solver& s, cudaStream_t st);
 int init_state(Solver* s, cudaStream_t st);
 
 }  // namespace cgp

@@ -640,7 +640,7 @@ static cudaLaunchConfig_t cluster_config(int csize, cudaStream_t st, cudaLaunchA
     return cfg;
 }
 
-int choose_coarse_solver(Solver& s) {
+int choose_coarse_solver(Solver& s, cudaStream_t st) {
     const cgp_params& p = s.prm;
     int mode = p.coarse_mode;
     if (mode == CGP_COARSE_ONCHIP && p.precision != CGP_MIXED) {
@@ -649,6 +649,10 @@ int choose_coarse_solver(Solver& s) {
     }
     // the on-chip cluster solve when asked for, or by default for the mixed form if it fits
     const bool want_onchip = p.precision == CGP_MIXED && (mode == CGP_COARSE_ONCHIP || mode == CGP_COARSE_AUTO);
+    if (p.precond == CGP_PRECOND_COARSE && !want_onchip) {
+        set_error("CGP_PRECOND_COARSE needs the on-chip coarse solver (CGP_MIXED, coarse_mode AUTO or ONCHIP)");
+        return CGP_EINVAL;
+    }
     if (mode == CGP_COARSE_AUTO || mode == CGP_COARSE_ONCHIP) mode = CGP_COARSE_PERSISTENT;
     const bool allow_rr = mode == CGP_COARSE_PERSISTENT;
     if (mode == CGP_COARSE_PERSISTENT_MEM) mode = CGP_COARSE_PERSISTENT;
@@ -680,50 +684,71 @@ int choose_coarse_solver(Solver& s) {
         const int cap = sms * (per_sm < 2 ? per_sm : 2);
         s.coarse_grid = need < cap ? need : cap;
         if (s.coarse_grid < 1) s.coarse_grid = 1;
-        // mixed precision: the whole FP32 inner solve on one cluster, if it fits on chip
+        // mixed precision: the whole FP32 inner solve on one cluster, if it fits on chip; the
+        // largest subdomain coarse space that fits beside it (AUTO / COARSE), else Jacobi
         s.onchip_bytes = 0;
         if (want_onchip && s.oc_li) {
-            std::vector<int32_t> ptr(C.nslices + 1), col(C.nnz_sell);
-            std::vector<double> xy(2 * (size_t)C.nv);
+            std::vector<int32_t> rowptr(C.nv + 1), ptr(C.nslices + 1), col(C.nnz_sell);
+            std::vector<double> xy(2 * (size_t)C.nv), val(C.nnz_sell);
+            std::vector<uint8_t> tag(C.nv), in_space(C.nv);
+            CGP_CUDA(cudaStreamSynchronize(st));   // the assembled K_c
+            CGP_CUDA(cudaMemcpy(rowptr.data(), C.rowptr, sizeof(int32_t) * (C.nv + 1), cudaMemcpyDeviceToHost));
             CGP_CUDA(cudaMemcpy(ptr.data(), C.sell_ptr, sizeof(int32_t) * (C.nslices + 1), cudaMemcpyDeviceToHost));
             CGP_CUDA(cudaMemcpy(col.data(), C.sell_col, sizeof(int32_t) * C.nnz_sell, cudaMemcpyDeviceToHost));
             CGP_CUDA(cudaMemcpy(xy.data(), C.xy, sizeof(double) * 2 * C.nv, cudaMemcpyDeviceToHost));
+            CGP_CUDA(cudaMemcpy(val.data(), s.Kc0, sizeof(double) * C.nnz_sell, cudaMemcpyDeviceToHost));
+            CGP_CUDA(cudaMemcpy(tag.data(), C.tag, C.nv, cudaMemcpyDeviceToHost));
+            for (int i = 0; i < C.nv; ++i) in_space[i] = (tag[i] & CGP_PHI_ZERO) ? 0 : 1;
             int optin = 0;
             CGP_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
             const size_t limit = (size_t)optin - 2048;   // static shared memory of the kernel
             CGP_CUDA(cudaFuncSetAttribute(k_pcg_onchip, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
             CGP_CUDA(cudaFuncSetAttribute(k_pcg_onchip, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)limit));
+            const bool coarse_space = p.precond != CGP_PRECOND_JACOBI;
             for (int cs : {16, 8}) {
-                OnchipHostPlan P;
-                if (!onchip_plan(C.nv, ptr, col, xy, cs, limit, P)) continue;
-                cudaLaunchAttribute attr[1];
-                cudaLaunchConfig_t cfg = cluster_config(cs, nullptr, attr);
-                cfg.blockDim = dim3(kOnchipThreads, 1, 1);
-                cfg.dynamicSmemBytes = P.bytes;
-                int n = 0;
-                if (cudaOccupancyMaxActiveClusters(&n, k_pcg_onchip, &cfg) != cudaSuccess || n < 1) {
-                    cudaGetLastError();
-                    continue;
+                for (int spc : {8, 4, 2, 1, 0}) {
+                    if (spc && !coarse_space) continue;
+                    OnchipHostPlan P;
+                    if (!onchip_plan(C.nv, rowptr, ptr, col, xy, in_space, cs, spc, limit, P)) continue;
+                    if (!onchip_coarse_space(rowptr, ptr, col, val, P)) continue;
+                    cudaLaunchAttribute attr[1];
+                    cudaLaunchConfig_t cfg = cluster_config(cs, nullptr, attr);
+                    cfg.blockDim = dim3(kOnchipThreads, 1, 1);
+                    cfg.dynamicSmemBytes = P.bytes;
+                    int n = 0;
+                    if (cudaOccupancyMaxActiveClusters(&n, k_pcg_onchip, &cfg) != cudaSuccess || n < 1) {
+                        cudaGetLastError();
+                        continue;
+                    }
+                    auto up = [](auto* dst, const auto& v) {
+                        return v.empty() ? cudaSuccess
+                                         : cudaMemcpy(dst, v.data(), sizeof(v[0]) * v.size(), cudaMemcpyHostToDevice);
+                    };
+                    CGP_CUDA(up(s.oc_grow, P.grow));
+                    CGP_CUDA(up(s.oc_soff, P.soff));
+                    CGP_CUDA(up(s.oc_ebase, P.ebase));
+                    CGP_CUDA(up(s.oc_width, P.width));
+                    CGP_CUDA(up(s.oc_li, P.li));
+                    CGP_CUDA(up(s.oc_src, P.src));
+                    CGP_CUDA(up(s.oc_send_lr, P.send_lr));
+                    CGP_CUDA(up(s.oc_send_dst, P.send_dst));
+                    CGP_CUDA(up(s.oc_send_off, P.send_off));
+                    CGP_CUDA(up(s.oc_halo_n, P.halo_n));
+                    CGP_CUDA(up(s.oc_hsub, P.hsub));
+                    CGP_CUDA(up(s.oc_einv, P.einv));
+                    s.onchip = OnchipPlan{s.oc_grow, s.oc_soff, s.oc_ebase, s.oc_width, s.oc_li, s.oc_src,
+                                          s.oc_send_lr, s.oc_send_dst, s.oc_send_off, s.oc_halo_n, s.oc_hsub,
+                                          s.oc_einv, P.rows_max, P.halo_max, P.send_max, (int)P.ent_max,
+                                          P.nsub, P.wpg};
+                    s.onchip_bytes = P.bytes;
+                    s.cluster_size = cs;
+                    break;
                 }
-                auto up = [](int32_t* dst, const std::vector<int32_t>& v) {
-                    return v.empty() ? cudaSuccess
-                                     : cudaMemcpy(dst, v.data(), sizeof(int32_t) * v.size(), cudaMemcpyHostToDevice);
-                };
-                CGP_CUDA(up(s.oc_slist, P.slist));
-                CGP_CUDA(up(s.oc_soff, P.soff));
-                CGP_CUDA(up(s.oc_ebase, P.ebase));
-                CGP_CUDA(up(s.oc_li, P.li));
-                CGP_CUDA(up(s.oc_src, P.src));
-                CGP_CUDA(up(s.oc_send_lr, P.send_lr));
-                CGP_CUDA(up(s.oc_send_dst, P.send_dst));
-                CGP_CUDA(up(s.oc_send_off, P.send_off));
-                CGP_CUDA(up(s.oc_halo_n, P.halo_n));
-                s.onchip = OnchipPlan{s.oc_slist, s.oc_soff, s.oc_ebase, s.oc_li, s.oc_src, s.oc_send_lr,
-                                      s.oc_send_dst, s.oc_send_off, s.oc_halo_n, P.rows_max, P.halo_max,
-                                      P.send_max, (int)P.ent_max};
-                s.onchip_bytes = P.bytes;
-                s.cluster_size = cs;
-                break;
+                if (s.onchip_bytes) break;
+            }
+            if (p.precond == CGP_PRECOND_COARSE && !(s.onchip_bytes && s.onchip.nsub)) {
+                set_error("the coarse system does not fit on one thread-block cluster with a coarse space");
+                return CGP_EINVAL;
             }
             if (p.coarse_mode == CGP_COARSE_ONCHIP && !s.onchip_bytes) {
                 set_error("the coarse system does not fit on one thread-block cluster");
@@ -1307,6 +1332,15 @@ extern "C" int cgp_set_vector(cgp_solver* h, int32_t which, const double* in, in
     cudaStream_t st = (cudaStream_t)stream;
     CGP_TRY(copy_in(dst, in, n * sizeof(double), where, st));
     if (where == CGP_HOST) CGP_CUDA(cudaStreamSynchronize(st));
+    return CGP_OK;
+}
+
+extern "C" int cgp_coarse_subdomains(const cgp_solver* h, int32_t* nsub) {
+    if (!h) {
+        set_error("null solver");
+        return CGP_EINVAL;
+    }
+    if (nsub) *nsub = h->s.onchip_bytes ? h->s.onchip.nsub : 0;
     return CGP_OK;
 }
 

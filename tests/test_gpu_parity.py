@@ -29,6 +29,10 @@ def _channel_small():
     return channel_cylinder_mesh(seed=4, h=0.05)
 
 
+def _channel_small_fine():
+    return channel_cylinder_mesh(seed=4, h=0.03)
+
+
 @pytest.mark.parametrize("mk,levels", [(lambda: square_mesh(8), 3), (lambda: crisscross_mesh(5), 2),
                                        (_channel_small, 2)])
 def test_mesh_hierarchy_bit_exact(cg, mk, levels):
@@ -79,8 +83,8 @@ def test_prolongation_bit_exact(cg):
     s.close(); m.close()
 
 
-@pytest.mark.parametrize("mode", ["kernels", "cluster", "persistent", "persistent_mem", "mixed", "mixed_cluster",
-                                  "mixed_persistent"])
+@pytest.mark.parametrize("mode", ["kernels", "cluster", "persistent", "persistent_mem", "mixed", "mixed_jacobi",
+                                  "mixed_cluster", "mixed_persistent"])
 @pytest.mark.parametrize("kind", ["neumann", "dirichlet"])
 def test_coarse_poisson_solve(cg, kind, mode):
     if kind == "neumann":
@@ -90,6 +94,7 @@ def test_coarse_poisson_solve(cg, kind, mode):
     m = cg.Mesh(base.xy, base.tri, base.tag, 2)
     extra = {"kernels": dict(coarse_mode=cg.CGP_COARSE_KERNELS), "cluster": dict(coarse_mode=cg.CGP_COARSE_CLUSTER),
              "persistent": dict(coarse_mode=cg.CGP_COARSE_PERSISTENT), "mixed": dict(precision=cg.CGP_MIXED),
+             "mixed_jacobi": dict(precision=cg.CGP_MIXED, precond=cg.CGP_PRECOND_JACOBI),
              "persistent_mem": dict(coarse_mode=cg.CGP_COARSE_PERSISTENT_MEM),
              "mixed_cluster": dict(precision=cg.CGP_MIXED, coarse_mode=cg.CGP_COARSE_CLUSTER),
              "mixed_persistent": dict(precision=cg.CGP_MIXED, coarse_mode=cg.CGP_COARSE_PERSISTENT)}[mode]
@@ -97,6 +102,7 @@ def test_coarse_poisson_solve(cg, kind, mode):
                                     **TIGHT, **extra))
     kind = {"kernels": cg.CGP_COARSE_KERNELS, "cluster": cg.CGP_COARSE_CLUSTER, "persistent": cg.CGP_COARSE_PERSISTENT,
             "persistent_mem": cg.CGP_COARSE_PERSISTENT_MEM, "mixed": cg.CGP_COARSE_ONCHIP,
+            "mixed_jacobi": cg.CGP_COARSE_ONCHIP,
             "mixed_cluster": cg.CGP_COARSE_CLUSTER, "mixed_persistent": cg.CGP_COARSE_PERSISTENT_MEM}[mode]
     assert s.coarse_info()[0] == kind
     o = CGPOracle(base, 2, 1, 100.0, 0.01, 0, bc, bc_param=bp)
@@ -236,6 +242,31 @@ def test_mixed_onchip_cluster_solve_on_channel(cg):
     s.close(); m.close()
 
 
+def test_onchip_coarse_correction_cuts_iterations(cg):
+    """The subdomain coarse correction of the on-chip solve (a preconditioner variant, not in
+    the paper): the same solution as the oracle's direct solve of Eq. 23, in far fewer inner
+    iterations than Jacobi alone, on a 10.5K-row coarse level with phi = 0 rows and a hole."""
+    base = _channel_small_fine()
+    bp = (0.3, 0.41, 0, 0)
+    m = cg.Mesh(base.xy, base.tri, base.tag, 3)
+    o = CGPOracle(base, 3, 1, 100.0, 0.01, 0, flows.BC_CHANNEL, bc_param=bp)
+    r = np.random.default_rng(2).standard_normal(o.coarse.n_vert)
+    r[o.phi0_mask] = 0.0
+    ref = o.poisson(r)
+    its = {}
+    for pc in (cg.CGP_PRECOND_JACOBI, cg.CGP_PRECOND_COARSE):
+        s = cg.Solver(m, cg.make_params(100.0, 0.01, k=1, bc_kind=flows.BC_CHANNEL, bc_param=bp,
+                                        guess=cg.CGP_GUESS_ZERO, precision=cg.CGP_MIXED, precond=pc, **TIGHT))
+        assert s.coarse_info()[0] == cg.CGP_COARSE_ONCHIP
+        assert (s.coarse_subdomains() == 0) == (pc == cg.CGP_PRECOND_JACOBI)
+        phi, it, rc = cg.cgp_poisson_solve(s.handle, r)
+        assert rc == 0 and rel(phi, ref) < 1e-9, (pc, rc, rel(phi, ref))
+        its[pc] = it
+        s.close()
+    assert its[cg.CGP_PRECOND_COARSE] < 0.5 * its[cg.CGP_PRECOND_JACOBI], its
+    m.close()
+
+
 def test_coarse_solver_choice(cg):
     base = square_mesh(16)
     m = cg.Mesh(base.xy, base.tri, base.tag, 2)
@@ -255,6 +286,14 @@ def test_coarse_solver_choice(cg):
     assert k == cg.CGP_COARSE_PERSISTENT_MEM and n > 0 and c == 0
     k, n, c = info(precision=cg.CGP_MIXED)              # mixed default: on-chip cluster solve
     assert k == cg.CGP_COARSE_ONCHIP and n == c and c in (8, 16)
+    s = cg.Solver(m, cg.make_params(100.0, 0.01, k=1, precision=cg.CGP_MIXED))
+    assert s.coarse_subdomains() >= 16                  # ... with the subdomain coarse correction
+    s.close()
+    s = cg.Solver(m, cg.make_params(100.0, 0.01, k=1, precision=cg.CGP_MIXED, precond=cg.CGP_PRECOND_JACOBI))
+    assert s.coarse_subdomains() == 0
+    s.close()
+    with pytest.raises(RuntimeError):
+        info(precond=cg.CGP_PRECOND_COARSE)             # the coarse correction lives in the on-chip solve
     k, n, c = info(precision=cg.CGP_MIXED, coarse_mode=cg.CGP_COARSE_PERSISTENT)   # FP32 inner in memory
     assert k == cg.CGP_COARSE_PERSISTENT_MEM and n > 0 and c == 0
     with pytest.raises(RuntimeError):
