@@ -82,6 +82,12 @@ __device__ __forceinline__ bool oc_mbar_try(uint64_t* mb, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
+__device__ __forceinline__ void oc_st_async4(uint32_t addr, float a, float b, float c, float d, uint32_t mbar) {
+    asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v4.b32 [%0], {%1, %2, %3, %4}, [%5];" ::"r"(addr),
+                 "r"(__float_as_uint(a)), "r"(__float_as_uint(b)), "r"(__float_as_uint(c)), "r"(__float_as_uint(d)),
+                 "r"(mbar)
+                 : "memory");
+}
 __device__ __forceinline__ void oc_st_async(uint32_t addr, float v, uint32_t mbar) {
     asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.b32 [%0], %1, [%2];" ::"r"(addr),
                  "r"(__float_as_uint(v)), "r"(mbar)
@@ -115,7 +121,8 @@ static __global__ void __launch_bounds__(kOnchipThreads, 1) k_pcg_onchip(CoarseP
     double* red64 = reinterpret_cast<double*>(smem + onchip_z_bytes(rows_max, pl.halo_max));
     float* red32 = reinterpret_cast<float*>(red64 + 128);
     float* einv = red32 + 2 * 16 * kOnchipSlot;
-    float* mu = einv + m * m;                     // mu[m] = 0: rows outside the coarse space
+    const int eld = onchip_einv_ld(m);            // row stride of E^+
+    float* mu = einv + m * eld;                   // mu[m] = 0: rows outside the coarse space
     float* qf = mu + ((m + 4) & ~3);
     uint8_t* hsub = reinterpret_cast<uint8_t*>(qf + 16);
     uint2* send = reinterpret_cast<uint2*>(hsub + ((pl.halo_max + 15) & ~15));
@@ -124,7 +131,7 @@ static __global__ void __launch_bounds__(kOnchipThreads, 1) k_pcg_onchip(CoarseP
     const int eb0 = npos > 0 ? __ldg(pl.ebase + q0) : 0;
     const int halo_self = __ldg(pl.halo_n + rank);
     for (int i = threadIdx.x; i < zn; i += blockDim.x) zl[i] = 0.0f;
-    for (int i = threadIdx.x; i < m * m; i += blockDim.x) einv[i] = __ldg(pl.einv + i);
+    for (int i = threadIdx.x; i < m * m; i += blockDim.x) einv[(i / m) * eld + i % m] = __ldg(pl.einv + i);
     for (int i = threadIdx.x; i < ((m + 4) & ~3); i += blockDim.x) mu[i] = 0.0f;
     for (int h = threadIdx.x; h < halo_self; h += blockDim.x) hsub[h] = __ldg(pl.hsub + (size_t)rank * pl.halo_max + h);
     // ---- rows of this thread: slice t of its warp is list position wid + nw * t of its CTA;
@@ -248,12 +255,22 @@ static __global__ void __launch_bounds__(kOnchipThreads, 1) k_pcg_onchip(CoarseP
             const uint32_t dst = red32_remote + (uint32_t)(4 * ((par * 16 + rank) * kOnchipSlot));
             if (sender)
                 for (int k = 0; k < nr; ++k) oc_st_async(dst + 4 * k, cs[k], mbar_remote[lane][par]);
-            for (int g = 0; g < ns; ++g) {
-                const float x = __shfl_sync(0xffffffffu, gs, g * pl.wpg);
-                if (sender) oc_st_async(dst + 4 * (nr + g), x, mbar_remote[lane][par]);
+            // the subdomain sums, four at a time (16-byte stores; unused ones are zero)
+            const int nv4 = (ns + 3) >> 2;
+            for (int g = 0; g < nv4; ++g) {
+                float x[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int gg = 4 * g + u;
+                    const float y = __shfl_sync(0xffffffffu, gs, (gg < ns ? gg : 0) * (ns ? pl.wpg : 1));
+                    x[u] = gg < ns ? y : 0.0f;
+                }
+                if (sender)
+                    oc_st_async4(dst + 4 * (kOnchipSubOff + 4 * g), x[0], x[1], x[2], x[3], mbar_remote[lane][par]);
             }
             if (lane == 0)
-                oc_mbar_arrive_expect(&mbar[par], (uint32_t)(4 * ((nr + ns) * ncl + (publish ? halo_self : 0))));
+                oc_mbar_arrive_expect(&mbar[par],
+                                      (uint32_t)(ncl * (4 * nr + 16 * nv4) + (publish ? 4 * halo_self : 0)));
             bool ok = live;
             if (ok) {
                 const long long t0 = clock64();
@@ -276,31 +293,36 @@ static __global__ void __launch_bounds__(kOnchipThreads, 1) k_pcg_onchip(CoarseP
         return abort_flag == 0;
     };
     // Coarse correction after a reduction that carried the subdomain sums s = Z^T r (slot set
-    // `par`, after `nr` scalars): every warp forms mu_j = (E^+ s)_j for j = wid, wid + nw, ...
-    // (lanes split the columns), then z += mu[subdomain] in the own rows and the halo.
+    // `par`): mu = E^+ s with tpr threads per row of E^+ (each a strided share of the
+    // columns, then an xor-shuffle sum), then z += mu[subdomain] in the own rows and the halo.
     // Returns s^T mu, the coarse part of <r, z>; identical in every CTA.
     float z_[kOnchipRows];
-    auto coarse_fix = [&](int par, int nr) -> float {
-        const float* sl = red32 + par * 16 * kOnchipSlot + nr;
+    const int tpr = onchip_mu_tpr(m);
+    auto coarse_fix = [&](int par) -> float {
+        const float* sl = red32 + par * 16 * kOnchipSlot + kOnchipSubOff;
         const int sh = __ffs(spc) - 1;
         auto s_at = [&](int j) { return sl[(j >> sh) * kOnchipSlot + (j & (spc - 1))]; };
-        float sv[4];   // m <= 128
-#pragma unroll
-        for (int i = 0; i < 4; ++i) sv[i] = lane + 32 * i < m ? s_at(lane + 32 * i) : 0.0f;
-        float qp = 0.0f;
-        for (int j = wid; j < m; j += nw) {
-            const float* er = einv + j * m;
-            float acc = 0.0f;
-#pragma unroll
-            for (int i = 0; i < 4; ++i)
-                if (lane + 32 * i < m) acc = fmaf(er[lane + 32 * i], sv[i], acc);
-            acc = warp_sum(acc);
-            if (lane == 0) {
-                mu[j] = acc;
-                qp = fmaf(s_at(j), acc, qp);
+        const int j = threadIdx.x / tpr, c = threadIdx.x & (tpr - 1);
+        float acc = 0.0f;
+        if (j < m) {
+            const float* er = einv + j * eld;
+            float a0 = 0.0f, a1 = 0.0f;
+            int col = c;
+            for (; col + tpr < m; col += 2 * tpr) {
+                a0 = fmaf(er[col], s_at(col), a0);
+                a1 = fmaf(er[col + tpr], s_at(col + tpr), a1);
             }
+            if (col < m) a0 = fmaf(er[col], s_at(col), a0);
+            acc = a0 + a1;
         }
-        if (lane == 0) qf[wid] = qp;
+        for (int o = 1; o < tpr; o <<= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        float part = 0.0f;
+        if (j < m && c == 0) {
+            mu[j] = acc;
+            part = s_at(j) * acc;
+        }
+        part = warp_sum(part);
+        if (lane == 0) qf[wid] = part;
         __syncthreads();
         float q = 0.0f;
         for (int w = 0; w < nw; ++w) q += qf[w];
@@ -473,7 +495,7 @@ static __global__ void __launch_bounds__(kOnchipThreads, 1) k_pcg_onchip(CoarseP
             break;
         }
         float rz = t1[0];
-        if (m) rz += coarse_fix(last_par, 1);
+        if (m) rz += coarse_fix(last_par);
         // ---- inner classical PCG in FP32 on the scaled residual; every warp carries the same
         // scalars (rz, beta, rr_best), computed from the same totals
         float beta = 0.0f, rr_best = INFINITY;
@@ -538,7 +560,7 @@ static __global__ void __launch_bounds__(kOnchipThreads, 1) k_pcg_onchip(CoarseP
             }
             if (t2[1] <= stop2 || t2[1] == 0.0f) break;
             float rzn = t2[0];
-            if (m) rzn += coarse_fix(last_par, 2);
+            if (m) rzn += coarse_fix(last_par);
             if (!(rzn > 0.0f)) break;   // restart from the true residual
             beta = rzn / rz;
             rz = rzn;
