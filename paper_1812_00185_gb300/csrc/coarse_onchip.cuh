@@ -95,6 +95,48 @@ __device__ __forceinline__ void oc_st_async(uint32_t addr, float v, uint32_t mba
 }
 constexpr long long kOnchipWaitCycles = 4000000000LL;   // ~2 s: a wait this long means a lost signal
 
+// R rows of mu = E^+ s in one warp: lane l holds s of columns l*cpl .. l*cpl+cpl-1 (cpl =
+// 4, 2 or 1; `has` = those columns exist) and forms the partial sums of all R rows over them
+// (one 16-, 8- or 4-byte load per row: the warp reads each row once, conflict-free); a
+// transpose reduction then halves the rows held per lane with each xor shuffle (offsets 16,
+// 8, ...) and sums the rest, leaving row `row`'s total in every lane.
+template <int R, int cpl>
+__device__ __forceinline__ float oc_mu_rows(const float* er, int m, bool has, const float (&sv)[4], int lane, int& row) {
+    float v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const float* e = er + r * m + lane * cpl;
+        float a = 0.0f;
+        if (has) {
+            if constexpr (cpl == 4) {
+                const float4 x = *reinterpret_cast<const float4*>(e);
+                a = fmaf(x.x, sv[0], fmaf(x.y, sv[1], fmaf(x.z, sv[2], x.w * sv[3])));
+            } else if constexpr (cpl == 2) {
+                const float2 x = *reinterpret_cast<const float2*>(e);
+                a = fmaf(x.x, sv[0], x.y * sv[1]);
+            } else {
+                a = e[0] * sv[0];
+            }
+        }
+        v[r] = a;
+    }
+    row = 0;
+#pragma unroll
+    for (int h = R, o = 16; h > 1; h >>= 1, o >>= 1) {
+        const bool up = (lane & o) != 0;
+        if (up) row += h / 2;
+#pragma unroll
+        for (int i = 0; i < h / 2; ++i) {
+            const float keep = up ? v[i + h / 2] : v[i];
+            const float send = up ? v[i] : v[i + h / 2];
+            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+        }
+    }
+#pragma unroll
+    for (int o = 16 / R; o > 0; o >>= 1) v[0] += __shfl_xor_sync(0xffffffffu, v[0], o);
+    return v[0];
+}
+
 // what warp 0 tells its CTA after an FP64 reduction
 struct OnchipScalars {
     int act;
@@ -102,6 +144,8 @@ struct OnchipScalars {
     double inv, norm, mu;      // 1 / ||r||, ||r|| of the outer residual; mean of the Neumann fix
 };
 
+// MR: rows of mu = E^+ s per warp (nsub / 16, at least 1), 0 without the coarse correction
+template <int MR>
 static __global__ void __launch_bounds__(kOnchipThreads, 1) k_pcg_onchip(CoarsePcgArgs a, OnchipPlan pl) {
     namespace cg = cooperative_groups;
     cg::cluster_group cluster = cg::this_cluster();
@@ -121,8 +165,7 @@ static __global__ void __launch_bounds__(kOnchipThreads, 1) k_pcg_onchip(CoarseP
     double* red64 = reinterpret_cast<double*>(smem + onchip_z_bytes(rows_max, pl.halo_max));
     float* red32 = reinterpret_cast<float*>(red64 + 128);
     float* einv = red32 + 2 * 16 * kOnchipSlot;
-    const int eld = onchip_einv_ld(m);            // row stride of E^+
-    float* mu = einv + m * eld;                   // mu[m] = 0: rows outside the coarse space
+    float* mu = einv + m * m;                     // mu[m] = 0: rows outside the coarse space
     float* qf = mu + ((m + 4) & ~3);
     uint8_t* hsub = reinterpret_cast<uint8_t*>(qf + 16);
     uint2* send = reinterpret_cast<uint2*>(hsub + ((pl.halo_max + 15) & ~15));
@@ -131,7 +174,7 @@ static __global__ void __launch_bounds__(kOnchipThreads, 1) k_pcg_onchip(CoarseP
     const int eb0 = npos > 0 ? __ldg(pl.ebase + q0) : 0;
     const int halo_self = __ldg(pl.halo_n + rank);
     for (int i = threadIdx.x; i < zn; i += blockDim.x) zl[i] = 0.0f;
-    for (int i = threadIdx.x; i < m * m; i += blockDim.x) einv[(i / m) * eld + i % m] = __ldg(pl.einv + i);
+    for (int i = threadIdx.x; i < m * m; i += blockDim.x) einv[i] = __ldg(pl.einv + i);
     for (int i = threadIdx.x; i < ((m + 4) & ~3); i += blockDim.x) mu[i] = 0.0f;
     for (int h = threadIdx.x; h < halo_self; h += blockDim.x) hsub[h] = __ldg(pl.hsub + (size_t)rank * pl.halo_max + h);
     // ---- rows of this thread: slice t of its warp is list position wid + nw * t of its CTA;
@@ -293,33 +336,38 @@ static __global__ void __launch_bounds__(kOnchipThreads, 1) k_pcg_onchip(CoarseP
         return abort_flag == 0;
     };
     // Coarse correction after a reduction that carried the subdomain sums s = Z^T r (slot set
-    // `par`): mu = E^+ s with tpr threads per row of E^+ (each a strided share of the
-    // columns, then an xor-shuffle sum), then z += mu[subdomain] in the own rows and the halo.
-    // Returns s^T mu, the coarse part of <r, z>; identical in every CTA.
+    // `par`): warp w forms rows w R .. w R + R - 1 of mu = E^+ s (R = m / 16, at least 1),
+    // then z += mu[subdomain] in the own rows and the halo.  Returns s^T mu, the coarse part
+    // of <r, z>; identical in every CTA.
     float z_[kOnchipRows];
-    const int tpr = onchip_mu_tpr(m);
+    constexpr int mrows = MR > 0 ? MR : 1, cpl = MR == 8 ? 4 : (MR == 4 ? 2 : 1);
     auto coarse_fix = [&](int par) -> float {
         const float* sl = red32 + par * 16 * kOnchipSlot + kOnchipSubOff;
         const int sh = __ffs(spc) - 1;
-        auto s_at = [&](int j) { return sl[(j >> sh) * kOnchipSlot + (j & (spc - 1))]; };
-        const int j = threadIdx.x / tpr, c = threadIdx.x & (tpr - 1);
-        float acc = 0.0f;
-        if (j < m) {
-            const float* er = einv + j * eld;
-            float a0 = 0.0f, a1 = 0.0f;
-            int col = c;
-            for (; col + tpr < m; col += 2 * tpr) {
-                a0 = fmaf(er[col], s_at(col), a0);
-                a1 = fmaf(er[col + tpr], s_at(col + tpr), a1);
+        auto s_at = [&](int j) -> const float& { return sl[(j >> sh) * kOnchipSlot + (j & (spc - 1))]; };
+        const int c0 = lane * cpl;
+        const bool has = c0 < m;
+        float sv[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+        if (has) {   // cpl > 1 only with spc >= 4: the columns lie in one CTA's slot
+            if constexpr (cpl == 4) {
+                const float4 x = *reinterpret_cast<const float4*>(&s_at(c0));
+                sv[0] = x.x; sv[1] = x.y; sv[2] = x.z; sv[3] = x.w;
+            } else if constexpr (cpl == 2) {
+                const float2 x = *reinterpret_cast<const float2*>(&s_at(c0));
+                sv[0] = x.x; sv[1] = x.y;
+            } else {
+                sv[0] = s_at(c0);
             }
-            if (col < m) a0 = fmaf(er[col], s_at(col), a0);
-            acc = a0 + a1;
         }
-        for (int o = 1; o < tpr; o <<= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        const int row0 = wid * mrows;
         float part = 0.0f;
-        if (j < m && c == 0) {
-            mu[j] = acc;
-            part = s_at(j) * acc;
+        if (row0 < m) {
+            int r = 0;
+            const float acc = oc_mu_rows<mrows, cpl>(einv + row0 * m, m, has, sv, lane, r);
+            if ((lane & (32 / mrows - 1)) == 0) {
+                mu[row0 + r] = acc;
+                part = s_at(row0 + r) * acc;
+            }
         }
         part = warp_sum(part);
         if (lane == 0) qf[wid] = part;
@@ -474,105 +522,107 @@ static __global__ void __launch_bounds__(kOnchipThreads, 1) k_pcg_onchip(CoarseP
             }
         }
         const float inv = (float)sc.inv;
-        float a1[2] = {0.0f, 0.0f}, s1 = 0.0f;
-#pragma unroll
-        for (int t = 0; t < kOnchipRows; ++t) {
-            if (row_of(t) >= 0) {
-                r_[t] *= inv;
-                z_[t] = d_[t] * r_[t];
-                e_[t] = 0.0f;
-                p_[t] = 0.0f;
-                q_[t] = 0.0f;
-                zl[lrow_of(t)] = z_[t];
-                a1[0] = fmaf(r_[t], z_[t], a1[0]);
-                if (in_space(t)) s1 += r_[t];
-            }
-        }
-        // <r, D^{-1} r> and Z^T r; the first z goes to every halo with it
-        float t1[2];
-        if (!cred32(a1, 1, s1, t1, true, m > 0)) {
-            status = CGP_ETIMEOUT;
-            break;
-        }
-        float rz = t1[0];
-        if (m) rz += coarse_fix(last_par);
         // ---- inner classical PCG in FP32 on the scaled residual; every warp carries the same
-        // scalars (rz, beta, rr_best), computed from the same totals
-        float beta = 0.0f, rr_best = INFINITY;
+        // scalars (rz, beta, rr_best), computed from the same totals.  Pass k = -1 only forms
+        // the first z (the scaled residual, its Jacobi part, its reduction and the coarse
+        // correction), so each reduction and the coarse correction have a single call site.
+        float beta = 0.0f, rr_best = INFINITY, rz = 0.0f;
         const float stop2 = sc.stop2;
         int best_k = 0;
         bool drift = false, aborted = false;
-        for (int k = 0; iters < a.maxit; ++k) {
-            // phase A: w = A z (local gathers), p = z + beta p, q = w + beta q, <p, q>
-            const float be = beta;
-            float pq_acc[2] = {0.0f, 0.0f};
-#pragma unroll
-            for (int t = 0; t < kOnchipRows; ++t) {
-                if (t >= nrow) break;
-                const uint2* ce = cent + base_[t] + lane;
-                const int w = width_[t];
-                float s = 0.0f;
-                for (int k = 0; k < w; k += 4) {
-                    const uint2 e0 = ce[32 * k], e1 = ce[32 * (k + 1)], e2 = ce[32 * (k + 2)], e3 = ce[32 * (k + 3)];
-                    const float g0 = zl[e0.x], g1 = zl[e1.x], g2 = zl[e2.x], g3 = zl[e3.x];
-                    s = fmaf(__uint_as_float(e0.y), g0, s);
-                    s = fmaf(__uint_as_float(e1.y), g1, s);
-                    s = fmaf(__uint_as_float(e2.y), g2, s);
-                    s = fmaf(__uint_as_float(e3.y), g3, s);
-                }
-                if (row_of(t) >= 0) {
-                    p_[t] = fmaf(be, p_[t], z_[t]);
-                    q_[t] = fmaf(be, q_[t], s);
-                    pq_acc[0] = fmaf(p_[t], q_[t], pq_acc[0]);
-                }
-            }
-            float pq[2];
-            if (!cred32(pq_acc, 1, 0.0f, pq, false, false)) {
-                aborted = true;
-                break;
-            }
-            if (!(pq[0] != 0.0f) || !isfinite(pq[0])) break;   // restart from the true residual
-            const float al = rz / pq[0];
-            // phase B (own rows): e += alpha p, r -= alpha q, z = D^{-1} r (+ the coarse
-            // correction once Z^T r is known)
+        for (int k = -1;; ++k) {
             float acc2[2] = {0.0f, 0.0f}, s2 = 0.0f;
+            if (k < 0) {
 #pragma unroll
-            for (int t = 0; t < kOnchipRows; ++t) {
-                if (row_of(t) >= 0) {
-                    e_[t] = fmaf(al, p_[t], e_[t]);
-                    r_[t] = fmaf(-al, q_[t], r_[t]);
-                    z_[t] = d_[t] * r_[t];
-                    zl[lrow_of(t)] = z_[t];
-                    acc2[0] = fmaf(r_[t], z_[t], acc2[0]);
-                    acc2[1] = fmaf(r_[t], r_[t], acc2[1]);
-                    if (in_space(t)) s2 += r_[t];
+                for (int t = 0; t < kOnchipRows; ++t) {
+                    if (row_of(t) >= 0) {
+                        r_[t] *= inv;
+                        z_[t] = d_[t] * r_[t];
+                        e_[t] = 0.0f;
+                        p_[t] = 0.0f;
+                        q_[t] = 0.0f;
+                        zl[lrow_of(t)] = z_[t];
+                        acc2[0] = fmaf(r_[t], z_[t], acc2[0]);
+                        acc2[1] = fmaf(r_[t], r_[t], acc2[1]);
+                        if (in_space(t)) s2 += r_[t];
+                    }
+                }
+            } else {
+                if (iters >= a.maxit) break;
+                // phase A: w = A z (local gathers), p = z + beta p, q = w + beta q, <p, q>
+                const float be = beta;
+                float pq_acc[2] = {0.0f, 0.0f};
+#pragma unroll
+                for (int t = 0; t < kOnchipRows; ++t) {
+                    if (t >= nrow) break;
+                    const uint2* ce = cent + base_[t] + lane;
+                    const int w = width_[t];
+                    float s = 0.0f;
+                    for (int k = 0; k < w; k += 4) {
+                        const uint2 e0 = ce[32 * k], e1 = ce[32 * (k + 1)], e2 = ce[32 * (k + 2)], e3 = ce[32 * (k + 3)];
+                        const float g0 = zl[e0.x], g1 = zl[e1.x], g2 = zl[e2.x], g3 = zl[e3.x];
+                        s = fmaf(__uint_as_float(e0.y), g0, s);
+                        s = fmaf(__uint_as_float(e1.y), g1, s);
+                        s = fmaf(__uint_as_float(e2.y), g2, s);
+                        s = fmaf(__uint_as_float(e3.y), g3, s);
+                    }
+                    if (row_of(t) >= 0) {
+                        p_[t] = fmaf(be, p_[t], z_[t]);
+                        q_[t] = fmaf(be, q_[t], s);
+                        pq_acc[0] = fmaf(p_[t], q_[t], pq_acc[0]);
+                    }
+                }
+                float pq[2];
+                if (!cred32(pq_acc, 1, 0.0f, pq, false, false)) {
+                    aborted = true;
+                    break;
+                }
+                if (!(pq[0] != 0.0f) || !isfinite(pq[0])) break;   // restart from the true residual
+                const float al = rz / pq[0];
+                // phase B (own rows): e += alpha p, r -= alpha q, z = D^{-1} r (+ the coarse
+                // correction once Z^T r is known)
+#pragma unroll
+                for (int t = 0; t < kOnchipRows; ++t) {
+                    if (row_of(t) >= 0) {
+                        e_[t] = fmaf(al, p_[t], e_[t]);
+                        r_[t] = fmaf(-al, q_[t], r_[t]);
+                        z_[t] = d_[t] * r_[t];
+                        zl[lrow_of(t)] = z_[t];
+                        acc2[0] = fmaf(r_[t], z_[t], acc2[0]);
+                        acc2[1] = fmaf(r_[t], r_[t], acc2[1]);
+                        if (in_space(t)) s2 += r_[t];
+                    }
                 }
             }
+            // <r, D^{-1} r>, <r, r> and Z^T r; the new z goes to every halo with them
             float t2[2];
-            if (!cred32(acc2, 2, s2, t2, true, m > 0)) {
+            if (!cred32(acc2, 2, s2, t2, true, MR > 0)) {
                 aborted = true;
                 break;
             }
-            ++iters;
+            if (k >= 0) ++iters;
             if (!isfinite(t2[0]) || !isfinite(t2[1])) {
                 drift = true;
                 break;
             }
-            if (t2[1] <= stop2 || t2[1] == 0.0f) break;
+            if (k >= 0 && (t2[1] <= stop2 || t2[1] == 0.0f)) break;
             float rzn = t2[0];
-            if (m) rzn += coarse_fix(last_par);
+            if constexpr (MR > 0) rzn += coarse_fix(last_par);
             if (!(rzn > 0.0f)) break;   // restart from the true residual
-            beta = rzn / rz;
-            rz = rzn;
-            if (t2[1] < 0.5f * rr_best) {
-                rr_best = t2[1];
-                best_k = k;
-            } else if (t2[1] > 1e4f * rr_best) {
-                drift = true;
-                break;
-            } else if (k - best_k > kStagnation32) {
-                break;
+            if (k >= 0) {
+                beta = rzn / rz;
+                if (t2[1] < 0.5f * rr_best) {
+                    rr_best = t2[1];
+                    best_k = k;
+                } else if (t2[1] > 1e4f * rr_best) {
+                    drift = true;
+                    break;
+                } else if (k - best_k > kStagnation32) {
+                    rz = rzn;
+                    break;
+                }
             }
+            rz = rzn;
         }
         if (aborted) {
             status = CGP_ETIMEOUT;
@@ -628,6 +678,14 @@ static __global__ void __launch_bounds__(kOnchipThreads, 1) k_pcg_onchip(CoarseP
         st->pad[1] = used_alt;
     }
     oc_barrier();   // no CTA leaves while another may still access its shared memory
+}
+
+// the kernel instance for a plan with nsub subdomains
+using OnchipKernelFn = void (*)(CoarsePcgArgs, OnchipPlan);
+inline OnchipKernelFn onchip_kernel(int nsub) {
+    if (nsub <= 0) return k_pcg_onchip<0>;
+    const int r = nsub >= 16 ? nsub / 16 : 1;
+    return r >= 8 ? k_pcg_onchip<8> : (r >= 4 ? k_pcg_onchip<4> : (r >= 2 ? k_pcg_onchip<2> : k_pcg_onchip<1>));
 }
 
 }  // namespace cgp

@@ -56,24 +56,15 @@ struct OnchipHostPlan {
 
 // Shared-memory layout of one CTA (byte offsets identical in every CTA):
 //   z[rows_max + halo_max] float (padded to 16 bytes) | red64[2][16][4] double |
-//   red32[2][16][kOnchipSlot] float | einv[nsub][onchip_einv_ld(nsub)] float |
-//   mu[nsub + 1] float (padded) |
+//   red32[2][16][kOnchipSlot] float | einv[nsub][nsub] float | mu[nsub + 1] float (padded) |
 //   qf[16] float | hsub[halo_max] byte (padded) | send[send_max] (local row, cluster address) |
 //   entry[ent] (local index of the column's z, FP32 value bits)
 __host__ __device__ __forceinline__ size_t onchip_z_bytes(int rows_max, int halo_max) {
     return (size_t)4 * (((size_t)rows_max + halo_max + 3) & ~(size_t)3);
 }
 __host__ __device__ __forceinline__ size_t onchip_red_bytes() { return 1024 + (size_t)4 * 2 * 16 * kOnchipSlot; }
-// threads that share one row of mu = E^+ s (a power of two, at most a warp), and the row
-// stride of E^+ in shared memory that keeps their loads free of bank conflicts
-__host__ __device__ __forceinline__ int onchip_mu_tpr(int nsub) {
-    int t = 32;
-    while (t > 1 && t * nsub > kOnchipThreads) t >>= 1;
-    return t;
-}
-__host__ __device__ __forceinline__ int onchip_einv_ld(int nsub) { return nsub ? nsub + onchip_mu_tpr(nsub) : 0; }
 __host__ __device__ __forceinline__ size_t onchip_cs_bytes(int nsub, int halo_max) {
-    return (size_t)4 * nsub * onchip_einv_ld(nsub) + (size_t)4 * ((nsub + 4) & ~3) + 64 +
+    return (size_t)4 * nsub * nsub + (size_t)4 * ((nsub + 4) & ~3) + 64 +
            (((size_t)halo_max + 15) & ~(size_t)15);
 }
 __host__ __device__ __forceinline__ size_t onchip_smem_bytes(int rows_max, int halo_max, int send_max, int64_t ent,

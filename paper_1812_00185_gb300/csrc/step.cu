@@ -702,8 +702,6 @@ int choose_coarse_solver(Solver& s, cudaStream_t st) {
             int optin = 0;
             CGP_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
             const size_t limit = (size_t)optin - 2048;   // static shared memory of the kernel
-            CGP_CUDA(cudaFuncSetAttribute(k_pcg_onchip, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
-            CGP_CUDA(cudaFuncSetAttribute(k_pcg_onchip, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)limit));
             const bool coarse_space = p.precond != CGP_PRECOND_JACOBI;
             for (int cs : {16, 8}) {
                 for (int spc : {8, 4, 2, 1, 0}) {
@@ -711,12 +709,15 @@ int choose_coarse_solver(Solver& s, cudaStream_t st) {
                     OnchipHostPlan P;
                     if (!onchip_plan(C.nv, rowptr, ptr, col, xy, in_space, cs, spc, limit, P)) continue;
                     if (!onchip_coarse_space(rowptr, ptr, col, val, P)) continue;
+                    const OnchipKernelFn kern = onchip_kernel(P.nsub);
+                    CGP_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+                    CGP_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)limit));
                     cudaLaunchAttribute attr[1];
                     cudaLaunchConfig_t cfg = cluster_config(cs, nullptr, attr);
                     cfg.blockDim = dim3(kOnchipThreads, 1, 1);
                     cfg.dynamicSmemBytes = P.bytes;
                     int n = 0;
-                    if (cudaOccupancyMaxActiveClusters(&n, k_pcg_onchip, &cfg) != cudaSuccess || n < 1) {
+                    if (cudaOccupancyMaxActiveClusters(&n, kern, &cfg) != cudaSuccess || n < 1) {
                         cudaGetLastError();
                         continue;
                     }
@@ -851,7 +852,7 @@ static int coarse_solve(Ctx& c) {
             cudaLaunchConfig_t cfg = cluster_config(s.cluster_size, c.st, attr);
             cfg.blockDim = dim3(kOnchipThreads, 1, 1);
             cfg.dynamicSmemBytes = s.onchip_bytes;
-            PL(c, CGP_PROF_POIS_CLUSTER, CGP_CUDA(cudaLaunchKernelEx(&cfg, k_pcg_onchip, a, s.onchip)));
+            PL(c, CGP_PROF_POIS_CLUSTER, CGP_CUDA(cudaLaunchKernelEx(&cfg, onchip_kernel(s.onchip.nsub), a, s.onchip)));
             return CGP_OK;
         }
         CGP_CUDA(cudaMemsetAsync(s.bar_count, 0, 2 * sizeof(unsigned int), c.st));   // counter + error word
