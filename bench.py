@@ -167,8 +167,8 @@ def kernel_bytes(name, n, z, t=0):
         "mom_prep": 64 * n, "finish": 112 * n, "corr_rhs": 20 * z + 4 * n + 8 * n + n + 16 * n,
         "div": 20 * z + 4 * n + 16 * n + 8 * n,
         # FP32 inner kernels of the mixed form: 4-byte values, vectors and Jacobi diagonal
-        "f32_corr_spmv": 8 * z + 4 * n + 32 * n, "f32_corr_update": 60 * n,
-        "f32_mass_spmv": 8 * z + 4 * n + 16 * n, "f32_mass_update": 32 * n,
+        # Chebyshev step of a mass solve: w = A d; e += d, r -= w, d' = c1 d + c2 D^-1 r
+        "cheb_corr": 8 * z + 4 * n + 52 * n, "cheb_mass": 8 * z + 4 * n + 28 * n,
         "f32_bicg_v": 8 * z + 4 * n + 24 * n, "f32_bicg_t": 8 * z + 4 * n + 24 * n,
         "f32_bicg_p": 44 * n, "f32_bicg_s": 36 * n, "f32_bicg_x": 64 * n, "to_f32": 12 * z + 12 * n,
     }

@@ -246,11 +246,12 @@ enum {
     CGP_PROF_DIV, CGP_PROF_MASS_SETUP, CGP_PROF_MASS_INIT, CGP_PROF_MASS_SPMV, CGP_PROF_MASS_UPDATE,
     CGP_PROF_FINISH, CGP_PROF_POIS_CLUSTER, CGP_PROF_MLP,
     /* CGP_MIXED fine-level solves: FP64 refinement residual / update, FP32 inner kernels */
-    CGP_PROF_IR_RESID, CGP_PROF_IR_UPDATE, CGP_PROF_TO_F32, CGP_PROF_F32_INIT, CGP_PROF_F32_CORR_SPMV,
-    CGP_PROF_F32_CORR_UPDATE, CGP_PROF_F32_MASS_SPMV, CGP_PROF_F32_MASS_UPDATE, CGP_PROF_F32_BICG_P,
+    CGP_PROF_IR_RESID, CGP_PROF_IR_UPDATE, CGP_PROF_TO_F32, CGP_PROF_F32_INIT, CGP_PROF_F32_BICG_P,
     CGP_PROF_F32_BICG_V, CGP_PROF_F32_BICG_S, CGP_PROF_F32_BICG_T, CGP_PROF_F32_BICG_X,
     /* p updates of the FP64 PCG loops (three kernels per iteration) */
-    CGP_PROF_POIS_PUPD, CGP_PROF_CORR_PUPD, CGP_PROF_MASS_PUPD, CGP_PROF_COUNT
+    CGP_PROF_POIS_PUPD, CGP_PROF_CORR_PUPD, CGP_PROF_MASS_PUPD,
+    /* CGP_MIXED: FP32 Chebyshev steps of the Eq. 26 and Eq. 25 mass-matrix solves */
+    CGP_PROF_CHEB_MASS, CGP_PROF_CHEB_CORR, CGP_PROF_COUNT
 };
 int cgp_profile_step(cgp_solver* s, cgp_stream_t stream, int32_t n_ids, int32_t* counts, double* total_ms);
 

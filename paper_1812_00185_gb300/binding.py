@@ -120,9 +120,9 @@ PROF_NAMES = ["mom_prep", "mom_assemble", "mom_setup", "mom_init", "bicg_p", "bi
               "bicg_x", "coarse_rhs", "pois_setup", "pois_init", "pois_spmv", "pois_update", "phi_mean",
               "phi_sub", "prolong", "corr_rhs", "corr_setup", "corr_init", "corr_spmv", "corr_update", "div",
               "mass_setup", "mass_init", "mass_spmv", "mass_update", "finish", "pois_onelaunch", "mlp_forward",
-              "ir_resid", "ir_update", "to_f32", "f32_init", "f32_corr_spmv", "f32_corr_update", "f32_mass_spmv",
-              "f32_mass_update", "f32_bicg_p", "f32_bicg_v", "f32_bicg_s", "f32_bicg_t", "f32_bicg_x",
-              "pois_pupd", "corr_pupd", "mass_pupd"]
+              "ir_resid", "ir_update", "to_f32", "f32_init", "f32_bicg_p", "f32_bicg_v", "f32_bicg_s", "f32_bicg_t",
+              "f32_bicg_x",
+              "pois_pupd", "corr_pupd", "mass_pupd", "cheb_mass", "cheb_corr"]
 
 _LIB = None
 

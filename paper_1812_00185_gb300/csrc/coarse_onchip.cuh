@@ -372,8 +372,11 @@ static __global__ void __launch_bounds__(kOnchipThreads, 1) k_pcg_onchip(CoarseP
         part = warp_sum(part);
         if (lane == 0) qf[wid] = part;
         __syncthreads();
-        float q = 0.0f;
-        for (int w = 0; w < nw; ++w) q += qf[w];
+        static_assert(kOnchipWarps == 16, "the partials of s^T mu are summed as four float4");
+        const float4* q4 = reinterpret_cast<const float4*>(qf);   // 16 warp partials, fixed-order tree
+        const float4 qa = q4[0], qb = q4[1], qc = q4[2], qd = q4[3];
+        const float q = (((qa.x + qa.y) + (qa.z + qa.w)) + ((qb.x + qb.y) + (qb.z + qb.w))) +
+                        (((qc.x + qc.y) + (qc.z + qc.w)) + ((qd.x + qd.y) + (qd.z + qd.w)));
         const float mw = mu[my_sub];
 #pragma unroll
         for (int t = 0; t < kOnchipRows; ++t) {

@@ -279,8 +279,9 @@ __global__ void k_finish(int nf, double* __restrict__ U, double* __restrict__ Up
         int64_t l = fixed_launches + 5 * (int64_t)ks[KS_MOM].iter;
         for (int k = KS_POIS; k < KS_COUNT; ++k)
             if (k != KS_POIS || pois_loop) l += 6 * (int64_t)((ks[k].iter + 1) / 2);
-        // FP32 inner loops of the mixed form: 5 kernels per BiCGStab trip, 4 per PCG trip
-        l += 5 * (int64_t)ks[KS_MOM].trips + 4 * (int64_t)(ks[KS_CORR].trips + ks[KS_MASS].trips);
+        // FP32 inner loops of the mixed form: 5 kernels per BiCGStab trip (the Chebyshev mass
+        // solves have a fixed launch count)
+        l += 5 * (int64_t)ks[KS_MOM].trips;
         stats->launches += l;
         if (ks[KS_POIS].pad[1]) stats->guess_used += 1;
         stats->sum_outer += ks[KS_POIS].pad[0];
@@ -524,7 +525,7 @@ __global__ void __launch_bounds__(kBlock) k_ir_update(int n, double* __restrict_
     if (in->skip) return;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         st->inner += in->iter;
-        st->trips += (in->iter + iters_per_trip - 1) / iters_per_trip;
+        if (iters_per_trip > 0) st->trips += (in->iter + iters_per_trip - 1) / iters_per_trip;
     }
     if (in->status == CGP_ENONFINITE) return;   // keep x; the FP64 loop takes over
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
@@ -538,6 +539,82 @@ __global__ void __launch_bounds__(kBlock) k_ir_update(int n, double* __restrict_
     }
 }
 
+// ---------------------------------------------------------------- Chebyshev mass solves
+// The two fine-level mass-matrix systems of the mixed form (Eq. 25's velocity correction
+// with M_0, Eq. 26's rotational term with M) run their FP32 inner solves as Chebyshev
+// semi-iteration with the Jacobi preconditioner instead of PCG.  For P1 triangles the
+// eigenvalues of D^{-1} M lie in [1/2, 2] (Wathen, IMA J. Numer. Anal. 7, 1987: each element
+// matrix D_e^{-1} M_e has eigenvalues 1/2, 1/2, 2), and so do those of D^{-1} M_0 (its phi =
+// 0 rows are identity rows, the rest a principal submatrix).  With those fixed bounds the
+// iteration needs no inner products: each step is one kernel (SpMV of d, then e, r and the
+// next d) with no grid-wide reduction, and k steps reduce the error by at least 2 / T_k(5/3)
+// (about 3^-k; 12 steps: below 1e-5).  The recurrence (theta, delta: centre and half-width
+// of the interval, sigma = theta / delta, rho_0 = 1 / sigma):
+//   d_0 = D^{-1} r_0 / theta;  e += d_k,  r -= A d_k,  rho_{k+1} = 1 / (2 sigma - rho_k),
+//   d_{k+1} = rho_{k+1} rho_k d_k + (2 rho_{k+1} / delta) D^{-1} r_{k+1}.
+// The FP64 residual of every refinement sweep and the FP64 PCG that follows stay the judge
+// of the tolerance, as for the other refinement solves.
+constexpr int kChebSweeps = 2;
+constexpr int kChebSteps = 12;
+constexpr double kChebLo = 0.5, kChebHi = 2.0;
+
+// d = D^{-1} r / theta, e = 0; the step count for the statistics
+template <int NC>
+__global__ void __launch_bounds__(kBlock) k_cheb_init(int n, const float* __restrict__ dinv, const float* __restrict__ r,
+                                                     float* __restrict__ d, float* __restrict__ e, KrylovState* in,
+                                                     float inv_theta) {
+    if (in->skip) return;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        in->iter = kChebSteps;
+        in->status = 0;
+    }
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        float rv[NC], dv[NC], zero[NC];
+        ldv<NC>(r, i, rv);
+        const float di = dinv[i] * inv_theta;
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            dv[c] = di * rv[c];
+            zero[c] = 0.0f;
+        }
+        stv<NC>(d, i, dv);
+        stv<NC>(e, i, zero);
+    }
+}
+
+// one step: w = A d_in; e += d_in, r -= w, d_out = c1 d_in + c2 D^{-1} r
+template <int NC>
+__global__ void __launch_bounds__(kBlock) k_cheb_step(SellView A, const float* __restrict__ val,
+                                                     const float* __restrict__ dinv, const float* __restrict__ din,
+                                                     float* __restrict__ dout, float* __restrict__ r,
+                                                     float* __restrict__ e, const KrylovState* in, float c1, float c2) {
+    if (in->skip) return;
+    const int lane = threadIdx.x & 31;
+    CGP_SLICE_LOOP(A, sl) {
+        const int i = sl * 32 + lane;
+        float ax[NC];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) ax[c] = 0.0f;
+        sell_accum<NC>(A, val, sl, lane, [&](int j, float (&o)[NC]) { ldv<NC>(din, j, o); }, ax);
+        if (i < A.n) {
+            float dv[NC], rv[NC], ev[NC];
+            ldv<NC>(din, i, dv);
+            ldv<NC>(r, i, rv);
+            ldv<NC>(e, i, ev);
+            const float di = dinv[i];
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+                ev[c] += dv[c];
+                rv[c] -= ax[c];
+                dv[c] = fmaf(c1, dv[c], c2 * di * rv[c]);
+            }
+            stv<NC>(e, i, ev);
+            stv<NC>(r, i, rv);
+            stv<NC>(dout, i, dv);
+        }
+    }
+}
+
 // FP32 copies of a matrix and its Jacobi diagonal
 __global__ void k_to_f32_pair(int64_t n1, const double* __restrict__ a1, float* __restrict__ b1, int64_t n2,
                               const double* __restrict__ a2, float* __restrict__ b2) {
@@ -546,43 +623,32 @@ __global__ void k_to_f32_pair(int64_t n1, const double* __restrict__ a1, float* 
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n2; i += stride) b2[i] = (float)a2[i];
 }
 
-// PCG with FP32 inner solves (mixed form); same contract as pcg<NC> without the projection
+// Mixed-form mass-matrix solve (Eqs. 25, 26): kChebSweeps refinement sweeps, each the FP64
+// residual (and convergence test) of the current x, kChebSteps FP32 Chebyshev steps on
+// A e = r, and x += e in FP64; then the FP64 PCG from that x to the tolerance.  Every kernel
+// of a sweep returns at once when the residual had already converged.
 template <int NC>
-static int pcg_mixed(Ctx& c, SellView A, const double* val, const float* valf, const double* dinv, const float* dinvf,
-                     double* b, double* x, KrylovState* ks, double tol, int maxit, bool zero_x, int pid, int spmv_id,
-                     int update_id) {
+static int cheb_mixed(Ctx& c, SellView A, const double* val, const float* valf, const double* dinv, const float* dinvf,
+                      double* b, double* x, KrylovState* ks, double tol, int maxit, bool zero_x, int pid, int step_id) {
     Solver& s = *c.s;
     KrylovState* in = s.ks + KS_COUNT;
     const int gs = grid_rows(s, A.nslices * 32, 1), gv = grid_rows(s, A.n, 1);
-    float *fr = s.fv[0], *fz = s.fv[1], *fp0 = s.fv[2], *fp1 = s.fv[3], *fq = s.fv[4], *fe = s.fv[5];
-    for (int sw = 0; sw < kIrSweeps; ++sw) {
+    float *fr = s.fv[0], *fe = s.fv[1], *fd[2] = {s.fv[2], s.fv[3]};
+    const double theta = 0.5 * (kChebHi + kChebLo), delta = 0.5 * (kChebHi - kChebLo), sigma = theta / delta;
+    for (int sw = 0; sw < kChebSweeps; ++sw) {
         PL(c, CGP_PROF_IR_RESID,
-           k_ir_residual<NC><<<gs, kBlock, 0, c.st>>>(A, val, b, x, s.frhs, ks, in, tol * tol, sw, zero_x && sw == 0,
+           k_ir_residual<NC><<<gs, kBlock, 0, c.st>>>(A, val, b, x, fr, ks, in, tol * tol, sw, zero_x && sw == 0,
                                                       s.partials, s.tickets));
-        CGP_LAUNCH_CHECK();
-        auto init = [&, gs](cudaStream_t st, unsigned long long h) -> int {
-            PL(c, CGP_PROF_F32_INIT,
-               k_pcg_init<NC, float><<<gs, kBlock, 0, st>>>(A, valf, dinvf, s.frhs, fe, fr, fz, fp0, in, s.partials,
-                                                            s.tickets, 1, 0, h));
-            CGP_LAUNCH_CHECK();
-            return CGP_OK;
-        };
-        auto body = [&, gs, gv](cudaStream_t st, unsigned long long h) -> int {
-            PL(c, spmv_id,
-               k_pcg_spmv<NC, float><<<gs, kBlock, 0, st>>>(A, valf, fz, fp0, fp1, fq, in, s.partials, s.tickets));
-            PL(c, update_id,
-               k_pcg_update<NC, float><<<gv, kBlock, 0, st>>>(A.n, dinvf, fe, fr, fz, fp1, fq, in, s.partials,
-                                                              s.tickets, h));
-            PL(c, spmv_id,
-               k_pcg_spmv<NC, float><<<gs, kBlock, 0, st>>>(A, valf, fz, fp1, fp0, fq, in, s.partials, s.tickets));
-            PL(c, update_id,
-               k_pcg_update<NC, float><<<gv, kBlock, 0, st>>>(A.n, dinvf, fe, fr, fz, fp0, fq, in, s.partials,
-                                                              s.tickets, h));
-            CGP_LAUNCH_CHECK();
-            return CGP_OK;
-        };
-        CGP_TRY(krylov_loop(c, in, (kIrInnerMaxit + 1) / 2 + 1, init, body));
-        PL(c, CGP_PROF_IR_UPDATE, k_ir_update<NC><<<gv, kBlock, 0, c.st>>>(A.n, x, fe, ks, in, 2));
+        PL(c, CGP_PROF_F32_INIT, k_cheb_init<NC><<<gv, kBlock, 0, c.st>>>(A.n, dinvf, fr, fd[0], fe, in, (float)(1.0 / theta)));
+        double rho = 1.0 / sigma;
+        for (int k = 0; k < kChebSteps; ++k) {
+            const double rho1 = 1.0 / (2.0 * sigma - rho);
+            PL(c, step_id,
+               k_cheb_step<NC><<<gs, kBlock, 0, c.st>>>(A, valf, dinvf, fd[k & 1], fd[(k + 1) & 1], fr, fe, in,
+                                                        (float)(rho1 * rho), (float)(2.0 * rho1 / delta)));
+            rho = rho1;
+        }
+        PL(c, CGP_PROF_IR_UPDATE, k_ir_update<NC><<<gv, kBlock, 0, c.st>>>(A.n, x, fe, ks, in, 0));
         CGP_LAUNCH_CHECK();
     }
     return pcg<NC>(c, A, val, dinv, b, x, ks, tol, maxit, false, false, pid);
@@ -952,9 +1018,8 @@ static int rotational_term(Ctx& c) {
        k_div<<<gs, kBlock, 0, c.st>>>(Af, s.Cx, s.Cy, s.Ut, s.div, lumped ? s.mlumpF : nullptr, s.qrot));
     CGP_LAUNCH_CHECK();
     if (!lumped && mixed)
-        CGP_TRY(pcg_mixed<1>(c, Af, s.M, s.Mf, s.dinvM, s.dinvMf, s.div, s.qrot, &s.ks[KS_MASS], p.tol_mass,
-                             p.max_it_mass, true, CGP_PROF_MASS_SETUP, CGP_PROF_F32_MASS_SPMV,
-                             CGP_PROF_F32_MASS_UPDATE));
+        CGP_TRY(cheb_mixed<1>(c, Af, s.M, s.Mf, s.dinvM, s.dinvMf, s.div, s.qrot, &s.ks[KS_MASS], p.tol_mass,
+                              p.max_it_mass, true, CGP_PROF_MASS_SETUP, CGP_PROF_CHEB_MASS));
     else if (!lumped)
         CGP_TRY(pcg<1>(c, Af, s.M, s.dinvM, s.div, s.qrot, &s.ks[KS_MASS], p.tol_mass, p.max_it_mass, true, false,
                        CGP_PROF_MASS_SETUP));
@@ -978,8 +1043,8 @@ int step_post(Ctx& c, bool mass_done) {
     CGP_LAUNCH_CHECK();
     const bool mixed = p.precision == CGP_MIXED;
     if (!lumped && mixed)
-        CGP_TRY(pcg_mixed<2>(c, Af, s.M0, s.M0f, s.dinvM0, s.dinvM0f, s.g, s.delta, &s.ks[KS_CORR], p.tol_mass,
-                             p.max_it_mass, true, CGP_PROF_CORR_SETUP, CGP_PROF_F32_CORR_SPMV, CGP_PROF_F32_CORR_UPDATE));
+        CGP_TRY(cheb_mixed<2>(c, Af, s.M0, s.M0f, s.dinvM0, s.dinvM0f, s.g, s.delta, &s.ks[KS_CORR], p.tol_mass,
+                              p.max_it_mass, true, CGP_PROF_CORR_SETUP, CGP_PROF_CHEB_CORR));
     else if (!lumped)
         CGP_TRY(pcg<2>(c, Af, s.M0, s.dinvM0, s.g, s.delta, &s.ks[KS_CORR], p.tol_mass, p.max_it_mass, true, false,
                        CGP_PROF_CORR_SETUP));
@@ -988,8 +1053,11 @@ int step_post(Ctx& c, bool mass_done) {
     const bool one_launch = s.coarse_kind != CGP_COARSE_KERNELS;
     const int coarse_fixed = (one_launch ? 1 : 2 + (s.pure_neumann ? 2 : 0)) +
                              ((p.guess == CGP_GUESS_LEARNED && s.guess_ready) ? 10 : 0);
-    // mixed: per refinement solve kIrSweeps x (residual, inner init, update), + the FP32 copy of A
-    const int ir_fixed = mixed ? 1 + 3 * kIrSweeps * (1 + (lumped ? 0 : 1) + (p.chi && !lumped ? 1 : 0)) : 0;
+    // mixed: the FP32 copy of A; momentum: kIrSweeps x (residual, inner init, update); each
+    // Chebyshev mass solve: kChebSweeps x (residual, init, kChebSteps steps, update)
+    const int ir_fixed = mixed ? 1 + 3 * kIrSweeps +
+                                     (3 + kChebSteps) * kChebSweeps * ((lumped ? 0 : 1) + (p.chi && !lumped ? 1 : 0))
+                               : 0;
     const int pt_fixed = p.restrict_mode == CGP_RESTRICT_PT ? 1 + (s.lf - s.lc) : 0;   // k_div + the P^T levels
     const int fixed =
         4 + 1 + coarse_fixed + (s.lf - s.lc) + 1 + (lumped ? 0 : 2) + (p.chi ? 1 + (lumped ? 0 : 2) : 0) + 1 + ir_fixed +
