@@ -592,16 +592,19 @@ __global__ void __launch_bounds__(kBlock) k_cheb_step(SellView A, const float* _
     const int lane = threadIdx.x & 31;
     CGP_SLICE_LOOP(A, sl) {
         const int i = sl * 32 + lane;
+        // the row's own operands first: their loads overlap the SpMV's dependent chain
+        float dv[NC], rv[NC], ev[NC], di = 0.0f;
+        if (i < A.n) {
+            ldv<NC>(din, i, dv);
+            ldv<NC>(r, i, rv);
+            ldv<NC>(e, i, ev);
+            di = dinv[i];
+        }
         float ax[NC];
 #pragma unroll
         for (int c = 0; c < NC; ++c) ax[c] = 0.0f;
         sell_accum<NC>(A, val, sl, lane, [&](int j, float (&o)[NC]) { ldv<NC>(din, j, o); }, ax);
         if (i < A.n) {
-            float dv[NC], rv[NC], ev[NC];
-            ldv<NC>(din, i, dv);
-            ldv<NC>(r, i, rv);
-            ldv<NC>(e, i, ev);
-            const float di = dinv[i];
 #pragma unroll
             for (int c = 0; c < NC; ++c) {
                 ev[c] += dv[c];
