@@ -399,6 +399,66 @@ static __device__ __forceinline__ void spmv2_row(const SellView& A, const T* __r
     sell_accum<2>(A, val, sl, lane, [&](int j, T (&o)[2]) { ldv<2>(u, j, o); }, ax);
 }
 
+// scalar steps of BiCGStab (one thread, after a grid sum), per right-hand side:
+// alpha = rho / <rhat, v>
+__device__ __forceinline__ void bicg_alpha(KrylovState* st, const double (&tot)[2]) {
+    for (int c = 0; c < 2; ++c) {
+        if (st->compdone[c]) {
+            st->alpha[c] = 0.0;
+        } else if (tot[c] != 0.0 && finite(tot[c])) {
+            st->alpha[c] = st->rho[c] / tot[c];
+        } else {
+            st->alpha[c] = 0.0;
+            st->compdone[c] = 1;
+            st->status = finite(tot[c]) ? CGP_EBREAKDOWN : CGP_ENONFINITE;
+        }
+    }
+}
+// omega = <t, s> / <t, t>
+__device__ __forceinline__ void bicg_omega(KrylovState* st, const double (&tot)[4]) {
+    for (int c = 0; c < 2; ++c) {
+        if (st->compdone[c]) {
+            st->omega[c] = 0.0;
+        } else if (tot[2 + c] > 0.0 && finite(tot[2 + c])) {
+            st->omega[c] = tot[c] / tot[2 + c];
+        } else {
+            st->omega[c] = 0.0;   // t = 0 means s = 0: x += alpha y finishes the solve
+        }
+    }
+}
+// from <rhat, r> and <r, r> of the new residual: convergence test, beta, rho, loop control
+__device__ __forceinline__ void bicg_finish(KrylovState* st, const double (&tot)[4], unsigned long long cond) {
+    int all = 1;
+    for (int c = 0; c < 2; ++c) {
+        if (!st->compdone[c]) {
+            if (!finite(tot[c]) || !finite(tot[2 + c])) {
+                st->status = CGP_ENONFINITE;
+                st->compdone[c] = 1;
+            } else {
+                st->rr[c] = tot[2 + c];
+                if (tot[2 + c] <= st->tol2 * st->bb[c]) {
+                    st->compdone[c] = 1;
+                } else if (st->omega[c] == 0.0 || st->rho[c] == 0.0) {
+                    st->compdone[c] = 1;
+                    st->status = CGP_EBREAKDOWN;
+                } else {
+                    st->beta[c] = (tot[c] / st->rho[c]) * (st->alpha[c] / st->omega[c]);
+                    st->rho[c] = tot[c];
+                }
+            }
+        }
+        if (st->compdone[c]) st->beta[c] = 0.0;
+        all &= st->compdone[c];
+    }
+    st->iter += 1;
+    if (!all && st->iter >= st->maxit) {
+        if (!st->status) st->status = CGP_ENOTCONV;
+        all = 1;
+    }
+    st->done = all;
+    set_loop_condition(cond, !all);
+}
+
 // init: r = b - A x (x = 0 if zero_x), rhat = r, p = v = 0; rho, rr, bb.  An inner solve
 // whose `skip` is set reports done at once.
 template <class T>
@@ -503,19 +563,7 @@ static __global__ void __launch_bounds__(kBlock) k_bicg_v(SellView A, const T* _
         }
     }
     double tot[2];
-    if (grid_sum<2>(acc, partials, ticket, tot) && threadIdx.x == 0) {
-        for (int c = 0; c < 2; ++c) {
-            if (st->compdone[c]) {
-                st->alpha[c] = 0.0;
-            } else if (tot[c] != 0.0 && finite(tot[c])) {
-                st->alpha[c] = st->rho[c] / tot[c];
-            } else {
-                st->alpha[c] = 0.0;
-                st->compdone[c] = 1;
-                st->status = finite(tot[c]) ? CGP_EBREAKDOWN : CGP_ENONFINITE;
-            }
-        }
-    }
+    if (grid_sum<2>(acc, partials, ticket, tot) && threadIdx.x == 0) bicg_alpha(st, tot);
 }
 
 // s = r - alpha v; z = D^{-1} s
@@ -560,17 +608,7 @@ static __global__ void __launch_bounds__(kBlock) k_bicg_t(SellView A, const T* _
         }
     }
     double tot[4];
-    if (grid_sum<4>(acc, partials, ticket, tot) && threadIdx.x == 0) {
-        for (int c = 0; c < 2; ++c) {
-            if (st->compdone[c]) {
-                st->omega[c] = 0.0;
-            } else if (tot[2 + c] > 0.0 && finite(tot[2 + c])) {
-                st->omega[c] = tot[c] / tot[2 + c];
-            } else {
-                st->omega[c] = 0.0;   // t = 0 means s = 0: x += alpha y finishes the solve
-            }
-        }
-    }
+    if (grid_sum<4>(acc, partials, ticket, tot) && threadIdx.x == 0) bicg_omega(st, tot);
 }
 
 // x += alpha y + omega z; r = s - omega t; rho' = <rhat, r>; beta; convergence test
@@ -601,37 +639,7 @@ static __global__ void __launch_bounds__(kBlock) k_bicg_x(int n, BicgVecsT<T> V,
         stv<2>(V.r, i, rv);
     }
     double tot[4];
-    if (grid_sum<4>(acc, partials, ticket, tot) && threadIdx.x == 0) {
-        int all = 1;
-        for (int c = 0; c < 2; ++c) {
-            if (!st->compdone[c]) {
-                if (!finite(tot[c]) || !finite(tot[2 + c])) {
-                    st->status = CGP_ENONFINITE;
-                    st->compdone[c] = 1;
-                } else {
-                    st->rr[c] = tot[2 + c];
-                    if (tot[2 + c] <= st->tol2 * st->bb[c]) {
-                        st->compdone[c] = 1;
-                    } else if (st->omega[c] == 0.0 || st->rho[c] == 0.0) {
-                        st->compdone[c] = 1;
-                        st->status = CGP_EBREAKDOWN;
-                    } else {
-                        st->beta[c] = (tot[c] / st->rho[c]) * (st->alpha[c] / st->omega[c]);
-                        st->rho[c] = tot[c];
-                    }
-                }
-            }
-            if (st->compdone[c]) st->beta[c] = 0.0;
-            all &= st->compdone[c];
-        }
-        st->iter += 1;
-        if (!all && st->iter >= st->maxit) {
-            if (!st->status) st->status = CGP_ENOTCONV;
-            all = 1;
-        }
-        st->done = all;
-        set_loop_condition(cond, !all);
-    }
+    if (grid_sum<4>(acc, partials, ticket, tot) && threadIdx.x == 0) bicg_finish(st, tot, cond);
 }
 
 }  // namespace cgp
