@@ -84,66 +84,85 @@ __device__ __forceinline__ float warp_sum(float v) {
     return v;
 }
 
-// Deterministic grid-wide sum of NR values per thread.  Every block writes its
-// partial sums to partials[blockIdx.x*NR + r]; the last block to arrive (ticket)
-// adds the partials in block order and returns true with the totals in tot[]
-// (valid in every thread of that block).  Other blocks return false.  All blocks
-// of the grid must call it exactly once.  The ticket is reset for the next use.
-// T = float: warp and block sums in FP32, block partials and the total in FP64.
+// Sums of NR values over a warp, written to out[0..NR) by the lanes that hold them (no
+// other lane writes).  A transpose reduction: with P = NR rounded up to a power of two,
+// each xor-shuffle round (offsets 16, 8, ...) halves the values a lane holds, until every
+// lane holds one partial row; the remaining rounds sum it.  That is P - 1 + log2(32 / P)
+// adds per lane instead of 5 NR, which matters for FP64 (a warp-wide FP64 add takes 16
+// clocks of this GPU's FP64 pipe).  The order of the additions is fixed.
+template <int NR, class T>
+__device__ __forceinline__ void warp_sums_to(const T (&v)[NR], T* out) {
+    constexpr int P = NR <= 1 ? 1 : (NR <= 2 ? 2 : (NR <= 4 ? 4 : 8));
+    static_assert(NR <= 8, "at most 8 values");
+    const int lane = threadIdx.x & 31;
+    T w[P];
+#pragma unroll
+    for (int i = 0; i < P; ++i) w[i] = i < NR ? v[i] : T(0);
+    int row = 0;
+#pragma unroll
+    for (int h = P, o = 16; h > 1; h >>= 1, o >>= 1) {
+        const bool up = (lane & o) != 0;
+        if (up) row += h / 2;
+#pragma unroll
+        for (int i = 0; i < h / 2; ++i) {
+            const T keep = up ? w[i + h / 2] : w[i];
+            const T send = up ? w[i] : w[i + h / 2];
+            w[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+        }
+    }
+#pragma unroll
+    for (int o = 16 / P; o > 0; o >>= 1) w[0] += __shfl_xor_sync(0xffffffffu, w[0], o);
+    if ((lane & (32 / P - 1)) == 0 && row < NR) out[row] = w[0];
+}
+
+// Deterministic grid-wide sum of NR values per thread, in the precision T of the values.
+// Every block writes its partial sums to partials[blockIdx.x*NR + r] (as T); the last
+// block to arrive (ticket) adds the partials in a fixed order and returns true with the
+// totals in tot[] (valid in every thread of that block).  Other blocks return false.  All
+// blocks of the grid must call it exactly once.  The ticket is reset for the next use.
+// T = float (the FP32 inner solves) keeps the whole reduction off the FP64 pipe: the
+// block partials are FP32 sums already, and an FP32 tree over them adds an error far below
+// the inner solves' tolerance.
 template <int NR, class T>
 __device__ bool grid_sum(const T (&v)[NR], double* partials, unsigned int* ticket, double (&tot)[NR]) {
     __shared__ T smt[kBlock / 32][NR];
-    __shared__ double sm[kBlock / 32][NR];
+    __shared__ T res[NR];
     __shared__ bool is_last;
+    T* pt = reinterpret_cast<T*>(partials);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    // warps -> CTA: the CTA's partials, written by lane 0 of warp 0
+    auto cta_sum = [&](const T (&x)[NR]) {
+        warp_sums_to(x, smt[wid]);
+        __syncthreads();
+        if (wid == 0) {
+            T y[NR];
 #pragma unroll
-    for (int r = 0; r < NR; ++r) {
-        T w = warp_sum(v[r]);
-        if (lane == 0) smt[wid][r] = w;
-    }
-    __syncthreads();
-    if (wid == 0) {
+            for (int r = 0; r < NR; ++r) y[r] = lane < nw ? smt[lane][r] : T(0);
+            warp_sums_to(y, res);
+        }
+        __syncthreads();
+    };
+    cta_sum(v);
+    if (threadIdx.x == 0) {
 #pragma unroll
-        for (int r = 0; r < NR; ++r) {
-            T x = lane < nw ? smt[lane][r] : T(0);
-            x = warp_sum(x);
-            if (lane == 0) partials[(size_t)blockIdx.x * NR + r] = (double)x;
-        }
-        if (lane == 0) {
-            __threadfence();
-            unsigned int t = atomicAdd(ticket, 1u);
-            is_last = (t == gridDim.x - 1);
-        }
+        for (int r = 0; r < NR; ++r) pt[(size_t)blockIdx.x * NR + r] = res[r];
+        __threadfence();
+        is_last = (atomicAdd(ticket, 1u) == gridDim.x - 1);
     }
     __syncthreads();
     if (!is_last) return false;
     __threadfence();
-    double s[NR];
+    T s[NR];
 #pragma unroll
-    for (int r = 0; r < NR; ++r) s[r] = 0.0;
+    for (int r = 0; r < NR; ++r) s[r] = T(0);
     for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
 #pragma unroll
-        for (int r = 0; r < NR; ++r) s[r] += __ldcg(partials + (size_t)b * NR + r);
+        for (int r = 0; r < NR; ++r) s[r] += __ldcg(pt + (size_t)b * NR + r);
     }
-    __syncthreads();   // sm reuse
+    cta_sum(s);
+    if (threadIdx.x == 0) *ticket = 0u;
 #pragma unroll
-    for (int r = 0; r < NR; ++r) {
-        double w = warp_sum(s[r]);
-        if (lane == 0) sm[wid][r] = w;
-    }
-    __syncthreads();
-    if (wid == 0) {
-#pragma unroll
-        for (int r = 0; r < NR; ++r) {
-            double x = lane < nw ? sm[lane][r] : 0.0;
-            x = warp_sum(x);
-            if (lane == 0) sm[0][r] = x;
-        }
-        if (lane == 0) *ticket = 0u;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int r = 0; r < NR; ++r) tot[r] = sm[0][r];
+    for (int r = 0; r < NR; ++r) tot[r] = (double)res[r];
     return true;
 }
 
