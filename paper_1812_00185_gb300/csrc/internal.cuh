@@ -155,9 +155,21 @@ __device__ bool grid_sum(const T (&v)[NR], double* partials, unsigned int* ticke
     T s[NR];
 #pragma unroll
     for (int r = 0; r < NR; ++r) s[r] = T(0);
-    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
+    // the partial loads are issued in chunks of U per thread (64 bytes of registers), so
+    // the block waits for one memory round trip per chunk instead of one per partial
+    constexpr int U = (64 / (NR * (int)sizeof(T))) < 1 ? 1 : ((64 / (NR * (int)sizeof(T))) > 8 ? 8 : 64 / (NR * (int)sizeof(T)));
+    for (int b0 = threadIdx.x; b0 < (int)gridDim.x; b0 += U * blockDim.x) {
+        T q[U][NR];
 #pragma unroll
-        for (int r = 0; r < NR; ++r) s[r] += __ldcg(pt + (size_t)b * NR + r);
+        for (int k = 0; k < U; ++k) {
+            const int b = b0 + k * blockDim.x;
+#pragma unroll
+            for (int r = 0; r < NR; ++r) q[k][r] = b < (int)gridDim.x ? __ldcg(pt + (size_t)b * NR + r) : T(0);
+        }
+#pragma unroll
+        for (int k = 0; k < U; ++k)
+#pragma unroll
+            for (int r = 0; r < NR; ++r) s[r] += q[k][r];
     }
     cta_sum(s);
     if (threadIdx.x == 0) *ticket = 0u;
