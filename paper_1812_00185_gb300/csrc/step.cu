@@ -455,8 +455,9 @@ static int bicgstab(Ctx& c, SellView A, const double* val, const double* dinv, c
 
 // ---------------------------------------------------------------- mixed form: FP32 inner solves
 // Iterative refinement for the fine-level systems of the mixed form (Eqs. 21, 25, 26): each
-// sweep forms the FP64 residual r = b - A x, solves A e = r in FP32 (PCG or BiCGStab, to a
-// reduction kIrInnerTol of its residual norm) and adds e to x in FP64.  The FP64 Krylov
+// sweep forms the FP64 residual r = b - A x, solves A e = r in FP32 (BiCGStab for Eq. 21 to
+// a reduction kIrInnerTol of its residual norm, or less when less is left to reach the
+// tolerance; fixed Chebyshev steps for the mass systems) and adds e to x in FP64.  The FP64 Krylov
 // loop that follows polishes x to the tolerance and stops at once (its init sees the
 // converged residual) when the sweeps already met it, so the result has the accuracy of
 // the FP64 solve.  A sweep whose residual already meets the tolerance skips its inner solve.
@@ -510,7 +511,16 @@ __global__ void __launch_bounds__(kBlock) k_ir_residual(SellView A, const double
             ok &= finite(tot[c]);
         }
         in->skip = (all || !ok) ? 1 : 0;
-        in->tol2 = kIrInnerTol * kIrInnerTol;
+        // the inner solve aims at kIrInnerTol, or at what is left to the tolerance with a
+        // factor 2 of margin in the norm when that is less (the strictest component counts)
+        double t2 = kIrInnerTol * kIrInnerTol;
+        if (ok) {
+            double need = 1.0;
+            for (int c = 0; c < NC; ++c)
+                if (tot[c] > tol2 * st->bb[c]) need = fmin(need, 0.25 * tol2 * st->bb[c] / tot[c]);
+            t2 = fmax(t2, need);
+        }
+        in->tol2 = t2;
         in->maxit = kIrInnerMaxit;
         in->iter = 0;
         in->done = 0;
