@@ -24,7 +24,9 @@ struct KrylovState {
     int compdone[2];
     int pad[2];
     int inner, trips;      // mixed form: FP32 inner iterations and inner loop trips of the solve
-    int skip, pad2;        // inner solves: set when the outer residual already meets the tolerance
+    int skip;              // inner solves: set when the outer residual already meets the tolerance
+    int ir_done;           // outer solves of the mixed form: the last refinement residual met the
+                           // tolerance (the FP64 loop that follows then reports done at its init)
 };
 
 // SELL-32 pattern of a level (see Level): one warp works on one slice of 32 rows,

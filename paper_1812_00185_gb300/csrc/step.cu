@@ -307,7 +307,8 @@ __global__ void k_ks_setup(KrylovState* st, double tol2, int maxit) {
     st->status = 0;
     st->pad[0] = 0;
     st->pad[1] = 0;
-    st->skip = 0;
+    st->skip = st->ir_done;   // refinement met the tolerance: the init keeps its residual, iter 0
+    st->ir_done = 0;
 }
 
 // ---------------------------------------------------------------- loop control
@@ -511,6 +512,7 @@ __global__ void __launch_bounds__(kBlock) k_ir_residual(SellView A, const double
             ok &= finite(tot[c]);
         }
         in->skip = (all || !ok) ? 1 : 0;
+        st->ir_done = (all && ok) ? 1 : 0;
         // the inner solve aims at kIrInnerTol, or at what is left to the tolerance with a
         // factor 2 of margin in the norm when that is less (the strictest component counts)
         double t2 = kIrInnerTol * kIrInnerTol;
