@@ -66,7 +66,10 @@ __global__ void k_mom_prep(int nf, const double* __restrict__ U, const double* _
 //   A = 3/2 M + dt N(w) + dt/Re K,  N_ij = sum_T |T|/12 (W_T + w_i) . grad psi_j
 //   b = dt (Cx^T P, Cy^T P) + M h     (pressure term in weak form, see the readings)
 // Dirichlet rows: identity row, b = u_D(t^{n+1}).  Also x0 = w (u_D on Dirichlet rows), dinv.
-__global__ void k_mom_assemble(int nf, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+// Rows of at most kAsmRow entries are accumulated in shared memory ([entry][thread], so the
+// lanes of a warp hit distinct banks) and written to A once; longer rows add into A directly.
+constexpr int kAsmRow = 16;
+__global__ void __launch_bounds__(kBlock) k_mom_assemble(int nf, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
                                const int32_t* __restrict__ sell_ptr, const int32_t* __restrict__ vt_ptr, const int32_t* __restrict__ vt_list,
                                const int32_t* __restrict__ tri, const double* __restrict__ geo,
                                const int32_t* __restrict__ vtslot, const double* __restrict__ S,
@@ -76,10 +79,12 @@ __global__ void k_mom_assemble(int nf, const int32_t* __restrict__ rowptr, const
                                const uint8_t* __restrict__ tag, const double* __restrict__ xy, BcParams bc,
                                const double* __restrict__ tdev, double dt, double* __restrict__ A,
                                double* __restrict__ dinv, double* __restrict__ b, double* __restrict__ x0) {
+    __shared__ double arow[kAsmRow][kBlock];
     const double tn = *tdev + dt;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nf; i += gridDim.x * blockDim.x) {
         const int rb = rowptr[i], re = rowptr[i + 1];
         const int64_t e0 = sell_pos(sell_ptr, i, 0);   // entry k of the row is at e0 + 32 k
+        const bool local = re - rb <= kAsmRow;
         if (tag[i] & CGP_VEL_DIR) {
             for (int q = rb; q < re; ++q) A[e0 + 32 * (q - rb)] = col[q] == i ? 1.0 : 0.0;
             dinv[i] = 1.0;
@@ -92,7 +97,10 @@ __global__ void k_mom_assemble(int nf, const int32_t* __restrict__ rowptr, const
         double bx = 0.0, by = 0.0;
         for (int q = rb; q < re; ++q) {
             const int64_t e = e0 + 32 * (q - rb);
-            A[e] = S[e];
+            if (local)
+                arow[q - rb][threadIdx.x] = S[e];
+            else
+                A[e] = S[e];
             const int j = col[q];
             const double2 hj = reinterpret_cast<const double2*>(h)[j];
             const double pj = P[j];
@@ -109,17 +117,26 @@ __global__ void k_mom_assemble(int nf, const int32_t* __restrict__ rowptr, const
             const double2 w0 = reinterpret_cast<const double2*>(w)[a0];
             const double2 w1 = reinterpret_cast<const double2*>(w)[a1];
             const double2 w2 = reinterpret_cast<const double2*>(w)[a2];
-            const double c = gt[0] / 12.0;
+            const double c = gt[0] * (1.0 / 12.0);
             const double cx = c * (w0.x + w1.x + w2.x + wi.x), cy = c * (w0.y + w1.y + w2.y + wi.y);
             const int li = packed & 3;
 #pragma unroll
             for (int k = 0; k < 3; ++k) {
                 const int slot = (packed >> (8 * (k + 1))) & 255;
-                A[e0 + 32 * slot] += dt * (cx * gt[1 + 2 * k] + cy * gt[2 + 2 * k]);
+                const double v = dt * (cx * gt[1 + 2 * k] + cy * gt[2 + 2 * k]);
+                if (local)
+                    arow[slot][threadIdx.x] += v;
+                else
+                    A[e0 + 32 * slot] += v;
                 if (k == li) diag_slot = slot;
             }
         }
-        dinv[i] = 1.0 / A[e0 + 32 * diag_slot];
+        if (local) {
+            for (int q = 0; q < re - rb; ++q) A[e0 + 32 * q] = arow[q][threadIdx.x];
+            dinv[i] = 1.0 / arow[diag_slot][threadIdx.x];
+        } else {
+            dinv[i] = 1.0 / A[e0 + 32 * diag_slot];
+        }
         reinterpret_cast<double2*>(b)[i] = make_double2(bx, by);
         reinterpret_cast<double2*>(x0)[i] = wi;
     }
