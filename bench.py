@@ -107,7 +107,7 @@ def workload_problem(name):
     return w, w.base_mesh()
 
 
-def make_params(cg, w, form, use_graph=1, tol_inner=0.0):
+def make_params(cg, w, form, use_graph=1, tol_inner=0.0, mass_mode=0):
     mixed = form in ("mixed", "mixed_learned", "mixed_zero", "mixed_jacobi")
     learned = form in ("learned", "mixed_learned")
     guess = cg.CGP_GUESS_LEARNED if learned else (cg.CGP_GUESS_ZERO if form == "mixed_zero" else cg.CGP_GUESS_PREV)
@@ -116,7 +116,8 @@ def make_params(cg, w, form, use_graph=1, tol_inner=0.0):
                           precision=cg.CGP_MIXED if mixed else cg.CGP_FP64,
                           guess=guess, bc_kind=w.bc,
                           bc_param=w.bc_param, use_graph=use_graph, tol_inner=tol_inner,
-                          precond=cg.CGP_PRECOND_JACOBI if form == "mixed_jacobi" else cg.CGP_PRECOND_AUTO)
+                          precond=cg.CGP_PRECOND_JACOBI if form == "mixed_jacobi" else cg.CGP_PRECOND_AUTO,
+                          mass_mode=mass_mode)
 
 
 def train_guess(cg, w, args):
@@ -166,6 +167,9 @@ def kernel_bytes(name, n, z, t=0):
                         + 16 * n + n,
         "mom_prep": 64 * n, "finish": 112 * n, "corr_rhs": 20 * z + 4 * n + 8 * n + n + 16 * n,
         "div": 20 * z + 4 * n + 16 * n + 8 * n,
+        # injection fused with the coarse divergence (Eqs. 22-23): Cx, Cy values + columns,
+        # U~ at the coarse vertices, the right-hand side and the tags
+        "coarse_rhs": 20 * z + 4 * n + 16 * n + 8 * n + n,
         # FP32 inner kernels of the mixed form: 4-byte values, vectors and Jacobi diagonal
         # Chebyshev step of a mass solve: w = A d; e += d, r -= w, d' = c1 d + c2 D^-1 r
         "cheb_corr": 8 * z + 4 * n + 52 * n, "cheb_mass": 8 * z + 4 * n + 28 * n,
@@ -202,7 +206,8 @@ def run_gpu(args, rank, world):
 
     def run_form(form, steps, warmup, timed=True):
         t0 = time.time()
-        s = cg.Solver(mesh, make_params(cg, w, form, args.graph, args.tol_inner))
+        s = cg.Solver(mesh, make_params(cg, w, form, args.graph, args.tol_inner,
+                                        cg.CGP_MASS_LUMPED if args.mass == "lumped" else cg.CGP_MASS_CONSISTENT))
         if form in ("learned", "mixed_learned"):
             cg.cgp_guess_set(s.handle, learned["net"])
         torch.cuda.synchronize()
@@ -276,9 +281,15 @@ def run_gpu(args, rank, world):
     prof = cg.cgp_profile_step(s.handle)
     peak, peak_kind = _peaks()
     kern = {}
+    # prolongation (Eq. 24), one launch per level: phi at the coarse vertices copied, the
+    # midpoint average of two parents (indices and values) at the new ones, phi written
+    lv = [mesh.info(l)[0] for l in range(w.n_levels - w.k, w.n_levels + 1)]
+    prolong_bytes = sum(8 * lv[i] + 16 * (lv[i + 1] - lv[i]) + 8 * lv[i + 1] for i in range(len(lv) - 1))
     for name, (cnt, tot) in prof.items():
         n, z, t = (nv_c, nnz_c, nt_c) if level_of(name) == "coarse" else (nv_f, nnz_f, nt_f)
         b = kernel_bytes(name, n, z, t)
+        if name == "prolong":
+            b = prolong_bytes / max(1, w.k)   # per launch (one per level)
         avg = tot / cnt
         kern[name] = {"launches": cnt, "total_ms": round(tot, 4), "avg_us": round(1000 * avg, 2),
                       "GBps": round(b / (avg * 1e-3) / 1e9, 1) if b else None}
@@ -333,7 +344,7 @@ def run_gpu(args, rank, world):
         "dtype": "f32+f64" if "mixed" in head_form else "f64", "data": "synthetic",
         "config": {"workload": args.workload, "form": head_form, "fine_triangles": nt_f, "fine_vertices": nv_f,
                    "coarse_vertices": nv_c, "k": w.k, "chi": w.chi, "Re": w.Re, "dt": w.dt,
-                   "tol": w.tol_poisson, "parallelism": "replicas" if world > 1 else "single",
+                   "tol": w.tol_poisson, "mass": args.mass, "parallelism": "replicas" if world > 1 else "single",
                    "l2": "working set %.2f GB > 129 MB L2 (no flush)" % (1e-9 * ws_bytes)},
         "e2e": e2e, "gpu_launches": int(head["launches"]), "clocks": head["clocks"], "roofline": roof, "roofline_hbm": roof_hbm,
         "forms": forms, "kernels": kern, "setup_s": {"mesh": round(t_mesh, 3), "assemble": round(head["assemble_s"], 3)},
@@ -479,6 +490,8 @@ def main():
     ap.add_argument("--quick", action="store_true", help="skip the secondary measurements")
     ap.add_argument("--graph", type=int, default=1, choices=[0, 1],
                     help="1: replay steps as CUDA graphs; 0: eager launches (what ncu can profile)")
+    ap.add_argument("--mass", default="consistent", choices=["consistent", "lumped"],
+                    help="mass matrix of Eqs. 25-26 (lumped = Eq. 27)")
     ap.add_argument("--pcg-only", action="store_true",
                     help="print only the PCG bandwidth sweep (one JSON line per problem size)")
     args = ap.parse_args()

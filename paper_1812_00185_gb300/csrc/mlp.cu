@@ -108,6 +108,66 @@ __global__ void k_mlp_nmean(int n, int batch, const int32_t* __restrict__ rowptr
     for (int f = 0; f < F; ++f) mb[(size_t)f * n + i] = acc[f] * inv;
 }
 
+// The 64-wide 1-ring means read vertex-major: a feature-major gather reads one 4-byte value
+// per 32-byte sector for each (neighbour, feature); a vertex-major one reads each neighbour's
+// 64 features as one 256-byte run.  hv[b][i][f] = act(h[b][f][i]) by 32 x 32 tiles through
+// shared memory (coalesced on both sides).
+template <bool RELU>
+__global__ void __launch_bounds__(256) k_mlp_to_vmajor(int n, const float* __restrict__ h, float* __restrict__ hv) {
+    __shared__ float tile[32][33];
+    const int b = blockIdx.z, i0 = blockIdx.x * 32, f0 = blockIdx.y * 32;
+    const float* hb = h + (size_t)b * kHid * n;
+    float* vb = hv + (size_t)b * n * kHid;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    for (int k = ty; k < 32; k += 8) {
+        const int i = i0 + tx;
+        const float v = i < n ? hb[(size_t)(f0 + k) * n + i] : 0.0f;
+        tile[k][tx] = RELU ? fmaxf(v, 0.0f) : v;
+    }
+    __syncthreads();
+    for (int k = ty; k < 32; k += 8) {
+        const int i = i0 + k;
+        if (i < n) vb[(size_t)i * kHid + f0 + tx] = tile[tx][k];
+    }
+}
+
+// m[b][f][i] = mean over the 1-ring (i excluded) of hv[b][j][f] for 32 vertices per block: a
+// warp per vertex (lanes over features, two each, neighbours in CSR order as in
+// k_mlp_nmean), written back feature-major through shared memory
+__global__ void __launch_bounds__(256) k_mlp_nmean64(int n, const int32_t* __restrict__ rowptr,
+                                                    const int32_t* __restrict__ col, const float* __restrict__ hv,
+                                                    float* __restrict__ m) {
+    static_assert(kHid == 64, "two features per lane");
+    __shared__ float tile[kHid][33];
+    const int b = blockIdx.y, i0 = blockIdx.x * 32;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const float2* vb = reinterpret_cast<const float2*>(hv + (size_t)b * n * kHid);
+    for (int v = wid; v < 32; v += 8) {
+        const int i = i0 + v;
+        float ax = 0.0f, ay = 0.0f;
+        int deg = 0;
+        if (i < n) {
+            for (int e = rowptr[i]; e < rowptr[i + 1]; ++e) {
+                const int j = col[e];
+                if (j == i) continue;
+                ++deg;
+                const float2 x = vb[(size_t)j * (kHid / 2) + lane];
+                ax += x.x;
+                ay += x.y;
+            }
+        }
+        const float inv = deg ? 1.0f / deg : 0.0f;
+        tile[2 * lane][v] = ax * inv;
+        tile[2 * lane + 1][v] = ay * inv;
+    }
+    __syncthreads();
+    float* mb = m + (size_t)b * kHid * n;
+    for (int f = wid; f < kHid; f += 8) {
+        const int i = i0 + lane;
+        if (i < n) mb[(size_t)f * n + i] = tile[f][lane];
+    }
+}
+
 // a[b][o][i] = sum_k W[o][k] x_k + bias[o], x = [act(h); m] (2*FIN inputs)
 template <int FIN, int FOUT, bool RELU_IN>
 __global__ void __launch_bounds__(128) k_mlp_dense(int n, int batch, const __nv_bfloat16* __restrict__ W,
@@ -347,6 +407,7 @@ void MlpBuffers::carve(Carve& cv, int n_, int batch) {
     m1 = cv.take<float>(kHid * nb);
     a2 = cv.take<float>(kHid * nb);
     m2 = cv.take<float>(kHid * nb);
+    hv = cv.take<float>(kHid * nb);
     out = cv.take<float>(nb);
     params_bf = cv.take<__nv_bfloat16>(kMlpParams);
     params = cv.take<float>(kMlpParams);
@@ -363,10 +424,13 @@ int mlp_forward(const MlpBuffers& B, const Level& L, const double* r, const doub
     k_mlp_nmean<4, false><<<g, kBlock, 0, st>>>(n, batch, L.rowptr, L.col, B.h0, B.m0);
     k_mlp_dense<4, kHid, false><<<g128, 128, 0, st>>>(n, batch, B.params_bf + kOffW1, B.params + kOffB1, B.h0, B.m0,
                                                       B.a1);
-    k_mlp_nmean<kHid, true><<<g, kBlock, 0, st>>>(n, batch, L.rowptr, L.col, B.a1, B.m1);
+    const dim3 gt((n + 31) / 32, kHid / 32, batch), gm((n + 31) / 32, batch);
+    k_mlp_to_vmajor<true><<<gt, 256, 0, st>>>(n, B.a1, B.hv);
+    k_mlp_nmean64<<<gm, 256, 0, st>>>(n, L.rowptr, L.col, B.hv, B.m1);
     k_mlp_dense<kHid, kHid, true><<<g128, 128, 0, st>>>(n, batch, B.params_bf + kOffW2, B.params + kOffB2, B.a1, B.m1,
                                                         B.a2);
-    k_mlp_nmean<kHid, true><<<g, kBlock, 0, st>>>(n, batch, L.rowptr, L.col, B.a2, B.m2);
+    k_mlp_to_vmajor<true><<<gt, 256, 0, st>>>(n, B.a2, B.hv);
+    k_mlp_nmean64<<<gm, 256, 0, st>>>(n, L.rowptr, L.col, B.hv, B.m2);
     k_mlp_dense<kHid, 1, true><<<g128, 128, 0, st>>>(n, batch, B.params_bf + kOffW3, B.params + kOffB3, B.a2, B.m2,
                                                      B.out);
     if (pred) k_mlp_predict<<<g, kBlock, 0, st>>>(n, batch, q, B.out, B.scale, pred);

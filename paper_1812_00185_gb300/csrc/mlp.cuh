@@ -28,6 +28,7 @@ struct MlpBuffers {
     float *h0 = nullptr, *m0 = nullptr;         // [batch][4][n]
     float *a1 = nullptr, *m1 = nullptr;         // [batch][64][n] pre-activations / neighbour means
     float *a2 = nullptr, *m2 = nullptr;
+    float* hv = nullptr;                        // [batch][n][64]: vertex-major copy for the 1-ring means
     float* out = nullptr;                       // [batch][n]
     __nv_bfloat16* params_bf = nullptr;         // bfloat16 copy used by the forward kernels
     float* params = nullptr;                    // FP32 master (biases are read from here)
