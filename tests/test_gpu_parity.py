@@ -267,6 +267,22 @@ def test_onchip_coarse_correction_cuts_iterations(cg):
     m.close()
 
 
+def test_mixed_mass_solves_run_chebyshev_steps(cg):
+    """The mixed form's mass-matrix solves (Eqs. 25-26) run fixed FP32 Chebyshev steps inside
+    FP64 refinement (two sweeps of 12 steps each), and the steps still match the oracle."""
+    m, s, o = _pair(cg, _channel_small(), 2, 1, 20.0, 0.005, 1, flows.BC_CHANNEL, bp=(0.3, 0.41, 0, 0),
+                    precision=cg.CGP_MIXED)
+    s.step(2)
+    o.run(2)
+    prof = cg.cgp_profile_step(s.handle)   # one more step, eager launches with events
+    o.run(1)
+    assert prof.get("cheb_corr", (0, 0.0))[0] == 24 and prof.get("cheb_mass", (0, 0.0))[0] == 24, prof
+    U, P, t, st, rc = s.fields()
+    assert rc == 0
+    assert rel(U, o.U) < 1e-6 and rel(P, o.P) < 1e-6, (rel(U, o.U), rel(P, o.P))
+    s.close(); m.close()
+
+
 def test_coarse_solver_choice(cg):
     base = square_mesh(16)
     m = cg.Mesh(base.xy, base.tri, base.tag, 2)

@@ -180,3 +180,23 @@ def test_pt_rhs_equals_injection_for_prolonged_velocity(k):
     # on a general fine field they differ (the variant is not the paper's restriction)
     Ur = rng.standard_normal(Uf.shape)
     assert np.abs(o_inj.coarse_rhs(Ur) - o_pt.coarse_rhs(Ur)).max() > 1e-3 * np.abs(o_inj.coarse_rhs(Ur)).max()
+
+
+@pytest.mark.parametrize("mk,levels", [(lambda: square_mesh(6), 1), (lambda: crisscross_mesh(4), 1),
+                                       (lambda: channel_cylinder_mesh(seed=4, h=0.05), 1)])
+def test_jacobi_scaled_mass_spectrum_in_wathen_interval(mk, levels):
+    """The eigenvalues of D^{-1} M for the consistent P1 mass matrix lie in [1/2, 2] (every
+    element matrix D_e^{-1} M_e has eigenvalues 1/2, 1/2, 2), and so do those of M with the
+    Dirichlet rows and columns eliminated (identity rows plus a principal submatrix).  The
+    mixed form's Chebyshev mass solves use exactly this interval; dense eigenvalues of the
+    symmetric scaling D^{-1/2} M D^{-1/2} on small meshes check it."""
+    from oracle.cgp import _symmetric_eliminate, VEL_DIR
+    base = mk()
+    lev = build_hierarchy(base.xy, base.tri, base.tag, levels)[levels]
+    M = fem.static_operators(lev.xy, lev.tri)["M"]
+    for A in (M, _symmetric_eliminate(M, (lev.tag & VEL_DIR) != 0)):
+        A = A.toarray()
+        d = 1.0 / np.sqrt(np.diag(A))
+        w = np.linalg.eigvalsh(d[:, None] * A * d[None, :])
+        assert w.min() >= 0.5 - 1e-12 and w.max() <= 2.0 + 1e-12, (w.min(), w.max())
+        assert w.max() > 1.9 and w.min() < 0.6   # the bound is nearly attained: not a loose test
