@@ -356,6 +356,37 @@ def run_gpu(args, rank, world):
     return out, (w, base)
 
 
+def mlp_forward_time(cg, torch, w, reps=50):
+    """Event-timed forward pass of the learned initial guess's MLP on the workload's Poisson
+    level (batch 1, seeded inputs, the untrained initial weights)."""
+    from paper_1812_00185_gb300 import learned
+    base = w.base_mesh()
+    mesh = cg.Mesh(base.xy, base.tri, base.tag, w.n_levels)
+    lvl = w.n_levels - w.k   # the Poisson (coarse) level
+    n = cg.cgp_mesh_level_info(mesh.handle, lvl)[0]
+    net = cg.cgp_mlp_create(mesh.handle, lvl, 1)
+    cg.cgp_mlp_set_params(net, learned.init_params(0))
+    g = torch.Generator().manual_seed(0)
+    r = torch.randn(n, dtype=torch.float64, generator=g).cuda()
+    q = torch.randn(n, dtype=torch.float64, generator=g).cuda()
+    pred = torch.empty(n, dtype=torch.float64, device="cuda")
+    for _ in range(3):
+        cg.cgp_mlp_forward(net, r, q, 1, pred)
+    torch.cuda.synchronize()
+    st = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(reps):
+        cg.cgp_mlp_forward(net, r, q, 1, pred)
+    e1.record(st)
+    torch.cuda.synchronize()
+    us = 1000.0 * e0.elapsed_time(e1) / reps
+    cg.cgp_mlp_destroy(net)
+    mesh.close()
+    return {"metric": "MLP forward time", "value": round(us, 2), "unit": "us", "higher_is_better": False,
+            "vertices": int(n), "batch": 1, "reps": reps, "config": {"workload": w.name, "level": lvl}}
+
+
 def pcg_bandwidth(cg, torch, n_side, peak):
     """GB/s of the coarse-Poisson PCG iteration on an n_side^2 x 2 structured mesh (k = 0)."""
     from workloads import square_mesh, PHI_ZERO
@@ -492,6 +523,9 @@ def main():
                     help="1: replay steps as CUDA graphs; 0: eager launches (what ncu can profile)")
     ap.add_argument("--mass", default="consistent", choices=["consistent", "lumped"],
                     help="mass matrix of Eqs. 25-26 (lumped = Eq. 27)")
+    ap.add_argument("--mlp-only", action="store_true",
+                    help="print only the MLP forward time of the learned guess on the workload's Poisson "
+                         "level (--steps forward passes)")
     ap.add_argument("--pcg-only", action="store_true",
                     help="print only the PCG bandwidth sweep (one JSON line per problem size)")
     args = ap.parse_args()
@@ -515,6 +549,14 @@ def main():
         }))
         return 0
 
+    if args.mlp_only:
+        if rank != 0:
+            return 0
+        import torch
+        from paper_1812_00185_gb300 import binding as cg
+        w, _ = workload_problem(args.workload)
+        print(json.dumps(mlp_forward_time(cg, torch, w, args.steps)), flush=True)
+        return 0
     if args.pcg_only:
         if rank != 0:
             return 0

@@ -110,27 +110,8 @@ __global__ void k_mlp_nmean(int n, int batch, const int32_t* __restrict__ rowptr
 
 // The 64-wide 1-ring means read vertex-major: a feature-major gather reads one 4-byte value
 // per 32-byte sector for each (neighbour, feature); a vertex-major one reads each neighbour's
-// 64 features as one 256-byte run.  hv[b][i][f] = act(h[b][f][i]) by 32 x 32 tiles through
-// shared memory (coalesced on both sides).
-template <bool RELU>
-__global__ void __launch_bounds__(256) k_mlp_to_vmajor(int n, const float* __restrict__ h, float* __restrict__ hv) {
-    __shared__ float tile[32][33];
-    const int b = blockIdx.z, i0 = blockIdx.x * 32, f0 = blockIdx.y * 32;
-    const float* hb = h + (size_t)b * kHid * n;
-    float* vb = hv + (size_t)b * n * kHid;
-    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-    for (int k = ty; k < 32; k += 8) {
-        const int i = i0 + tx;
-        const float v = i < n ? hb[(size_t)(f0 + k) * n + i] : 0.0f;
-        tile[k][tx] = RELU ? fmaxf(v, 0.0f) : v;
-    }
-    __syncthreads();
-    for (int k = ty; k < 32; k += 8) {
-        const int i = i0 + k;
-        if (i < n) vb[(size_t)i * kHid + f0 + tx] = tile[tx][k];
-    }
-}
-
+// 64 features as one 256-byte run.  The dense layer that produces the features also writes
+// this copy, hv[b][i][f] = relu(a[b][f][i]).
 // m[b][f][i] = mean over the 1-ring (i excluded) of hv[b][j][f] for 32 vertices per block: a
 // warp per vertex (lanes over features, two each, neighbours in CSR order as in
 // k_mlp_nmean), written back feature-major through shared memory
@@ -168,35 +149,98 @@ __global__ void __launch_bounds__(256) k_mlp_nmean64(int n, const int32_t* __res
     }
 }
 
-// a[b][o][i] = sum_k W[o][k] x_k + bias[o], x = [act(h); m] (2*FIN inputs)
-template <int FIN, int FOUT, bool RELU_IN>
+// a[b][o][i] = sum_k W[o][k] x_k + bias[o], x = [act(h); m] (2*FIN inputs), summed in k
+// order; with VOUT also hv[b][i][o] = relu(a[b][o][i]) (the vertex-major copy the next
+// 1-ring mean gathers).  W (bf16, row-major FOUT x 2*FIN) is staged per block as FP32
+// columns wt[k][o]: lane l of a warp loads 8 consecutive k of row o = l (16 bytes) and
+// writes them down column l, so the transposed writes are free of bank conflicts.  With
+// FOUT >= 32 two threads share a vertex (the first half of the block takes outputs
+// [0, FOUT/2), the second half the rest, so a warp reads one wt row as a broadcast).  Each
+// thread loads its inputs in chunks before using them, so the L2 latency of the
+// feature-major input loads is paid once per chunk, not once per input.
+template <int FOUT>
+__host__ __device__ constexpr int dense_vertices_per_block() { return FOUT >= 32 ? 64 : 128; }   // of 128 threads
+
+template <int FIN, int FOUT, bool RELU_IN, bool VOUT>
 __global__ void __launch_bounds__(128) k_mlp_dense(int n, int batch, const __nv_bfloat16* __restrict__ W,
                                                    const float* __restrict__ bias, const float* __restrict__ h,
-                                                   const float* __restrict__ m, float* __restrict__ a) {
+                                                   const float* __restrict__ m, float* __restrict__ a,
+                                                   float* __restrict__ hv) {
     constexpr int K = 2 * FIN;
-    __shared__ float wt[K][FOUT];   // transposed, FP32
-    for (int e = threadIdx.x; e < K * FOUT; e += blockDim.x) {
-        const int o = e / K, k = e % K;
-        wt[k][o] = __bfloat162float(W[e]);
+    constexpr int VB = dense_vertices_per_block<FOUT>();
+    constexpr int OS = 128 / VB;                        // threads per vertex
+    constexpr int FO = FOUT / OS;                       // outputs per thread
+    constexpr int LD = FOUT == 1 ? 1 : FOUT + 4;        // row stride of wt (16-byte rows)
+    constexpr int KCMAX = FO == 1 ? 32 : 16;
+    constexpr int KC = FIN < KCMAX ? FIN : KCMAX;       // inputs loaded per chunk
+    constexpr int NV8 = K * FOUT / 8;                   // 16-byte pieces of W
+    static_assert(FOUT % OS == 0 && (FO == 1 || FO % 4 == 0) && FIN % KC == 0 && K % 8 == 0, "dense layer shape");
+    static_assert(!VOUT || FO % 4 == 0, "vertex-major copy in 16-byte stores");
+    __shared__ __align__(16) float wt[K][LD];
+    const uint4* W8 = reinterpret_cast<const uint4*>(W);
+#pragma unroll
+    for (int r = 0; r < (NV8 + 127) / 128; ++r) {
+        const int f = threadIdx.x + 128 * r;
+        if (f < NV8) {
+            const int o = f % FOUT, k0 = 8 * (f / FOUT);
+            const uint4 u = __ldg(W8 + (o * K + k0) / 8);
+            const uint32_t wd[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const float2 w2 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&wd[j]));
+                wt[k0 + 2 * j][o] = w2.x;
+                wt[k0 + 2 * j + 1][o] = w2.y;
+            }
+        }
     }
     __syncthreads();
-    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int part = threadIdx.x / VB;
+    const int64_t t = blockIdx.x * (int64_t)VB + threadIdx.x % VB;
     if (t >= (int64_t)n * batch) return;
     const int b = (int)(t / n), i = (int)(t % n);
-    const float* hb = h + (size_t)b * FIN * n;
-    const float* mb = m + (size_t)b * FIN * n;
-    float acc[FOUT];
+    const int o0 = part * FO;
+    float acc[FO];
 #pragma unroll
-    for (int o = 0; o < FOUT; ++o) acc[o] = bias[o];
-    for (int k = 0; k < K; ++k) {
-        float x = k < FIN ? hb[(size_t)k * n + i] : mb[(size_t)(k - FIN) * n + i];
-        if (RELU_IN && k < FIN) x = fmaxf(x, 0.0f);
+    for (int o = 0; o < FO; ++o) acc[o] = bias[o0 + o];
+    auto block = [&](const float* src, int kb, bool relu) {
+        for (int c = 0; c < FIN; c += KC) {
+            float xs[KC];
 #pragma unroll
-        for (int o = 0; o < FOUT; ++o) acc[o] += wt[k][o] * x;
-    }
+            for (int u = 0; u < KC; ++u) {
+                const float x = src[(size_t)(c + u) * n + i];
+                xs[u] = relu ? fmaxf(x, 0.0f) : x;
+            }
+#pragma unroll
+            for (int u = 0; u < KC; ++u) {
+                const float* wr = &wt[kb + c + u][o0];
+                if constexpr (FO % 4 == 0) {
+#pragma unroll
+                    for (int o = 0; o < FO; o += 4) {
+                        const float4 w4 = *reinterpret_cast<const float4*>(wr + o);
+                        acc[o] += w4.x * xs[u];
+                        acc[o + 1] += w4.y * xs[u];
+                        acc[o + 2] += w4.z * xs[u];
+                        acc[o + 3] += w4.w * xs[u];
+                    }
+                } else {
+#pragma unroll
+                    for (int o = 0; o < FO; ++o) acc[o] += wr[o] * xs[u];
+                }
+            }
+        }
+    };
+    block(h + (size_t)b * FIN * n, 0, RELU_IN);
+    block(m + (size_t)b * FIN * n, FIN, false);
     float* ab = a + (size_t)b * FOUT * n;
 #pragma unroll
-    for (int o = 0; o < FOUT; ++o) ab[(size_t)o * n + i] = acc[o];
+    for (int o = 0; o < FO; ++o) ab[(size_t)(o0 + o) * n + i] = acc[o];
+    if constexpr (VOUT) {
+        float4* vr = reinterpret_cast<float4*>(hv + ((size_t)b * n + i) * FOUT + o0);
+#pragma unroll
+        for (int o = 0; o < FO; o += 4)
+            vr[o / 4] = make_float4(fmaxf(acc[o], 0.0f), fmaxf(acc[o + 1], 0.0f), fmaxf(acc[o + 2], 0.0f),
+                                    fmaxf(acc[o + 3], 0.0f));
+    }
 }
 
 // Phi0 = q + s_q * out (double)
@@ -417,22 +461,22 @@ int mlp_forward(const MlpBuffers& B, const Level& L, const double* r, const doub
                 cudaStream_t st) {
     const int n = B.n;
     const int64_t nb = (int64_t)n * batch;
-    const int g = blocks_for(nb), g128 = blocks_for(nb, 128);
+    const int g = blocks_for(nb);
+    const int gh = blocks_for(nb, dense_vertices_per_block<kHid>());
+    const int g1 = blocks_for(nb, dense_vertices_per_block<1>());
     k_mlp_scales<<<dim3(kScaleBlocks, batch), kBlock, 0, st>>>(n, r, q, B.spart);
     k_mlp_scales_fin<<<batch, 32, 0, st>>>(n, kScaleBlocks, B.spart, B.scale);
     k_mlp_features<<<g, kBlock, 0, st>>>(n, batch, r, q, L.xy, B.scale, B.h0);
     k_mlp_nmean<4, false><<<g, kBlock, 0, st>>>(n, batch, L.rowptr, L.col, B.h0, B.m0);
-    k_mlp_dense<4, kHid, false><<<g128, 128, 0, st>>>(n, batch, B.params_bf + kOffW1, B.params + kOffB1, B.h0, B.m0,
-                                                      B.a1);
-    const dim3 gt((n + 31) / 32, kHid / 32, batch), gm((n + 31) / 32, batch);
-    k_mlp_to_vmajor<true><<<gt, 256, 0, st>>>(n, B.a1, B.hv);
+    k_mlp_dense<4, kHid, false, true><<<gh, 128, 0, st>>>(n, batch, B.params_bf + kOffW1, B.params + kOffB1, B.h0,
+                                                           B.m0, B.a1, B.hv);
+    const dim3 gm((n + 31) / 32, batch);
     k_mlp_nmean64<<<gm, 256, 0, st>>>(n, L.rowptr, L.col, B.hv, B.m1);
-    k_mlp_dense<kHid, kHid, true><<<g128, 128, 0, st>>>(n, batch, B.params_bf + kOffW2, B.params + kOffB2, B.a1, B.m1,
-                                                        B.a2);
-    k_mlp_to_vmajor<true><<<gt, 256, 0, st>>>(n, B.a2, B.hv);
+    k_mlp_dense<kHid, kHid, true, true><<<gh, 128, 0, st>>>(n, batch, B.params_bf + kOffW2, B.params + kOffB2, B.a1,
+                                                             B.m1, B.a2, B.hv);
     k_mlp_nmean64<<<gm, 256, 0, st>>>(n, L.rowptr, L.col, B.hv, B.m2);
-    k_mlp_dense<kHid, 1, true><<<g128, 128, 0, st>>>(n, batch, B.params_bf + kOffW3, B.params + kOffB3, B.a2, B.m2,
-                                                     B.out);
+    k_mlp_dense<kHid, 1, true, false><<<g1, 128, 0, st>>>(n, batch, B.params_bf + kOffW3, B.params + kOffB3, B.a2,
+                                                           B.m2, B.out, nullptr);
     if (pred) k_mlp_predict<<<g, kBlock, 0, st>>>(n, batch, q, B.out, B.scale, pred);
     CGP_LAUNCH_CHECK();
     return CGP_OK;
