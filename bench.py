@@ -275,7 +275,7 @@ def run_gpu(args, rank, world):
     torch.cuda.synchronize()
     e2e_ms = ev0.elapsed_time(ev1) / e2e_steps
     e2e = {"value": 1000.0 / e2e_ms * world, "unit": "steps/s", "h2d_bytes_per_step": 8 * 5 * nv_f,
-           "d2h_bytes_per_step": 8 * 3 * nv_f}
+           "d2h_bytes_per_step": 8 * 3 * nv_f, "ms_per_step": round(e2e_ms, 4)}
 
     # per-kernel device times of one profiled step (events around every launch)
     prof = cg.cgp_profile_step(s.handle)
@@ -500,6 +500,21 @@ def cpu_oracle_rate(w, base, budget_s):
                                         % (n, w.name, o.fine.n_vert, setup)}, n, wall
 
 
+def aggregate_ranks(out, world, device):
+    """Replicas on `world` ranks: the slowest rank's step time (device-timed and end to
+    end) sets the job's time, and the job's throughput is the steps of all ranks over it.
+    Every rank calls this (an all-reduce over the default process group)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([out["ms_per_step"], out["e2e"]["ms_per_step"]], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    out["ms_per_step"] = round(float(t[0].item()), 4)
+    out["value"] = round(1000.0 * world / out["ms_per_step"], 3)
+    out["e2e"]["ms_per_step"] = round(float(t[1].item()), 4)
+    out["e2e"]["value"] = round(1000.0 * world / out["e2e"]["ms_per_step"], 3)
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -574,12 +589,7 @@ def main():
         dist.init_process_group("nccl")
     out, (w, base) = run_gpu(args, rank, world)
     if world > 1:
-        import torch
-        import torch.distributed as dist
-        t = torch.tensor([out["ms_per_step"]], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        out["ms_per_step"] = round(float(t.item()), 4)
-        out["value"] = round(1000.0 * world / out["ms_per_step"], 3)
+        aggregate_ranks(out, world, "cuda")
     if rank == 0:
         if world == 1 and not args.quick:
             out["cpu_baseline"], _, _ = cpu_oracle_rate(w, base, args.cpu_budget)
