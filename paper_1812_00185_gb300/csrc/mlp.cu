@@ -156,8 +156,8 @@ __global__ void __launch_bounds__(256) k_mlp_nmean64(int n, const int32_t* __res
 // writes them down column l, so the transposed writes are free of bank conflicts.  With
 // FOUT >= 32 two threads share a vertex (the first half of the block takes outputs
 // [0, FOUT/2), the second half the rest, so a warp reads one wt row as a broadcast).  Each
-// thread loads its inputs in chunks before using them, so the L2 latency of the
-// feature-major input loads is paid once per chunk, not once per input.
+// thread loads its inputs in chunks, the next chunk while it multiplies the current one,
+// so the latency of the feature-major input loads overlaps the FMAs.
 template <int FOUT>
 __host__ __device__ constexpr int dense_vertices_per_block() { return FOUT >= 32 ? 64 : 128; }   // of 128 threads
 
@@ -202,35 +202,49 @@ __global__ void __launch_bounds__(128) k_mlp_dense(int n, int batch, const __nv_
     float acc[FO];
 #pragma unroll
     for (int o = 0; o < FO; ++o) acc[o] = bias[o0 + o];
-    auto block = [&](const float* src, int kb, bool relu) {
-        for (int c = 0; c < FIN; c += KC) {
-            float xs[KC];
+    // chunk c holds inputs k = c KC .. c KC + KC - 1: the first FIN / KC chunks come from h
+    // (with the ReLU when RELU_IN), the rest from m; two register buffers alternate, so the
+    // loads of chunk c + 1 are in flight while chunk c is multiplied
+    constexpr int NCH = K / KC;
+    static_assert(NCH % 2 == 0, "chunks come in pairs");
+    const float* hb = h + (size_t)b * FIN * n + i;
+    const float* mb = m + (size_t)b * FIN * n + i;
+    auto load = [&](float (&xs)[KC], int c) {
+        const bool from_h = c < FIN / KC;
+        const float* src = from_h ? hb + (size_t)c * KC * n : mb + (size_t)(c - FIN / KC) * KC * n;
 #pragma unroll
-            for (int u = 0; u < KC; ++u) {
-                const float x = src[(size_t)(c + u) * n + i];
-                xs[u] = relu ? fmaxf(x, 0.0f) : x;
-            }
+        for (int u = 0; u < KC; ++u) {
+            const float x = src[(size_t)u * n];
+            xs[u] = (RELU_IN && from_h) ? fmaxf(x, 0.0f) : x;
+        }
+    };
+    auto mul = [&](const float (&xs)[KC], int c) {
 #pragma unroll
-            for (int u = 0; u < KC; ++u) {
-                const float* wr = &wt[kb + c + u][o0];
-                if constexpr (FO % 4 == 0) {
+        for (int u = 0; u < KC; ++u) {
+            const float* wr = &wt[c * KC + u][o0];
+            if constexpr (FO % 4 == 0) {
 #pragma unroll
-                    for (int o = 0; o < FO; o += 4) {
-                        const float4 w4 = *reinterpret_cast<const float4*>(wr + o);
-                        acc[o] += w4.x * xs[u];
-                        acc[o + 1] += w4.y * xs[u];
-                        acc[o + 2] += w4.z * xs[u];
-                        acc[o + 3] += w4.w * xs[u];
-                    }
-                } else {
-#pragma unroll
-                    for (int o = 0; o < FO; ++o) acc[o] += wr[o] * xs[u];
+                for (int o = 0; o < FO; o += 4) {
+                    const float4 w4 = *reinterpret_cast<const float4*>(wr + o);
+                    acc[o] += w4.x * xs[u];
+                    acc[o + 1] += w4.y * xs[u];
+                    acc[o + 2] += w4.z * xs[u];
+                    acc[o + 3] += w4.w * xs[u];
                 }
+            } else {
+#pragma unroll
+                for (int o = 0; o < FO; ++o) acc[o] += wr[o] * xs[u];
             }
         }
     };
-    block(h + (size_t)b * FIN * n, 0, RELU_IN);
-    block(m + (size_t)b * FIN * n, FIN, false);
+    float xa[KC], xb[KC];
+    load(xa, 0);
+    for (int c = 0; c < NCH; c += 2) {
+        load(xb, c + 1);
+        mul(xa, c);
+        if (c + 2 < NCH) load(xa, c + 2);
+        mul(xb, c + 1);
+    }
     float* ab = a + (size_t)b * FOUT * n;
 #pragma unroll
     for (int o = 0; o < FO; ++o) ab[(size_t)(o0 + o) * n + i] = acc[o];
