@@ -48,31 +48,79 @@ def _peaks():
 
 
 class ClockSampler:
-    """nvidia-smi samples of SM clock and throttle reasons while the timed region runs."""
+    """nvidia-smi samples of SM clock and throttle reasons around a timed region.
 
-    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    The sampler starts before the region (nvidia-smi needs a moment to start), every sample
+    carries nvidia-smi's own timestamp, and the summary keeps the samples taken between
+    `start()` and `stop()`; `stop()` waits (bounded) for the first sample after the region,
+    and when the region is shorter than the interval, that sample stands for it."""
+
+    Q = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    NAMES = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
 
-    def __init__(self, gpu_index):
+    def __init__(self, gpu_index, interval_ms=50, cmd=None):
         self.gpu = gpu_index
+        self.intervals = [interval_ms] if cmd else [interval_ms, 200]   # 200 ms if nvidia-smi refuses the first
+        self.interval = interval_ms / 1000.0
+        self.cmd = cmd
         self.proc = None
-        self.lines = []
+        self.samples = []          # (unix time, fields)
+        self.t0 = self.t1 = None
+
+    def _command(self, interval_ms):
+        return self.cmd or ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.Q,
+                            "--format=csv,noheader,nounits", "-lms", str(interval_ms)]
 
     def __enter__(self):
-        try:
-            self.proc = subprocess.Popen(
-                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.Q, "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
-            self.t = threading.Thread(target=self._read, daemon=True)
-            self.t.start()
-        except Exception:
+        for ms in self.intervals:
+            try:
+                self.interval = ms / 1000.0
+                self.proc = subprocess.Popen(self._command(ms), stdout=subprocess.PIPE, stderr=subprocess.DEVNULL,
+                                             text=True)
+                self.t = threading.Thread(target=self._read, daemon=True)
+                self.t.start()
+                self._wait(lambda: len(self.samples) > 0, 5.0)
+            except Exception:
+                self.proc = None
+            if self.samples:
+                break
+            self.__exit__()
             self.proc = None
         return self
 
+    @staticmethod
+    def _parse(line):
+        import datetime
+        f = [x.strip() for x in line.split(",")]
+        if len(f) < 10:
+            return None
+        try:
+            ts = datetime.datetime.strptime(f[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+            float(f[2])
+        except ValueError:
+            return None
+        return ts, f
+
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            r = self._parse(line)
+            if r is not None:
+                self.samples.append(r)
+
+    def _wait(self, cond, limit):
+        end = time.time() + limit
+        while not cond() and time.time() < end and self.proc is not None and self.proc.poll() is None:
+            time.sleep(0.005)
+
+    def start(self):
+        self.t0 = time.time()
+
+    def stop(self):
+        self.t1 = time.time()
+        t1 = self.t1
+        self._wait(lambda: any(ts >= t1 for ts, _ in self.samples), 4 * self.interval + 1.0)
 
     def __exit__(self, *a):
         if self.proc:
@@ -82,23 +130,36 @@ class ClockSampler:
             except Exception:
                 self.proc.kill()
 
+    def window(self):
+        """Samples of the timed region: those between start() and stop(), else the first
+        one after start() (a region shorter than the sampling interval)."""
+        rows = list(self.samples)
+        if self.t0 is None or self.t1 is None:
+            return rows
+        inside = [r for r in rows if self.t0 <= r[0] <= self.t1]
+        if inside:
+            return inside
+        after = [r for r in rows if r[0] >= self.t0]
+        return after[:1]
+
     def summary(self):
         sm, mx, reasons = [], None, set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for l in self.lines:
-            f = [x.strip() for x in l.split(",")]
-            if len(f) < 9:
-                continue
+        rows = self.window()
+        for _, f in rows:
             try:
-                sm.append(float(f[1]))
-                mx = float(f[2])
+                sm.append(float(f[2]))
+                mx = float(f[3])
             except ValueError:
                 continue
-            for n, v in zip(names, f[5:9]):
+            for n, v in zip(self.NAMES, f[6:10]):
                 if v.lower() == "active":
                     reasons.add(n)
-        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
-                "reasons": sorted(reasons), "samples": len(sm)}
+        out = {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+               "reasons": sorted(reasons), "samples": len(sm)}
+        if self.t0 is not None and self.t1 is not None:
+            out["window_ms"] = round(1000.0 * (self.t1 - self.t0), 1)
+            out["interval_ms"] = round(1000.0 * self.interval)
+        return out
 
 
 def workload_problem(name):
@@ -212,19 +273,21 @@ def run_gpu(args, rank, world):
             cg.cgp_guess_set(s.handle, learned["net"])
         torch.cuda.synchronize()
         t_asm = time.time() - t0
-        s.step(warmup)
-        U0, P0, t0_sim, st0, _ = s.fields()
-        # state at the start of the timed region (fields and the previous increment the coarse guess uses)
-        start = (U0, s.vector(cg.CGP_VEC_UPREV), P0, t0_sim, s.vector(cg.CGP_VEC_PHI_C))
-        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        if world > 1:
-            torch.distributed.barrier()
-        torch.cuda.synchronize()
         with ClockSampler(dev) as clk:
+            s.step(warmup)
+            U0, P0, t0_sim, st0, _ = s.fields()
+            # state at the start of the timed region (fields and the previous increment the coarse guess uses)
+            start = (U0, s.vector(cg.CGP_VEC_UPREV), P0, t0_sim, s.vector(cg.CGP_VEC_PHI_C))
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            if world > 1:
+                torch.distributed.barrier()
+            torch.cuda.synchronize()
+            clk.start()
             ev0.record(stream)
             s.step(steps)
             ev1.record(stream)
             torch.cuda.synchronize()
+            clk.stop()
         if world > 1:
             torch.distributed.barrier()
         ms = ev0.elapsed_time(ev1)
