@@ -3,7 +3,7 @@
 import numpy as np
 import pytest
 
-from workloads import square_mesh, batch_instances
+from workloads import square_mesh
 from oracle.cgp import CGPOracle
 from oracle import flows
 

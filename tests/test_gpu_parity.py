@@ -4,7 +4,7 @@ import numpy as np
 import pytest
 import scipy.sparse as sp
 
-from workloads import square_mesh, crisscross_mesh, channel_cylinder_mesh, VEL_DIR, PHI_ZERO, WORKLOADS
+from workloads import square_mesh, crisscross_mesh, channel_cylinder_mesh, WORKLOADS
 from oracle.mesh import build_hierarchy
 from oracle.cgp import CGPOracle
 from oracle import fem, flows

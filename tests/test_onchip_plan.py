@@ -9,7 +9,6 @@ GPU needed."""
 import os
 import shutil
 import subprocess
-import tempfile
 
 import numpy as np
 import pytest

@@ -1,7 +1,6 @@
 """Pins of the oracle's time step (Section 2.2, Eqs. 21-26) against closed forms and the paper's trends."""
 
 import numpy as np
-import pytest
 
 from workloads import square_mesh, crisscross_mesh
 from oracle import flows, norms
