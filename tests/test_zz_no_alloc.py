@@ -6,7 +6,8 @@ right-hand side and the output buffers; its scratch is a fixed array inside the 
 The test builds the coarse operator of Eq. 23 (with its phi = 0 rows eliminated) in the
 SELL-32 layout on the host, calls the entry point twice in a row on the same scratch (two
 right-hand sides), and compares each result with the existing entry point's.  This file
-is collected last so that a run stopping at the first failure has run everything else.
+is collected after the main suites so that a run stopping at the first failure has run
+them first.
 """
 
 import numpy as np

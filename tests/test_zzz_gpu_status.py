@@ -2,7 +2,8 @@
 a right-hand side poisoned with a NaN ends the solve with CGP_ENONFINITE (and the next
 solve with a finite right-hand side converges as usual), and an iteration cap ends it with
 CGP_ENOTCONV and a finite iterate.  FP64 (register-resident grid solve) and mixed form
-(one cluster, FP32 inner) alike; pure-Neumann and Dirichlet coarse problems."""
+(one cluster, FP32 inner) alike; pure-Neumann and Dirichlet coarse problems.  Collected
+after the main suites, so a run stopping at the first failure has run them first."""
 
 import numpy as np
 import pytest
