@@ -31,6 +31,13 @@ Readings of points the paper leaves open (listed with the design notes):
 
 Solves use scipy's sparse LU (a library primitive), so each result is the
 exact discrete solution up to rounding.
+
+Pins (tests/test_oracle_step.py, tests/test_oracle_pins.py): Taylor-Green convergence;
+uniform flow as a fixed point; chi = 1 minus chi = 0 equal to the Eq. 26 term; plane
+Poiseuille flow in a channel with the traction-free outflow (a fixed point on the uniform
+mesh, second-order convergence on unstructured ones); the change of Eq. 21's right-hand
+side under P -> P + c against the outflow boundary integral; Eq. 27's lumped masses and
+corrections against hand-worked values and linear fields.
 """
 
 import numpy as np

@@ -20,7 +20,9 @@ copies of W and FP32 arithmetic; this reference takes whatever weights it is giv
 FP64, so a test passes it the bfloat16-rounded weights.
 
 Parity: backward pinned by central finite differences of the loss in
-tests/test_oracle_mlp.py; the forward by a per-vertex loop written out independently.
+tests/test_oracle_mlp.py; the forward by a per-vertex loop written out independently;
+adam_step (Kingma and Ba 2015, Algorithm 1) by its first bias-corrected step,
+-lr g / (|g| + eps), and two scalar steps worked out by hand (tests/test_oracle_pins.py).
 """
 
 import numpy as np

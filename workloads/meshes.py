@@ -199,6 +199,7 @@ def channel_cylinder_mesh(seed=0, h=0.0084, L=2.2, H=0.41, xc=0.2, yc=0.2, r=0.0
     inside the polygon removed.  Flags: inflow (x=0), walls (y=0, y=H) and
     cylinder get VEL_DIR; the outflow (x=L) gets PHI_ZERO; the two outflow
     corners get both.  The default h gives about 16k triangles (8.3k vertices).
+    r = 0 gives the plain channel (no cylinder).
     """
     from scipy.spatial import Delaunay
 
@@ -211,7 +212,7 @@ def channel_cylinder_mesh(seed=0, h=0.0084, L=2.2, H=0.41, xc=0.2, yc=0.2, r=0.0
     top = np.stack([xs, np.full_like(xs, H)], 1)
     left = np.stack([np.zeros(ny - 1), ys[1:-1]], 1)
     right = np.stack([np.full(ny - 1, L), ys[1:-1]], 1)
-    nc = max(8, int(round(2.0 * np.pi * r / h)))
+    nc = max(8, int(round(2.0 * np.pi * r / h))) if r > 0 else 0
     th = 2.0 * np.pi * np.arange(nc) / nc
     cyl = np.stack([xc + r * np.cos(th), yc + r * np.sin(th)], 1)
     fixed = np.concatenate([bottom, top, left, right, cyl])
@@ -237,8 +238,9 @@ def channel_cylinder_mesh(seed=0, h=0.0084, L=2.2, H=0.41, xc=0.2, yc=0.2, r=0.0
     d = Delaunay(pts)
     tri = d.simplices.astype(np.int64)
     cen = pts[tri].mean(axis=1)
-    keep = (cen[:, 0] - xc) ** 2 + (cen[:, 1] - yc) ** 2 > r * r
-    tri = tri[keep]
+    if nc:
+        keep = (cen[:, 0] - xc) ** 2 + (cen[:, 1] - yc) ** 2 > r * r
+        tri = tri[keep]
     a2 = _signed_area2(pts, tri)
     flip = a2 < 0
     tri[flip] = tri[flip][:, [0, 2, 1]]
@@ -262,7 +264,7 @@ def channel_cylinder_mesh(seed=0, h=0.0084, L=2.2, H=0.41, xc=0.2, yc=0.2, r=0.0
     # triangles in Morton order of their centroids
     cen = pts[tri].mean(axis=1)
     tri = tri[np.argsort(_morton_key(cen, lo, hi), kind="stable")]
-    area = L * H - 0.5 * nc * r * r * np.sin(2.0 * np.pi / nc)
+    area = L * H - (0.5 * nc * r * r * np.sin(2.0 * np.pi / nc) if nc else 0.0)
     return BaseMesh(pts.astype(np.float64), tri.astype(np.int32), tag,
                     name="channel_seed%d" % seed,
                     meta={"area": area, "h": h, "L": L, "H": H, "xc": xc, "yc": yc,
