@@ -169,49 +169,15 @@ def workload_problem(name):
 
 
 def make_params(cg, w, form, use_graph=1, tol_inner=0.0, mass_mode=0):
-    mixed = form in ("mixed", "mixed_learned", "mixed_zero", "mixed_jacobi")
-    learned = form in ("learned", "mixed_learned")
-    guess = cg.CGP_GUESS_LEARNED if learned else (cg.CGP_GUESS_ZERO if form == "mixed_zero" else cg.CGP_GUESS_PREV)
-    return cg.make_params(w.Re, w.dt, chi=w.chi, k=w.k, tol_mom=w.tol_mom, tol_poisson=w.tol_poisson,
-                          tol_mass=1e-10, max_it_mom=1000, max_it_poisson=20000, max_it_mass=1000,
-                          precision=cg.CGP_MIXED if mixed else cg.CGP_FP64,
-                          guess=guess, bc_kind=w.bc,
-                          bc_param=w.bc_param, use_graph=use_graph, tol_inner=tol_inner,
-                          precond=cg.CGP_PRECOND_JACOBI if form == "mixed_jacobi" else cg.CGP_PRECOND_AUTO,
-                          mass_mode=mass_mode)
+    from paper_1812_00185_gb300.forms import workload_params
+    return workload_params(w, form, use_graph=use_graph, tol_inner=tol_inner, mass_mode=mass_mode)
 
 
 def train_guess(cg, w, args):
     """Train the learned-guess network on a held-out seed of the same workload (the timed
     run uses seed w.base_n).  Returns (FP32 parameter vector, info dict)."""
-    import torch
-    from paper_1812_00185_gb300.learned import PairStore, train, init_params
-    from workloads import channel_cylinder_mesh, square_mesh
-    t0 = time.time()
-    if w.base == "channel":
-        base = channel_cylinder_mesh(seed=w.base_n + 1, h=w.extra.get("h", 0.0084))
-    else:
-        base = w.base_mesh()
-    mesh = cg.Mesh(base.xy, base.tri, base.tag, w.n_levels)
-    rec = cg.Solver(mesh, make_params(cg, w, "fp64"))
-    store = PairStore(rec.nc, args.train_pairs)
-    store.record(rec, args.train_pairs)
-    rec.close()
-    torch.cuda.synchronize()
-    t_rec = time.time() - t0
-    net = cg.cgp_mlp_create(mesh.handle, w.n_levels - w.k, 8)
-    cg.cgp_mlp_set_params(net, init_params(0))
-    t1 = time.time()
-    hist = train(net, store, args.train_iters, batch=8, lr=2e-3, log_every=max(1, args.train_iters // 4))
-    torch.cuda.synchronize()
-    t_train = time.time() - t1
-    p = cg.cgp_mlp_get_params(net)
-    cg.cgp_mlp_destroy(net)
-    del store
-    mesh.close()
-    return p, {"pairs": args.train_pairs, "iters": args.train_iters, "record_s": round(t_rec, 2),
-               "train_s": round(t_train, 2), "loss": [(int(i), round(float(l), 5)) for i, l in hist],
-               "train_mesh_seed": w.base_n + 1}
+    from paper_1812_00185_gb300.forms import train_guess as train
+    return train(w, pairs=args.train_pairs, iters=args.train_iters)
 
 
 # algorithmic bytes per launch of each kernel kind (int32 indices, FP64 values);
@@ -309,7 +275,7 @@ def run_gpu(args, rank, world):
     if not args.quick:
         # the coarse initial guesses side by side: previous increment (mixed), zero, learned;
         # and the on-chip solve with Jacobi alone instead of Jacobi + the subdomain correction
-        for other in ("fp64", "mixed", "mixed_zero", "mixed_jacobi"):
+        for other in ("fp64", "mixed", "mixed_zero", "mixed_jacobi", "mixed_proj"):
             if other != head_form:
                 s2, res = run_form(other, args.steps, args.warmup)
                 forms[other] = {k: res[k] for k in keys}
@@ -390,6 +356,22 @@ def run_gpu(args, rank, world):
                 "peak_source": "derived: 128 B/clock/SM x %d SMs x %.0f MHz (median SM clock, timed region)"
                                % (cl, sm_mhz)}
 
+    # the CPU baseline and the parity of the headline form: the FP64 oracle advances a bounded
+    # number of steps from the state the timed region started from, and the GPU solver the
+    # same steps from the same state; relative L2 of the fields after them
+    cpu_base, parity = None, None
+    if rank == 0 and world == 1 and not args.quick:
+        cpu_base, n_o, _, o = cpu_oracle_rate(w, base, args.cpu_budget, state=head["start"])
+        U0, Up0, P0, tt0, phic0 = head["start"]
+        s.set_fields(U0, Up0, P0, tt0)
+        cg.cgp_set_vector(s.handle, cg.CGP_VEC_PHI_C, phic0)
+        s.step(n_o)
+        Ug, Pg, tg, stg, rcg = s.fields()
+        rel = lambda a, b: float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+        parity = {"form": head_form, "oracle_steps": n_o, "from_t": round(float(tt0), 6),
+                  "rel_l2_U": rel(Ug, o.U), "rel_l2_P": rel(Pg, o.P),
+                  "bound": 1e-4 if "mixed" in head_form else 1e-6, "status": int(rcg)}
+
     # PCG iteration bandwidth on a synthetic Poisson problem far larger than L2
     pcg = None
     if not args.quick and rank == 0:
@@ -413,6 +395,17 @@ def run_gpu(args, rank, world):
         "forms": forms, "kernels": kern, "setup_s": {"mesh": round(t_mesh, 3), "assemble": round(head["assemble_s"], 3)},
         "pcg_hbm": pcg, "batch": batch,
     }
+    # the metric's comparison, decomposed: plain FP64 (Jacobi coarse PCG), then FP32 inner /
+    # FP64 outer with Jacobi, + the subdomain coarse correction, + the projection guess,
+    # + the learned network (the headline form)
+    sps = {k: v["steps_per_s"] for k, v in forms.items()}
+    if "fp64" in sps:
+        out["vs_fp64"] = {k: round(sps[k], 1) for k in ("fp64", "mixed_jacobi", "mixed", "mixed_zero", "mixed_proj",
+                                                        "mixed_learned") if k in sps}
+        out["vs_fp64"]["headline_over_fp64"] = round(sps[head_form] / sps["fp64"], 3)
+    if cpu_base is not None:
+        out["parity"] = parity
+        out["cpu_baseline"] = cpu_base
     if learned:
         out["learned"] = learned["info"]
         cg.cgp_mlp_destroy(learned["net"])
@@ -541,11 +534,95 @@ def batch_throughput(cg, torch, n_inst, steps, warmup):
     return out
 
 
-def cpu_oracle_rate(w, base, budget_s):
-    """Steps/s of the FP64 oracle (setup excluded), bounded to about budget_s seconds."""
+def _fe_errors(cg, mesh, s, level, U, P, Ue, Pe):
+    """FE L2 (sqrt(e^T M e), M the library's P1 mass matrix of the fine level) and nodal max
+    errors of U and of P (P with its M-weighted mean removed, as in the paper's tables)."""
+    import scipy.sparse as sp
+    lev = mesh.level(level)
+    M = sp.csr_matrix((s.matrix(cg.CGP_MAT_M), lev["col"], lev["rowptr"]))
+    m = np.asarray(M.sum(axis=1)).ravel()
+    eU = U - Ue
+    eP = (P - m @ P / m.sum()) - (Pe - m @ Pe / m.sum())
+    l2U = float(np.sqrt(sum(eU[:, d] @ (M @ eU[:, d]) for d in range(2))))
+    return {"l2_u": l2U, "linf_u": float(np.sqrt((eU ** 2).sum(1)).max()),
+            "l2_p": float(np.sqrt(eP @ (M @ eP))), "linf_p": float(np.abs(eP).max())}
+
+
+def manufactured_run(cg, torch, base, n_levels, k, Re, dt, chi, bc, steps, form="fp64", mass_mode=0, tol=1e-10):
+    """Advance a manufactured problem (closed-form solution) `steps` steps on the GPU;
+    returns device ms per step and the errors at the final time."""
+    mesh = cg.Mesh(base.xy, base.tri, base.tag, n_levels)
+    prm = cg.make_params(Re, dt, chi=chi, k=k, tol_mom=tol, tol_poisson=tol, tol_mass=min(tol, 1e-10) * 1e-2,
+                         max_it_mom=2000, max_it_poisson=50000, max_it_mass=2000,
+                         precision=cg.CGP_MIXED if form.startswith("mixed") else cg.CGP_FP64,
+                         guess=cg.CGP_GUESS_PROJ if form.endswith("proj") else cg.CGP_GUESS_PREV,
+                         bc_kind=bc, mass_mode=mass_mode)
+    s = cg.Solver(mesh, prm)
+    st = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(st)
+    s.step(steps)
+    e1.record(st)
+    torch.cuda.synchronize()
+    U, P, t, stats, rc = s.fields()
+    Ue, Pe = cg.cgp_exact_fields(s.handle, t)
+    out = {"ms_per_step": round(e0.elapsed_time(e1) / steps, 4), "t": round(t, 6), "status": int(rc),
+           "fine_triangles": mesh.info(n_levels)[1], "poisson_triangles": mesh.info(n_levels - k)[1]}
+    out.update({key: float("%.4e" % v) for key, v in _fe_errors(cg, mesh, s, n_levels, U, P, Ue, Pe).items()})
+    s.close()
+    mesh.close()
+    return out
+
+
+def e1_grid(cg, torch, steps=800, form="fp64"):
+    """The paper's first experiment (Section 3.1, Tables 1-4): the decaying Taylor-Green vortex
+    (Eqs. 28-30) at Re = 10, dt = 0.00125, to t = 1 (800 steps), on meshes of 1024 * 4^j
+    triangles (four per square), the pressure increment on 1024 * 4^(j-k) triangles, standard
+    (chi = 0) and rotational (chi = 1) forms.  Errors at t = 1 and the device time of each run;
+    speedup = time(k = 0) / time(k) on the same fine mesh, as Table 4 defines it."""
+    from workloads import crisscross_mesh
+    base = crisscross_mesh(16)
+    rows = []
+    for j in range(4):
+        for chi in (0, 1):
+            t0 = None
+            for k in range(j + 1):
+                r = manufactured_run(cg, torch, base, j, k, 10.0, 0.00125, chi, cg.CGP_BC_TG, steps, form)
+                t0 = r["ms_per_step"] if k == 0 else t0
+                r.update({"M:N": "%d:%d" % (r["fine_triangles"], r["poisson_triangles"]), "chi": chi, "k": k,
+                          "speedup": round(t0 / r["ms_per_step"], 3)})
+                rows.append(r)
+    return rows
+
+
+def lumped_accuracy(cg, torch, steps=200):
+    """Eq. 27 against Eq. 20: the rotational update with the lumped mass matrix (and the
+    lumped velocity correction) against the consistent one, on the periodic-forced
+    Taylor-Green vortex of the 512^2 workload (Re = 100, dt = 0.002, to t = 0.4), pressure
+    1-3 levels coarser; errors against the closed form and device time per step."""
+    from workloads import WORKLOADS
+    rows = []
+    for k in (1, 2, 3):
+        w = WORKLOADS["tgp512_k2"]
+        base = w.base_mesh()
+        for form in ("fp64", "mixed"):
+            for mass in (0, 1):
+                r = manufactured_run(cg, torch, base, w.n_levels, k, w.Re, w.dt, 1, w.bc, steps, form, mass, tol=1e-8)
+                r.update({"k": k, "form": form, "mass": "lumped (Eq. 27)" if mass else "consistent (Eq. 20)"})
+                rows.append(r)
+    return rows
+
+
+def cpu_oracle_rate(w, base, budget_s, state=None):
+    """Steps/s of the FP64 oracle (setup excluded), bounded to about budget_s seconds; from
+    rest, or from `state` = (U, U_prev, P, t) when given.  Returns (baseline dict, steps,
+    seconds, the oracle after its steps)."""
     from oracle.cgp import CGPOracle
     t0 = time.time()
     o = CGPOracle(base, w.n_levels, w.k, w.Re, w.dt, w.chi, w.bc, bc_param=w.bc_param)
+    if state is not None:
+        o.set_state(*state[:4])
     setup = time.time() - t0
     r0 = resource.getrusage(resource.RUSAGE_SELF)
     t0 = time.time()
@@ -558,9 +635,10 @@ def cpu_oracle_rate(w, base, budget_s):
     wall = time.time() - t0
     r1 = resource.getrusage(resource.RUSAGE_SELF)
     cpu = (r1.ru_utime - r0.ru_utime) + (r1.ru_stime - r0.ru_stime)
+    where = "from rest" if state is None else "from the GPU state at t = %.4g" % state[3]
     return {"value": round(n / wall, 5), "unit": "steps/s", "cores": max(1, int(round(cpu / wall))),
-            "kind": "oracle", "sample": "%d oracle time steps of %s (%d fine vertices) after %.1f s of setup"
-                                        % (n, w.name, o.fine.n_vert, setup)}, n, wall
+            "kind": "oracle", "sample": "%d oracle time steps of %s (%d fine vertices, %s) after %.1f s of setup"
+                                        % (n, w.name, o.fine.n_vert, where, setup)}, n, wall, o
 
 
 def aggregate_ranks(out, world, device):
@@ -586,7 +664,8 @@ def main():
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--workload", default="channel1m_k2")
     ap.add_argument("--form", default="mixed_learned",
-                    choices=["fp64", "mixed", "learned", "mixed_learned", "mixed_zero", "mixed_jacobi"])
+                    choices=["fp64", "mixed", "learned", "mixed_learned", "mixed_zero", "mixed_jacobi", "mixed_proj",
+                             "fp64_proj"])
     ap.add_argument("--batch", type=int, default=256, help="instances of the batched form (0: skip)")
     ap.add_argument("--batch-steps", type=int, default=10)
     ap.add_argument("--train-pairs", type=int, default=150)
@@ -606,6 +685,10 @@ def main():
                          "level (--steps forward passes)")
     ap.add_argument("--pcg-only", action="store_true",
                     help="print only the PCG bandwidth sweep (one JSON line per problem size)")
+    ap.add_argument("--e1", action="store_true",
+                    help="print only the paper's Taylor-Green study (Tables 1-4) run on the GPU, one JSON line")
+    ap.add_argument("--accuracy", action="store_true",
+                    help="print only the Eq. 27 (lumped) against Eq. 20 (consistent) accuracy comparison")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "gpu":
         args.warmup = 3
@@ -616,7 +699,7 @@ def main():
         if rank != 0:
             return 0
         w, base = workload_problem(args.workload)
-        res, n, wall = cpu_oracle_rate(w, base, min(120.0, 20.0 * max(1, args.steps) / 10.0))
+        res, n, wall, _ = cpu_oracle_rate(w, base, min(120.0, 20.0 * max(1, args.steps) / 10.0))
         print(json.dumps({
             "metric": METRIC, "value": res["value"], "unit": "steps/s", "n_gpus": args.gpus, "steps": n,
             "warmup": 0, "ms_per_step": round(1000 * wall / n, 3), "higher_is_better": True, "scaling": "weak",
@@ -634,6 +717,20 @@ def main():
         from paper_1812_00185_gb300 import binding as cg
         w, _ = workload_problem(args.workload)
         print(json.dumps(mlp_forward_time(cg, torch, w, args.steps)), flush=True)
+        return 0
+    if args.e1 or args.accuracy:
+        if rank != 0:
+            return 0
+        import torch
+        from paper_1812_00185_gb300 import binding as cg
+        if args.e1:
+            print(json.dumps({"metric": "Taylor-Green errors and CGP speedup (paper Section 3.1)", "form": args.form
+                              if args.form in ("fp64", "mixed") else "fp64",
+                              "rows": e1_grid(cg, torch, form=args.form if args.form in ("fp64", "mixed") else "fp64")}),
+                  flush=True)
+        if args.accuracy:
+            print(json.dumps({"metric": "Eq. 27 vs Eq. 20 accuracy (periodic Taylor-Green 512^2)",
+                              "rows": lumped_accuracy(cg, torch)}), flush=True)
         return 0
     if args.pcg_only:
         if rank != 0:
@@ -654,8 +751,6 @@ def main():
     if world > 1:
         aggregate_ranks(out, world, "cuda")
     if rank == 0:
-        if world == 1 and not args.quick:
-            out["cpu_baseline"], _, _ = cpu_oracle_rate(w, base, args.cpu_budget)
         print(json.dumps(out))
     if world > 1:
         import torch.distributed as dist

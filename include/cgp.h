@@ -56,15 +56,28 @@ enum {
     CGP_BC_CHANNEL = 1,      /* u=(4 Umax y(H-y)/H^2, 0) on x=0 (Umax=bc_param[0], H=bc_param[1]), u=0 elsewhere on VEL_DIR */
     CGP_BC_TG = 2,           /* Taylor-Green vortex, paper Eqs. 28-30 */
     CGP_BC_TG_PERIODIC = 3,  /* Taylor-Green with amplitude cos(2 pi t) and the body force that makes it exact */
-    CGP_BC_USER = 4          /* caller's data: the Dirichlet velocity of every VEL_DIR vertex and the body force
+    CGP_BC_USER = 4,         /* caller's data: the Dirichlet velocity of every VEL_DIR vertex and the body force
                                 f of Eq. 21 at t^{n+1}, given by cgp_set_dirichlet / cgp_set_forcing before
                                 each step (both zero until set; they keep their values between steps) */
+    CGP_BC_JOBELIN_OPEN = 5, /* Section 3.2 vortex, u = sin x sin(y+t), v = cos x cos(y+t), p = cos x sin(y+t), with
+                                its body force: velocity data on the VEL_DIR vertices, and on the PHI_ZERO
+                                vertices (the traction boundary, the y-axis x = 0 of [0,1]^2) the traction of
+                                Eq. 4 and the pressure from the closed form: Eq. 21 gains
+                                dt * int_{Gamma_N} t psi_i ds (t linear on each boundary edge), Eq. 23 takes
+                                phi = p(t^{n+1}) - P^n there (restrict_mode INJECT only) */
+    CGP_BC_JOBELIN_DISK = 6  /* Section 3.3 vortex, u = sin(x+t) sin(y+t), v = cos(x+t) cos(y+t), p = cos(x-y+t),
+                                with its body force; velocity data on the VEL_DIR vertices (the whole
+                                boundary of the disk) */
 };
 enum { CGP_FP64 = 0, CGP_MIXED = 1 };                   /* precision of the coarse Poisson solve */
-/* initial guess of the coarse Poisson solve: zero, the previous step's increment, or the
- * learned network's prediction (falls back to the previous increment whenever that one has
- * the smaller FP64 residual, and until cgp_guess_set provides weights) */
-enum { CGP_GUESS_ZERO = 0, CGP_GUESS_PREV = 1, CGP_GUESS_LEARNED = 2 };
+/* initial guess of the coarse Poisson solve (Eq. 23; the paper starts from nothing in
+ * particular): zero, the previous step's increment, the projection onto the last 8
+ * increments (PROJ: the combination of them that minimises the K_c-norm of the error,
+ * Fischer 1998), or LEARNED: the projection refined by the network's prediction (the
+ * one-launch solve starts from the K_c-norm-optimal combination of the projection and the
+ * prediction, so never worse than the projection; until cgp_guess_set provides weights, the
+ * projection alone) */
+enum { CGP_GUESS_ZERO = 0, CGP_GUESS_PREV = 1, CGP_GUESS_LEARNED = 2, CGP_GUESS_PROJ = 3 };
 enum { CGP_MASS_CONSISTENT = 0, CGP_MASS_LUMPED = 1 };    /* mass matrix of Eqs. 25-26 (lumped = Eq. 27) */
 enum { CGP_HOST = 0, CGP_DEVICE = 1 };
 
@@ -222,6 +235,20 @@ int cgp_coarse_info(const cgp_solver* s, int32_t* kind, int32_t* ctas, int32_t* 
 /* Subdomains of the coarse solve's coarse correction (0: Jacobi alone), through *nsub.
  * CGP_EINVAL before cgp_assemble. */
 int cgp_coarse_subdomains(const cgp_solver* s, int32_t* nsub);
+/* Closed-form fields of the built-in manufactured kinds (CGP_BC_TG: Eqs. 28-30;
+ * CGP_BC_TG_PERIODIC) at time t on every fine vertex: U (2 N_f, interleaved) and P (N_f);
+ * either may be NULL.  For measuring errors; CGP_EINVAL for kinds without a closed form.
+ * Host (synchronises) or device (asynchronous on stream) arrays. */
+int cgp_exact_fields(cgp_solver* s, double t, double* U, double* P, int32_t where, cgp_stream_t stream);
+/* Test hook of the failure path (the paper has no counterpart; off unless a caller sets
+ * it): with on = 1, every bounded device wait inside the one-launch coarse solves (the
+ * software grid barrier of the PERSISTENT kinds, the mbarrier waits of the on-chip
+ * cluster solve) also waits for one signal that nothing sends, under a limit of
+ * milliseconds instead of seconds, so the solve gives up and returns CGP_ETIMEOUT while
+ * the context stays usable.  Applies to launches made after the call (cgp_poisson_solve,
+ * eager steps; a step graph captured before keeps the earlier setting).  on = 0 restores
+ * normal waits.  CGP_EINVAL for a null solver. */
+int cgp_set_wait_test(cgp_solver* s, int32_t on);
 
 /* Eq. 23 alone: solve K_c phi = rhs (N_c values; phi=0 rows and the pure-Neumann
  * projection/mean fix as in a step) with the configured precision and tolerance.
@@ -251,7 +278,9 @@ enum {
     /* p updates of the FP64 PCG loops (three kernels per iteration) */
     CGP_PROF_POIS_PUPD, CGP_PROF_CORR_PUPD, CGP_PROF_MASS_PUPD,
     /* CGP_MIXED: FP32 Chebyshev steps of the Eq. 26 and Eq. 25 mass-matrix solves */
-    CGP_PROF_CHEB_MASS, CGP_PROF_CHEB_CORR, CGP_PROF_COUNT
+    CGP_PROF_CHEB_MASS, CGP_PROF_CHEB_CORR,
+    /* projection guess of the coarse solve (CGP_GUESS_PROJ, CGP_GUESS_LEARNED) */
+    CGP_PROF_PROJ, CGP_PROF_COUNT
 };
 int cgp_profile_step(cgp_solver* s, cgp_stream_t stream, int32_t n_ids, int32_t* counts, double* total_ms);
 
@@ -309,19 +338,24 @@ int cgp_mlp_train_step(cgp_mlp* m, const double* r, const double* q, const doubl
 int cgp_guess_set(cgp_solver* s, const cgp_mlp* m, cgp_stream_t stream);
 /* Training data for the learned guess, generated by the solver itself: advances n_steps
  * steps (as cgp_step) and stores, for step k, row k (N_c values) of rhs = the right-hand
- * side of Eq. 23, prev = the increment Phi_c before the step (the network's second input)
- * and target = the increment Phi_c the coarse solve produced.  Arrays of n_steps * N_c
+ * side of Eq. 23, prev = the network's second input (the projection guess of the step for
+ * a solver assembled with CGP_GUESS_PROJ or CGP_GUESS_LEARNED, else the increment Phi_c
+ * before the step) and target = the increment Phi_c the coarse solve produced.  Arrays of n_steps * N_c
  * doubles, host or device (where); host: synchronises, device: asynchronous on stream. */
 int cgp_record_pairs(cgp_solver* s, int32_t n_steps, double* rhs, double* prev, double* target, int32_t where,
                      cgp_stream_t stream);
+/* Copy the weights and the Adam state (moments and step count) of src into dst, on the
+ * device, asynchronously on stream: one network trained on several meshes (one cgp_mlp per
+ * mesh level, the state handed from one to the next between training steps). */
+int cgp_mlp_copy_state(cgp_mlp* dst, const cgp_mlp* src, cgp_stream_t stream);
 void cgp_mlp_destroy(cgp_mlp* m);
 
 /* ---- allocation-free solve (the paper has no counterpart) ----
  * For callers that cannot call cudaMalloc (a host program that owns every device
  * allocation, a fixed-memory real-time loop, a plug-in handed only the buffers it may
  * touch): solves A x = b for a symmetric positive definite A with the library's Jacobi-
- * preconditioned, one-launch PCG (the coarse-solve kernel of Eq. 23, Chronopoulos-Gear
- * recurrence, true-residual stopping test ||b - A x|| <= tol ||b||) and allocates nothing:
+ * preconditioned, one-launch PCG (Chronopoulos-Gear recurrence on a cooperative grid,
+ * true-residual stopping test ||b - A x|| <= tol ||b||) and allocates nothing:
  * every scratch word lives in one fixed file-scope device array of about 4.3 MB that each
  * device loading the library keeps until the process exits.
  *  - A in SELL-32 form (see cgp_mesh_get_level: slice s = rows 32s..32s+31, entries of a
@@ -332,7 +366,9 @@ void cgp_mlp_destroy(cgp_mlp* m);
  *    of the solve: iterations, status (CGP_OK, CGP_ENOTCONV, CGP_EBREAKDOWN, ...).
  *  - Asynchronous on `stream`.  The first call on a device looks up the array's device
  *    address and the launch size (make it before any stream capture); later calls only
- *    enqueue a memset of the barrier counter, the solve and a status copy.
+ *    enqueue a memset of the barrier counter, the solve and a status copy.  The address is
+ *    kept per device and context: after cudaDeviceReset the next call looks it up again
+ *    (that call, too, belongs before any capture).
  *  - Every call shares the one array: calls whose solves may overlap on the GPU (different
  *    streams without ordering, or other host threads) race and must not be made. */
 int cgp_pcg_sell_noalloc(int32_t n, int32_t nslices, const int32_t* sell_ptr, const int32_t* sell_col,

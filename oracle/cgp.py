@@ -28,6 +28,13 @@ Readings of points the paper leaves open (listed with the design notes):
   sum_i m_i Phi_i = 0 with m the lumped coarse mass (row sums of M_c).
 * The mean of nothing else is touched: P carries whatever constant the
   Phi updates give.
+* Traction data on the natural boundary Gamma_N (Eq. 11; nonzero only for the open-boundary
+  vortex of Section 3.2): Eq. 21's right-hand side gains dt * int_{Gamma_N} t psi_i ds, with
+  t interpolated linearly between the vertices of each boundary edge (the boundary mass
+  matrix l/6 [[2, 1], [1, 2]] of the edge times the nodal values).  Where the problem
+  prescribes the pressure on Gamma_N, Eq. 14 is read with that data: phi = p(t^{n+1}) - p^n
+  at the coarse Gamma_N vertices (lifted into the right-hand side of Eq. 23), so that the
+  pressure follows the prescribed values; otherwise phi = 0 there.
 
 Solves use scipy's sparse LU (a library primitive), so each result is the
 exact discrete solution up to rounding.
@@ -45,7 +52,7 @@ import scipy.sparse as sp
 import scipy.sparse.linalg as spla
 
 from . import fem, flows
-from .mesh import build_hierarchy
+from .mesh import build_hierarchy, unique_edges
 
 VEL_DIR, PHI_ZERO = 1, 2
 
@@ -88,6 +95,7 @@ class CGPOracle:
         self.phi0_mask = (c.tag & PHI_ZERO) != 0
         self.pure_neumann = not self.phi0_mask.any()
         M = self.ops_f["M"]
+        self.BN = self._natural_boundary_mass(f, (f.tag & PHI_ZERO) != 0)
         self.mlump_f = np.asarray(M.sum(axis=1)).ravel()
         self.mlump_c = np.asarray(self.ops_c["M"].sum(axis=1)).ravel()
         # factorisations of the constant systems
@@ -105,6 +113,19 @@ class CGPOracle:
         self.t = 0.0
         self.n = 0
 
+    @staticmethod
+    def _natural_boundary_mass(lev, on_n):
+        """int psi_i psi_j ds over the boundary edges (edges of one triangle) whose ends both
+        lie on Gamma_N: l/6 (1 + delta_ij) per edge."""
+        ends, count, _ = unique_edges(lev.tri)
+        e = ends[(count == 1) & on_n[ends[:, 0]] & on_n[ends[:, 1]]]
+        ell = np.hypot(*(lev.xy[e[:, 1]] - lev.xy[e[:, 0]]).T)
+        rows = np.concatenate([e[:, 0], e[:, 1], e[:, 0], e[:, 1]])
+        cols = np.concatenate([e[:, 0], e[:, 1], e[:, 1], e[:, 0]])
+        vals = np.concatenate([ell / 3.0, ell / 3.0, ell / 6.0, ell / 6.0])
+        n = lev.xy.shape[0]
+        return sp.csr_matrix((vals, (rows, cols)), shape=(n, n))
+
     # ---- individual steps (each follows one equation) ----
     def momentum(self, U, Uprev, P, t_new):
         """Eq. 21: the intermediate velocity U~ (n_f, 2)."""
@@ -115,18 +136,21 @@ class CGPOracle:
         A = 1.5 * M + dt * N + (dt / Re) * K
         F = flows.body_force(self.bc, f.xy, t_new, Re, self.bc_param)
         hist = 2.0 * U - 0.5 * Uprev
-        bx = dt * (Cx.T @ P) + M @ (dt * F[:, 0] + hist[:, 0])
-        by = dt * (Cy.T @ P) + M @ (dt * F[:, 1] + hist[:, 1])
+        T = flows.traction(self.bc, f.xy, t_new, Re, self.bc_param)
+        bx = dt * (Cx.T @ P) + M @ (dt * F[:, 0] + hist[:, 0]) + dt * (self.BN @ T[:, 0])
+        by = dt * (Cy.T @ P) + M @ (dt * F[:, 1] + hist[:, 1]) + dt * (self.BN @ T[:, 1])
         uD = flows.dirichlet_value(self.bc, f.xy, t_new, Re, self.bc_param)
         d = self.dir_mask
         bx[d], by[d] = uD[d, 0], uD[d, 1]
         lu = spla.splu(_dirichlet_replace(A.tocsr(), d))
         return np.stack([lu.solve(bx), lu.solve(by)], 1)
 
-    def coarse_rhs(self, Ut):
+    def coarse_rhs(self, Ut, P=None, t_new=None):
         """Eqs. 22-23: inject U~ and form -3/(2 dt) (Cx_c u~_c + Cy_c v~_c).  restrict_mode
         "pt" (a variant, not the paper's): -3/(2 dt) P^T (Cx_f u~ + Cy_f v~), the fine
-        divergence restricted by the transpose of the prolongation."""
+        divergence restricted by the transpose of the prolongation.  With a prescribed
+        pressure on Gamma_N (P = P^n and t_new given), the phi = 0 rows carry g = p(t_new) - P^n
+        and the other rows have K_c[:, Gamma_N] g moved to the right-hand side."""
         if self.restrict_mode == "pt":
             g = self.ops_f["Cx"] @ Ut[:, 0] + self.ops_f["Cy"] @ Ut[:, 1]
             r = -1.5 / self.dt * fem.restrict_t(g, self.levels, self.lf, self.lc)
@@ -134,6 +158,11 @@ class CGPOracle:
             Uc = fem.inject(Ut, self.coarse.n_vert)
             r = -1.5 / self.dt * (self.ops_c["Cx"] @ Uc[:, 0] + self.ops_c["Cy"] @ Uc[:, 1])
         r[self.phi0_mask] = 0.0
+        pn = None if t_new is None else flows.natural_pressure(self.bc, self.coarse.xy, t_new, self.Re, self.bc_param)
+        if pn is not None and self.phi0_mask.any():
+            g = np.where(self.phi0_mask, pn - P[:self.coarse.n_vert], 0.0)
+            r = r - self.ops_c["K"] @ g
+            r[self.phi0_mask] = g[self.phi0_mask]
         if self.pure_neumann:
             r = r - r.sum() / r.size
         return r
@@ -175,7 +204,7 @@ class CGPOracle:
     def step(self):
         t_new = self.t + self.dt
         Ut = self.momentum(self.U, self.Uprev, self.P, t_new)
-        r = self.coarse_rhs(Ut)
+        r = self.coarse_rhs(Ut, self.P, t_new)
         phic = self.poisson(r)
         phif = self.prolong(phic)
         U = self.correct(Ut, phif)

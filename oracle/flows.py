@@ -14,6 +14,18 @@ Problem statements used by the workloads:
   u = g U0(x), p = g^2 P0(x) with U0, P0 the t = 0 Taylor-Green fields, and the
   body force f = (g' + 8 pi^2 g / Re) U0 that makes it an exact solution
   ((U0 . grad) U0 + grad P0 = 0 and -Lap U0 = 8 pi^2 U0).
+* BC_JOBELIN_OPEN (5): the vortex of Section 3.2 on [0,1]^2: u = sin x sin(y+t),
+  v = cos x cos(y+t), p = cos x sin(y+t), with the body force that makes it a solution of
+  Eq. 1; velocity Dirichlet data on x = 1, y = 0, y = 1, the traction of Eq. 4 on the
+  y-axis x = 0 (Gamma_N, outward normal (-1, 0)) taken from the closed form (the paper
+  calls it homogeneous, but the closed form has -p n + grad u . n / Re = ((1 - 1/Re)
+  sin(y+t), 0) there), and the pressure on Gamma_N from the closed form.
+* BC_JOBELIN_DISK (6): the vortex of Section 3.3 on the disk x^2 + y^2 < 1/4:
+  u = sin(x+t) sin(y+t), v = cos(x+t) cos(y+t), p = cos(x-y+t), velocity Dirichlet data on
+  the whole boundary.
+
+The body forces are f = u_t + (u . grad) u - Lap u / Re + grad p written out from the
+derivatives of the closed forms (both fields are divergence free and Lap u = -2 u).
 
 Start of BDF2 (Eq. 5 needs u^{n-1}): where a closed form exists u^{-1} is the
 exact field at t = -dt, otherwise u^{-1} = u^0.  p^0 is the exact pressure at
@@ -23,6 +35,26 @@ t = 0, or 0.
 import numpy as np
 
 BC_CAVITY, BC_CHANNEL, BC_TG, BC_TG_PERIODIC = 0, 1, 2, 3
+BC_JOBELIN_OPEN, BC_JOBELIN_DISK = 5, 6
+
+
+def _jobelin(kind, x, y, t):
+    """(u, v, p) and the first derivatives the body force and the traction need:
+    returns dict with u, v, p, u_t, v_t, u_x, u_y, v_x, v_y, p_x, p_y."""
+    if kind == BC_JOBELIN_OPEN:
+        a, b = x, y + t
+        sa, ca, sb, cb = np.sin(a), np.cos(a), np.sin(b), np.cos(b)
+        d = {"u": sa * sb, "v": ca * cb, "p": ca * sb,
+             "u_t": sa * cb, "v_t": -ca * sb,
+             "p_x": -sa * sb, "p_y": ca * cb}
+    else:
+        a, b, c = x + t, y + t, x - y + t
+        sa, ca, sb, cb = np.sin(a), np.cos(a), np.sin(b), np.cos(b)
+        d = {"u": sa * sb, "v": ca * cb, "p": np.cos(c),
+             "u_t": ca * sb + sa * cb, "v_t": -sa * cb - ca * sb,
+             "p_x": -np.sin(c), "p_y": np.sin(c)}
+    d.update({"u_x": ca * sb, "u_y": sa * cb, "v_x": -sa * cb, "v_y": -ca * sb})
+    return d
 
 
 def _tg_shape(x, y):
@@ -43,6 +75,9 @@ def exact(kind, xy, t, Re, bc_param=(1.0, 0.0, 0.0, 0.0)):
         u, v, p = _tg_shape(x, y)
         g = np.cos(2 * np.pi * t)
         return np.stack([u * g, v * g], 1), p * g * g
+    if kind in (BC_JOBELIN_OPEN, BC_JOBELIN_DISK):
+        d = _jobelin(kind, x, y, t)
+        return np.stack([d["u"], d["v"]], 1), d["p"]
     return None
 
 
@@ -70,7 +105,32 @@ def body_force(kind, xy, t, Re, bc_param=(1.0, 0.0, 0.0, 0.0)):
         gp = -2 * np.pi * np.sin(2 * np.pi * t)
         c = gp + 8 * np.pi ** 2 * g / Re
         return np.stack([c * u, c * v], 1)
+    if kind in (BC_JOBELIN_OPEN, BC_JOBELIN_DISK):
+        d = _jobelin(kind, xy[:, 0], xy[:, 1], t)
+        # Lap u = -2 u, Lap v = -2 v for both vortices
+        fx = d["u_t"] + d["u"] * d["u_x"] + d["v"] * d["u_y"] + 2.0 * d["u"] / Re + d["p_x"]
+        fy = d["v_t"] + d["u"] * d["v_x"] + d["v"] * d["v_y"] + 2.0 * d["v"] / Re + d["p_y"]
+        return np.stack([fx, fy], 1)
     return np.zeros((xy.shape[0], 2))
+
+
+def traction(kind, xy, t, Re, bc_param=(1.0, 0.0, 0.0, 0.0)):
+    """Nodal traction t = -p n + (grad u) n / Re of Eq. 4 on the natural boundary (zero for
+    every kind but BC_JOBELIN_OPEN, whose Gamma_N is x = 0 with outward normal (-1, 0))."""
+    out = np.zeros((xy.shape[0], 2))
+    if kind == BC_JOBELIN_OPEN:
+        d = _jobelin(kind, xy[:, 0], xy[:, 1], t)
+        out[:, 0] = d["p"] - d["u_x"] / Re
+        out[:, 1] = -d["v_x"] / Re
+    return out
+
+
+def natural_pressure(kind, xy, t, Re, bc_param=(1.0, 0.0, 0.0, 0.0)):
+    """Pressure prescribed on the natural boundary at time t, or None (then it stays 0 there,
+    as on the channel's outflow)."""
+    if kind == BC_JOBELIN_OPEN:
+        return exact(kind, xy, t, Re, bc_param)[1]
+    return None
 
 
 def initial_state(kind, xy, dirichlet, dt, Re, bc_param=(1.0, 0.0, 0.0, 0.0)):

@@ -18,10 +18,11 @@ CGP_OK, CGP_EINVAL, CGP_ENOTCONV, CGP_EBREAKDOWN, CGP_ENONFINITE, CGP_ETIMEOUT, 
     0, -1, -2, -3, -4, -5, -6, -7
 CGP_VEL_DIR, CGP_PHI_ZERO = 1, 2
 CGP_BC_CAVITY, CGP_BC_CHANNEL, CGP_BC_TG, CGP_BC_TG_PERIODIC, CGP_BC_USER = 0, 1, 2, 3, 4
+CGP_BC_JOBELIN_OPEN, CGP_BC_JOBELIN_DISK = 5, 6
 CGP_RESTRICT_INJECT, CGP_RESTRICT_PT = 0, 1
 CGP_PRECOND_AUTO, CGP_PRECOND_JACOBI, CGP_PRECOND_COARSE = 0, 1, 2
 CGP_FP64, CGP_MIXED = 0, 1
-CGP_GUESS_ZERO, CGP_GUESS_PREV, CGP_GUESS_LEARNED = 0, 1, 2
+CGP_GUESS_ZERO, CGP_GUESS_PREV, CGP_GUESS_LEARNED, CGP_GUESS_PROJ = 0, 1, 2, 3
 CGP_MASS_CONSISTENT, CGP_MASS_LUMPED = 0, 1
 (CGP_COARSE_AUTO, CGP_COARSE_KERNELS, CGP_COARSE_CLUSTER, CGP_COARSE_PERSISTENT, CGP_COARSE_PERSISTENT_MEM,
  CGP_COARSE_ONCHIP) = 0, 1, 2, 3, 4, 5
@@ -90,6 +91,9 @@ _SIGS = {
     "cgp_record_pairs": (c_int32, [c_void_p, c_int32, c_void_p, c_void_p, c_void_p, c_int32, c_void_p]),
     "cgp_coarse_info": (c_int32, [c_void_p, POINTER(c_int32), POINTER(c_int32), POINTER(c_int32)]),
     "cgp_coarse_subdomains": (c_int32, [c_void_p, POINTER(c_int32)]),
+    "cgp_set_wait_test": (c_int32, [c_void_p, c_int32]),
+    "cgp_exact_fields": (c_int32, [c_void_p, c_double, c_void_p, c_void_p, c_int32, c_void_p]),
+    "cgp_mlp_copy_state": (c_int32, [c_void_p, c_void_p, c_void_p]),
     "cgp_poisson_solve": (c_int32, [c_void_p, c_void_p, c_void_p, POINTER(c_int32), c_int32, c_void_p]),
     "cgp_prolong": (c_int32, [c_void_p, c_void_p, c_void_p, c_int32, c_void_p]),
     "cgp_profile_step": (c_int32, [c_void_p, c_void_p, c_int32, c_void_p, c_void_p]),
@@ -122,7 +126,7 @@ PROF_NAMES = ["mom_prep", "mom_assemble", "mom_setup", "mom_init", "bicg_p", "bi
               "mass_setup", "mass_init", "mass_spmv", "mass_update", "finish", "pois_onelaunch", "mlp_forward",
               "ir_resid", "ir_update", "to_f32", "f32_init", "f32_bicg_p", "f32_bicg_v", "f32_bicg_s", "f32_bicg_t",
               "f32_bicg_x",
-              "pois_pupd", "corr_pupd", "mass_pupd", "cheb_mass", "cheb_corr"]
+              "pois_pupd", "corr_pupd", "mass_pupd", "cheb_mass", "cheb_corr", "proj"]
 
 _LIB = None
 
@@ -295,6 +299,21 @@ def cgp_coarse_info(solver):
     return k.value, n.value, c.value
 
 
+def cgp_exact_fields(solver, t, stream=None):
+    """Closed-form (U (N_f, 2), P (N_f,)) of a manufactured problem kind at time t (host)."""
+    nf = cgp_solver_info(solver)[0]
+    U = np.empty((nf, 2))
+    P = np.empty(nf)
+    _check(load().cgp_exact_fields(solver, float(t), _ptr(U), _ptr(P), CGP_HOST, _stream(stream)))
+    return U, P
+
+
+def cgp_set_wait_test(solver, on):
+    """Test hook: bounded device waits of the coarse solves wait for a signal nothing sends
+    (short limit), so the next solve returns CGP_ETIMEOUT; on = 0 restores them."""
+    _check(load().cgp_set_wait_test(solver, int(on)))
+
+
 def cgp_coarse_subdomains(solver):
     """Subdomains of the coarse solve's coarse correction (0: Jacobi alone)."""
     m = c_int32()
@@ -441,6 +460,11 @@ def cgp_mlp_train_step(m, r, q, target, batch, lr, want_loss=True, stream=None):
 
 def cgp_guess_set(solver, m, stream=None):
     _check(load().cgp_guess_set(solver, m, _stream(stream)))
+
+
+def cgp_mlp_copy_state(dst, src, stream=None):
+    """Weights and Adam state of src into dst (device to device, asynchronous)."""
+    _check(load().cgp_mlp_copy_state(dst, src, _stream(stream)))
 
 
 def cgp_mlp_destroy(m):

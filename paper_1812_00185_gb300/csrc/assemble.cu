@@ -7,6 +7,7 @@
 #include <cstring>
 
 #include "flows.cuh"
+#include "guess_proj.cuh"
 #include "solver.cuh"
 
 namespace cgp {
@@ -165,6 +166,12 @@ static int layout(Solver& s, void* base, size_t* bytes) {
         s.phi_guess = cv.take<double>(nc);
         s.mlp.carve(cv, (int)nc, 1);
     }
+    if (s.prm.guess == CGP_GUESS_LEARNED || s.prm.guess == CGP_GUESS_PROJ) {
+        s.hist_x = cv.take<double>((size_t)kProjL * nc);
+        s.hist_b = cv.take<double>((size_t)kProjL * nc);
+        s.phi_q = cv.take<double>(nc);
+        s.proj = reinterpret_cast<ProjState*>(cv.take<double>((sizeof(ProjState) + 7) / 8));
+    }
     s.cw32 = cv.take<float>(9 * nc);
     if (s.prm.precision == CGP_MIXED) {
         // on-chip plan: at most kOnchipMaxCluster x 16 warps x kOnchipRows slices; entries: the
@@ -230,8 +237,9 @@ static int check_params(const cgp_mesh* m, const cgp_params* p) {
     }
     if (p->k < 0 || p->k > m->n_levels || !(p->Re > 0) || !(p->dt > 0) || (p->chi != 0 && p->chi != 1) ||
         !(p->tol_mom > 0) || !(p->tol_poisson > 0) || !(p->tol_mass > 0) || p->max_it_mom < 1 ||
-        p->max_it_poisson < 1 || p->max_it_mass < 1 || p->bc_kind < 0 || p->bc_kind > CGP_BC_USER || p->restrict_mode < 0 || p->restrict_mode > CGP_RESTRICT_PT || p->precond < 0 || p->precond > CGP_PRECOND_COARSE ||
-        (p->precision != CGP_FP64 && p->precision != CGP_MIXED) || p->guess < 0 || p->guess > 2 ||
+        p->max_it_poisson < 1 || p->max_it_mass < 1 || p->bc_kind < 0 || p->bc_kind > CGP_BC_JOBELIN_DISK ||
+        (p->bc_kind == CGP_BC_JOBELIN_OPEN && p->restrict_mode != CGP_RESTRICT_INJECT) || p->restrict_mode < 0 || p->restrict_mode > CGP_RESTRICT_PT || p->precond < 0 || p->precond > CGP_PRECOND_COARSE ||
+        (p->precision != CGP_FP64 && p->precision != CGP_MIXED) || p->guess < 0 || p->guess > CGP_GUESS_PROJ ||
         (p->mass_mode != CGP_MASS_CONSISTENT && p->mass_mode != CGP_MASS_LUMPED) || p->coarse_mode < 0 ||
         p->coarse_mode > CGP_COARSE_ONCHIP || p->cluster_size < 0 || p->cluster_size > 16 || p->tol_inner < 0 ||
         p->tol_inner >= 1) {
@@ -360,7 +368,8 @@ extern "C" int cgp_assemble(const cgp_mesh* mesh, const cgp_params* params, void
         cudaMemsetAsync(s.phi, 0, sizeof(double) * s.nf, st) != cudaSuccess ||
         (s.user_ud && cudaMemsetAsync(s.user_ud, 0, sizeof(double) * 2 * s.nf, st) != cudaSuccess) ||
         (s.user_f && cudaMemsetAsync(s.user_f, 0, sizeof(double) * 2 * s.nf, st) != cudaSuccess) ||
-        cudaMemsetAsync(s.scal, 0, sizeof(double) * 16, st) != cudaSuccess) {
+        cudaMemsetAsync(s.scal, 0, sizeof(double) * 16, st) != cudaSuccess ||
+        (s.proj && cudaMemsetAsync(s.proj, 0, sizeof(ProjState), st) != cudaSuccess)) {
         set_error("workspace initialisation failed");
         return fail(CGP_ECUDA);
     }

@@ -94,6 +94,7 @@ __device__ __forceinline__ void oc_st_async(uint32_t addr, float v, uint32_t mba
                  : "memory");
 }
 constexpr long long kOnchipWaitCycles = 4000000000LL;   // ~2 s: a wait this long means a lost signal
+constexpr long long kOnchipWaitCyclesTest = 20000000LL; // ~10 ms, under the wait test hook
 
 // R rows of mu = E^+ s in one warp: lane l holds s of columns l*cpl .. l*cpl+cpl-1 (cpl =
 // 4, 2 or 1; `has` = those columns exist) and forms the partial sums of all R rows over them
@@ -311,14 +312,16 @@ static __global__ void __launch_bounds__(kOnchipThreads, 1) k_pcg_onchip(CoarseP
                 if (sender)
                     oc_st_async4(dst + 4 * (kOnchipSubOff + 4 * g), x[0], x[1], x[2], x[3], mbar_remote[lane][par]);
             }
+            // (the wait test hook expects 4 bytes more than anyone sends)
             if (lane == 0)
-                oc_mbar_arrive_expect(&mbar[par],
-                                      (uint32_t)(ncl * (4 * nr + 16 * nv4) + (publish ? 4 * halo_self : 0)));
+                oc_mbar_arrive_expect(&mbar[par], (uint32_t)(ncl * (4 * nr + 16 * nv4) + (publish ? 4 * halo_self : 0) +
+                                                             (a.wait_test ? 4 : 0)));
             bool ok = live;
             if (ok) {
                 const long long t0 = clock64();
+                const long long limit = a.wait_test ? kOnchipWaitCyclesTest : kOnchipWaitCycles;
                 while (!oc_mbar_try(&mbar[par], phase)) {
-                    if (abort_flag || clock64() - t0 > kOnchipWaitCycles) {
+                    if (abort_flag || clock64() - t0 > limit) {
                         ok = false;
                         break;
                     }

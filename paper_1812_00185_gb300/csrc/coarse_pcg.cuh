@@ -39,6 +39,7 @@ namespace cgrp = cooperative_groups;
 constexpr int kClusterThreads = 1024;
 constexpr int kGridThreads = 256;
 constexpr unsigned kSpinLimit = 1u << 24;   // polls of one grid barrier before giving up (~seconds)
+constexpr unsigned kSpinLimitTest = 1u << 14;   // the same under the wait test hook (milliseconds)
 constexpr int kStagnation = 2000;           // FP64 inner iterations without halving the best residual
 constexpr int kStagnation32 = 300;          // the same for the FP32 inner solve of the mixed form
 
@@ -64,6 +65,10 @@ struct CoarsePcgArgs {
     unsigned int* bar_count;   // zeroed before the launch
     int* bar_err;              // zeroed before the launch; set on a barrier timeout
     double* partials;          // 2 slots x gridDim x 4 doubles
+    // test hook (cgp_set_wait_test; 0 otherwise): every bounded wait also waits for one
+    // signal that nothing sends, under a limit of milliseconds, so the solve ends with
+    // CGP_ETIMEOUT without a fault or a hang
+    int wait_test;
 };
 
 template <class T>
@@ -135,7 +140,11 @@ struct GridSync {
     double (*wsum)[4];
     unsigned gen = 0;
     int slot = 0;
-    __device__ GridSync(unsigned* c, int* e, double* p, double (*ws)[4]) : count(c), err(e), partials(p), wsum(ws) {}
+    unsigned extra = 0;            // arrivals awaited beyond the grid's (1 under the wait test hook)
+    unsigned limit = kSpinLimit;
+    __device__ GridSync(unsigned* c, int* e, double* p, double (*ws)[4], int wait_test = 0)
+        : count(c), err(e), partials(p), wsum(ws), extra(wait_test ? 1u : 0u),
+          limit(wait_test ? kSpinLimitTest : kSpinLimit) {}
     __device__ int part() const { return (int)blockIdx.x; }
     __device__ int parts() const { return (int)gridDim.x; }
     __device__ bool sync() {
@@ -147,12 +156,12 @@ struct GridSync {
             // arrive: a release-ordered add publishes this CTA's writes (cumulative over the
             // CTA through the barrier above); wait: acquire-spin on the counter
             asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(count) : "memory");
-            const unsigned target = gen * gridDim.x;
+            const unsigned target = gen * gridDim.x + extra;
             unsigned spins = 0;
             for (;;) {
                 const unsigned v = ld_acquire_gpu(count);
                 if ((int)(v - target) >= 0) break;
-                if (++spins > kSpinLimit) {
+                if (++spins > limit) {
                     atomicExch(err, 1);
                     good = 0;
                     break;
@@ -657,7 +666,7 @@ static __global__ void __launch_bounds__(kClusterThreads, 1) k_pcg_batch(const C
 
 static __global__ void __launch_bounds__(kGridThreads) k_pcg_grid(CoarsePcgArgs a) {
     __shared__ double wsum[kGridThreads / 32][4];
-    GridSync sy(a.bar_count, a.bar_err, a.partials, wsum);
+    GridSync sy(a.bar_count, a.bar_err, a.partials, wsum, a.wait_test);
     coarse_pcg_body(a, sy);
 }
 

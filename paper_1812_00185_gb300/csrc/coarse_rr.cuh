@@ -258,7 +258,7 @@ __device__ void coarse_pcg_rr_body(const CoarsePcgArgs& a, Sync& sy) {
 
 static __global__ void __launch_bounds__(kGridThreads) k_pcg_grid_rr(CoarsePcgArgs a) {
     __shared__ double wsum[kGridThreads / 32][4];
-    GridSync sy(a.bar_count, a.bar_err, a.partials, wsum);
+    GridSync sy(a.bar_count, a.bar_err, a.partials, wsum, a.wait_test);
     coarse_pcg_rr_body(a, sy);
 }
 

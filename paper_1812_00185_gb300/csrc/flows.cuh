@@ -24,9 +24,54 @@ __device__ __forceinline__ void tg_shape(double x, double y, double& u, double& 
     p = -(cos(2.0 * tp * x) + cos(2.0 * tp * y)) / 4.0;
 }
 
+// The vortices of Sections 3.2 (open boundary, kind CGP_BC_JOBELIN_OPEN) and 3.3 (disk,
+// CGP_BC_JOBELIN_DISK): the fields and the first derivatives the body force and the
+// traction need.  Open: u = sin x sin(y+t), v = cos x cos(y+t), p = cos x sin(y+t).  Disk:
+// u = sin(x+t) sin(y+t), v = cos(x+t) cos(y+t), p = cos(x-y+t).  Both are divergence free
+// with Lap u = -2 u, Lap v = -2 v.
+struct JobelinPoint {
+    double u, v, p, ut, vt, ux, uy, vx, vy, px, py;
+};
+__device__ __forceinline__ JobelinPoint jobelin_point(int kind, double x, double y, double t) {
+    JobelinPoint d;
+    double sa, ca, sb, cb;
+    if (kind == CGP_BC_JOBELIN_OPEN) {
+        sincos(x, &sa, &ca);
+        sincos(y + t, &sb, &cb);
+        d.p = ca * sb;
+        d.ut = sa * cb;
+        d.vt = -ca * sb;
+        d.px = -sa * sb;
+        d.py = ca * cb;
+    } else {
+        sincos(x + t, &sa, &ca);
+        sincos(y + t, &sb, &cb);
+        const double c = x - y + t;
+        d.p = cos(c);
+        d.ut = ca * sb + sa * cb;
+        d.vt = -sa * cb - ca * sb;
+        d.px = -sin(c);
+        d.py = sin(c);
+    }
+    d.u = sa * sb;
+    d.v = ca * cb;
+    d.ux = ca * sb;
+    d.uy = sa * cb;
+    d.vx = -sa * cb;
+    d.vy = -ca * sb;
+    return d;
+}
+
 // closed form (u, v, p) at (x, y, t); false if the kind has none
 __device__ __forceinline__ bool exact_field(const BcParams& bc, double x, double y, double t, double& u, double& v,
                                             double& p) {
+    if (bc.kind == CGP_BC_JOBELIN_OPEN || bc.kind == CGP_BC_JOBELIN_DISK) {
+        const JobelinPoint d = jobelin_point(bc.kind, x, y, t);
+        u = d.u;
+        v = d.v;
+        p = d.p;
+        return true;
+    }
     if (bc.kind == CGP_BC_TG) {
         tg_shape(x, y, u, v, p);
         const double e = exp(-8.0 * M_PI * M_PI * t / bc.Re);
@@ -86,7 +131,31 @@ __device__ __forceinline__ void body_force(const BcParams& bc, int i, double x, 
         const double c = gp + 8.0 * M_PI * M_PI * g / bc.Re;
         fx = c * u;
         fy = c * v;
+        return;
     }
+    if (bc.kind == CGP_BC_JOBELIN_OPEN || bc.kind == CGP_BC_JOBELIN_DISK) {
+        // f = u_t + (u . grad) u - Lap u / Re + grad p, with Lap u = -2 u
+        const JobelinPoint d = jobelin_point(bc.kind, x, y, t);
+        fx = d.ut + d.u * d.ux + d.v * d.uy + 2.0 * d.u / bc.Re + d.px;
+        fy = d.vt + d.u * d.vx + d.v * d.vy + 2.0 * d.v / bc.Re + d.py;
+    }
+}
+
+// Data on the natural boundary Gamma_N (the PHI_ZERO vertices): the traction of Eq. 4 and
+// the prescribed pressure.  Only the open-boundary vortex has any (Gamma_N = the y-axis,
+// outward normal (-1, 0)); elsewhere the traction is zero and phi = 0 on Gamma_N.
+__device__ __forceinline__ bool has_natural_data(const BcParams& bc) { return bc.kind == CGP_BC_JOBELIN_OPEN; }
+
+// t = -p n + (grad u) n / Re at a Gamma_N vertex
+__device__ __forceinline__ void natural_traction(const BcParams& bc, double x, double y, double t, double& tx,
+                                                 double& ty) {
+    const JobelinPoint d = jobelin_point(CGP_BC_JOBELIN_OPEN, x, y, t);
+    tx = d.p - d.ux / bc.Re;
+    ty = -d.vx / bc.Re;
+}
+
+__device__ __forceinline__ double natural_pressure(const BcParams& bc, double x, double y, double t) {
+    return jobelin_point(CGP_BC_JOBELIN_OPEN, x, y, t).p;
 }
 
 inline BcParams bc_from(const cgp_params& p) {

@@ -590,6 +590,24 @@ extern "C" int cgp_mlp_set_params(cgp_mlp* m, const float* params, int32_t where
     return CGP_OK;
 }
 
+extern "C" int cgp_mlp_copy_state(cgp_mlp* dst, const cgp_mlp* src, cgp_stream_t stream) {
+    clear_error();
+    if (!dst || !src) {
+        set_error("cgp_mlp_copy_state: null argument");
+        return CGP_EINVAL;
+    }
+    if (dst == src) return CGP_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t fb = sizeof(float) * kMlpParams;
+    CGP_CUDA(cudaMemcpyAsync(dst->B.params, src->B.params, fb, cudaMemcpyDeviceToDevice, st));
+    CGP_CUDA(cudaMemcpyAsync(dst->B.params_bf, src->B.params_bf, sizeof(__nv_bfloat16) * kMlpParams,
+                             cudaMemcpyDeviceToDevice, st));
+    CGP_CUDA(cudaMemcpyAsync(dst->adam_m, src->adam_m, fb, cudaMemcpyDeviceToDevice, st));
+    CGP_CUDA(cudaMemcpyAsync(dst->adam_v, src->adam_v, fb, cudaMemcpyDeviceToDevice, st));
+    dst->adam_t = src->adam_t;
+    return CGP_OK;
+}
+
 extern "C" int cgp_mlp_get_params(cgp_mlp* m, float* params, int32_t where, cgp_stream_t stream) {
     clear_error();
     if (!m || !params) {

@@ -9,6 +9,8 @@
 // work vectors) in one file-scope __device__ array of fixed size, so the call allocates
 // nothing: the caller passes only the operator, the right-hand side, the solution buffer
 // and a two-int status buffer.
+#include <mutex>
+
 #include "coarse_pcg.cuh"
 
 namespace cgp {
@@ -38,8 +40,36 @@ using namespace cgp;
 
 namespace {
 constexpr int kMaxDevices = 64;
-double* g_scratch_ptr[kMaxDevices] = {nullptr};
-int g_grid[kMaxDevices] = {0};
+// Per device: the context the address was looked up in, the array's device address there,
+// and the launch size.  A symbol's address belongs to a context, so a new primary context
+// (after cudaDeviceReset) is looked up again.  The mutex orders first calls from several
+// host threads.
+struct NoAllocSlot {
+    void* ctx;
+    double* ptr;
+    int grid;
+};
+NoAllocSlot g_slot[kMaxDevices] = {};
+std::mutex g_slot_mu;
+typedef int (*CtxGetCurrentFn)(void**);   // the driver's cuCtxGetCurrent, reached through the runtime
+
+// The calling thread's current context on `dev` (made current by cudaSetDevice, which
+// initialises the device's primary context), or nullptr where the driver does not give it.
+void* current_context(int dev) {
+    static CtxGetCurrentFn fn = nullptr;
+    static bool looked = false;
+    if (!looked) {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (CtxGetCurrentFn)f;
+        looked = true;
+    }
+    if (cudaSetDevice(dev) != cudaSuccess || !fn) return nullptr;
+    void* ctx = nullptr;
+    return fn(&ctx) == 0 ? ctx : nullptr;
+}
 }  // namespace
 
 extern "C" int cgp_pcg_sell_noalloc(int32_t n, int32_t nslices, const int32_t* sell_ptr, const int32_t* sell_col,
@@ -61,26 +91,35 @@ extern "C" int cgp_pcg_sell_noalloc(int32_t n, int32_t nslices, const int32_t* s
         set_error("cgp_pcg_sell_noalloc: device index %d out of range", dev);
         return CGP_EINVAL;
     }
-    if (!g_scratch_ptr[dev]) {
-        // first call on this device: the device address of the scratch array, and the
-        // number of co-resident CTAs of the cooperative launch
-        void* p = nullptr;
-        CGP_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch));
-        int sms = 0, per_sm = 0, coop = 0;
-        CGP_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-        CGP_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
-        CGP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pcg_grid, kGridThreads, 0));
-        if (!coop || per_sm < 1) {
-            set_error("cgp_pcg_sell_noalloc: cooperative launch unavailable");
-            return CGP_EINVAL;
+    double* base = nullptr;
+    int max_grid = 0;
+    {
+        std::lock_guard<std::mutex> lock(g_slot_mu);
+        NoAllocSlot& sl = g_slot[dev];
+        void* ctx = current_context(dev);
+        if (!sl.ptr || ctx != sl.ctx) {
+            // first call on this device (or in a new context of it): the device address of
+            // the scratch array, and the number of co-resident CTAs of the cooperative launch
+            void* p = nullptr;
+            CGP_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+            int sms = 0, per_sm = 0, coop = 0;
+            CGP_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+            CGP_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
+            CGP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pcg_grid, kGridThreads, 0));
+            if (!coop || per_sm < 1) {
+                set_error("cgp_pcg_sell_noalloc: cooperative launch unavailable");
+                return CGP_EINVAL;
+            }
+            const int g = sms * (per_sm < 2 ? per_sm : 2);
+            sl.grid = g < kNoAllocMaxCtas ? g : kNoAllocMaxCtas;
+            sl.ptr = (double*)p;
+            sl.ctx = ctx;
         }
-        int g = sms * (per_sm < 2 ? per_sm : 2);
-        g_grid[dev] = g < kNoAllocMaxCtas ? g : kNoAllocMaxCtas;
-        g_scratch_ptr[dev] = (double*)p;
+        base = sl.ptr;
+        max_grid = sl.grid;
     }
-    double* base = g_scratch_ptr[dev];
     int grid = (nslices + kGridThreads / 32 - 1) / (kGridThreads / 32);
-    if (grid > g_grid[dev]) grid = g_grid[dev];
+    if (grid > max_grid) grid = max_grid;
     if (grid < 1) grid = 1;
     cudaStream_t st = (cudaStream_t)stream;
     CoarsePcgArgs a = {};

@@ -36,6 +36,8 @@ struct DeviceStats {
     double res[KS_COUNT];
 };
 
+struct ProjState;   // guess_proj.cuh
+
 struct Solver {
     const cgp_mesh* mesh = nullptr;
     cgp_params prm{};
@@ -58,6 +60,12 @@ struct Solver {
     float *Kc0f = nullptr, *dinvKcf = nullptr;                   // FP32 copies (mixed precision)
     MlpBuffers mlp;               // learned guess (CGP_GUESS_LEARNED): weights and batch-1 activations
     bool guess_ready = false;     // weights set by cgp_guess_set
+    int wait_test = 0;            // test hook of cgp_set_wait_test
+    // projection guess (CGP_GUESS_PROJ, CGP_GUESS_LEARNED): the last solutions and right-hand
+    // sides of the coarse solve (kProjL x n_c each), their Galerkin matrix, and the guess the
+    // network sees (copied for cgp_record_pairs)
+    double *hist_x = nullptr, *hist_b = nullptr, *phi_q = nullptr;
+    ProjState* proj = nullptr;
     double* phi_guess = nullptr;  // n_c: the network's prediction of Phi_c
     double* cw64 = nullptr;       // coarse one-launch solver work: 8 FP64 vectors of n_c
     float* cw32 = nullptr;        // and 9 FP32 vectors of n_c

@@ -8,6 +8,7 @@
 #include "coarse_rr.cuh"
 #include "coarse_onchip.cuh"
 #include "flows.cuh"
+#include "guess_proj.cuh"
 #include "solver.cuh"
 
 namespace cgp {
@@ -65,7 +66,12 @@ __global__ void k_mom_prep(int nf, const double* __restrict__ U, const double* _
 // Row i of the momentum system of Eq. 21:
 //   A = 3/2 M + dt N(w) + dt/Re K,  N_ij = sum_T |T|/12 (W_T + w_i) . grad psi_j
 //   b = dt (Cx^T P, Cy^T P) + M h     (pressure term in weak form, see the readings)
-// Dirichlet rows: identity row, b = u_D(t^{n+1}).  Also x0 = w (u_D on Dirichlet rows), dinv.
+// Dirichlet rows: s_ii times the identity row, b = s_ii u_D(t^{n+1}), with s_ii the diagonal
+// of S = 3/2 M + dt/Re K at that row: the same solution as the plain identity row, but rows
+// of one scale, so that the relative residual test ||b - A x|| <= tol ||b|| measures the
+// interior equations (with identity rows the O(1) boundary values dominate ||b|| against
+// interior rows of the size of the mass matrix, O(h^2), and the test passes while the
+// interior equations hold only to ~1e-4).  Also x0 = w (u_D on Dirichlet rows), dinv.
 // Rows of at most kAsmRow entries are accumulated in shared memory ([entry][thread], so the
 // lanes of a warp hit distinct banks) and written to A once; longer rows add into A directly.
 constexpr int kAsmRow = 16;
@@ -86,11 +92,15 @@ __global__ void __launch_bounds__(kBlock) k_mom_assemble(int nf, const int32_t* 
         const int64_t e0 = sell_pos(sell_ptr, i, 0);   // entry k of the row is at e0 + 32 k
         const bool local = re - rb <= kAsmRow;
         if (tag[i] & CGP_VEL_DIR) {
-            for (int q = rb; q < re; ++q) A[e0 + 32 * (q - rb)] = col[q] == i ? 1.0 : 0.0;
-            dinv[i] = 1.0;
+            double sii = 1.0;
+            for (int q = rb; q < re; ++q)
+                if (col[q] == i) sii = S[e0 + 32 * (q - rb)];
+            if (!(sii > 0.0)) sii = 1.0;
+            for (int q = rb; q < re; ++q) A[e0 + 32 * (q - rb)] = col[q] == i ? sii : 0.0;
+            dinv[i] = 1.0 / sii;
             double u, v;
             dirichlet_value(bc, i, xy[2 * i], xy[2 * i + 1], tn, u, v);
-            reinterpret_cast<double2*>(b)[i] = make_double2(u, v);
+            reinterpret_cast<double2*>(b)[i] = make_double2(sii * u, sii * v);
             reinterpret_cast<double2*>(x0)[i] = make_double2(u, v);
             continue;
         }
@@ -137,6 +147,30 @@ __global__ void __launch_bounds__(kBlock) k_mom_assemble(int nf, const int32_t* 
         } else {
             dinv[i] = 1.0 / A[e0 + 32 * diag_slot];
         }
+        if ((tag[i] & CGP_PHI_ZERO) && has_natural_data(bc)) {
+            // traction boundary (Eq. 11): dt int_{Gamma_N} t psi_i ds over the boundary edges
+            // (i, j), j on Gamma_N too, an edge being on the boundary when one triangle has it;
+            // t linear on the edge: l/6 (2 t_i + t_j)
+            const double xi = xy[2 * i], yi = xy[2 * i + 1];
+            double ti_x, ti_y;
+            natural_traction(bc, xi, yi, tn, ti_x, ti_y);
+            for (int q = rb; q < re; ++q) {
+                const int j = col[q];
+                if (j == i || !(tag[j] & CGP_PHI_ZERO)) continue;
+                int owners = 0;
+                for (int m = vt_ptr[i]; m < vt_ptr[i + 1]; ++m) {
+                    const int t = vt_list[m];
+                    owners += (tri[3 * t] == j) + (tri[3 * t + 1] == j) + (tri[3 * t + 2] == j);
+                }
+                if (owners != 1) continue;
+                const double xj = xy[2 * j], yj = xy[2 * j + 1];
+                double tj_x, tj_y;
+                natural_traction(bc, xj, yj, tn, tj_x, tj_y);
+                const double c = dt * hypot(xj - xi, yj - yi) / 6.0;
+                bx += c * (2.0 * ti_x + tj_x);
+                by += c * (2.0 * ti_y + tj_y);
+            }
+        }
         reinterpret_cast<double2*>(b)[i] = make_double2(bx, by);
         reinterpret_cast<double2*>(x0)[i] = wi;
     }
@@ -165,6 +199,25 @@ __global__ void __launch_bounds__(kBlock) k_coarse_rhs(SellView Ac, const double
     }
     double tot[1];
     if (grid_sum<1>(acc, partials, ticket, tot) && threadIdx.x == 0) st->mean = pure_neumann ? tot[0] / Ac.n : 0.0;
+}
+
+// Eq. 23 with a prescribed pressure on Gamma_N (has_natural_data): phi = g = p(t^{n+1}) - P^n
+// at the PHI_ZERO rows and K_c[i, Gamma_N] g moved to the right-hand side of the others
+// (the rows and columns of the PHI_ZERO vertices are those of the identity in the solve)
+__global__ void __launch_bounds__(kBlock) k_coarse_lift(SellView Ac, const double* __restrict__ Kc,
+                                                       const uint8_t* __restrict__ tag, const double* __restrict__ xy,
+                                                       const double* __restrict__ P, BcParams bc,
+                                                       const double* __restrict__ tdev, double dt,
+                                                       double* __restrict__ rc) {
+    const int lane = threadIdx.x & 31;
+    const double tn = *tdev + dt;
+    auto g = [&](int j) { return natural_pressure(bc, xy[2 * j], xy[2 * j + 1], tn) - P[j]; };
+    CGP_SLICE_LOOP(Ac, sl) {
+        const int i = sl * 32 + lane;
+        double s[1] = {0.0};
+        sell_accum<1>(Ac, Kc, sl, lane, [&](int j, double (&o)[1]) { o[0] = (tag[j] & CGP_PHI_ZERO) ? g(j) : 0.0; }, s);
+        if (i < Ac.n) rc[i] = (tag[i] & CGP_PHI_ZERO) ? g(i) : rc[i] - s[0];
+    }
 }
 
 // One level of P^T, the transposed prolongation (CGP_RESTRICT_PT).  On a red refinement the
@@ -919,6 +972,7 @@ CoarsePcgArgs coarse_args(Solver& s) {
     a.bar_count = s.bar_count;
     a.bar_err = s.bar_err;
     a.partials = s.coarse_partials;
+    a.wait_test = s.wait_test;
     return a;
 }
 
@@ -1032,8 +1086,19 @@ int step_pre(Ctx& c) {
         PL(c, CGP_PROF_COARSE_RHS,
            k_coarse_rhs<<<grid_rows(s, C.nslices * 32, 1), kBlock, 0, c.st>>>(
                Ac, s.Cxc, s.Cyc, s.Ut, C.tag, p.dt, s.rc, &s.ks[KS_POIS], s.pure_neumann, s.partials, s.tickets));
+        if (p.bc_kind == CGP_BC_JOBELIN_OPEN)
+            PL(c, CGP_PROF_COARSE_RHS, k_coarse_lift<<<grid_rows(s, C.nslices * 32, 1), kBlock, 0, c.st>>>(
+                                           Ac, s.Kc, C.tag, C.xy, s.P, bc, s.tdev, p.dt, s.rc));
     }
     CGP_LAUNCH_CHECK();
+    if (s.proj) {
+        // the projection guess of the coarse solve (and the network's second input)
+        const int gc = grid_rows(s, C.nv, 1);
+        PL(c, CGP_PROF_PROJ, k_proj_coef<<<gc, kBlock, 0, c.st>>>(C.nv, s.hist_x, s.hist_b, s.rc, &s.ks[KS_POIS],
+                                                                   s.proj, p.tol_poisson, s.partials, s.tickets));
+        PL(c, CGP_PROF_PROJ, k_proj_combine<<<gc, kBlock, 0, c.st>>>(C.nv, s.hist_x, s.proj, s.phi, s.phi_q));
+        CGP_LAUNCH_CHECK();
+    }
     return learned_guess(c);
 }
 
@@ -1065,6 +1130,13 @@ int step_post(Ctx& c, bool mass_done) {
     const Level& F = s.mesh->lev[s.lf];
     SellView Af = sell_of(F);
     const int gv = grid_rows(s, F.nv, 1), gs = grid_rows(s, F.nslices * 32, 1);
+    if (s.proj) {
+        // the new coarse solution joins the projection window
+        const int nc = s.mesh->lev[s.lc].nv;
+        PL(c, CGP_PROF_PROJ, k_proj_push<<<grid_rows(s, nc, 1), kBlock, 0, c.st>>>(nc, s.phi, s.hist_x, s.hist_b,
+                                                                                     s.proj, s.partials, s.tickets));
+        CGP_LAUNCH_CHECK();
+    }
     // Eq. 24: prolongation
     CGP_TRY(prolong_all(c));
     // Eq. 25: velocity correction
@@ -1084,13 +1156,14 @@ int step_post(Ctx& c, bool mass_done) {
     if (p.chi && !mass_done) CGP_TRY(rotational_term(c));
     const bool one_launch = s.coarse_kind != CGP_COARSE_KERNELS;
     const int coarse_fixed = (one_launch ? 1 : 2 + (s.pure_neumann ? 2 : 0)) +
-                             ((p.guess == CGP_GUESS_LEARNED && s.guess_ready) ? 10 : 0);
+                             ((p.guess == CGP_GUESS_LEARNED && s.guess_ready) ? 10 : 0) + (s.proj ? 3 : 0);
     // mixed: the FP32 copy of A; momentum: kIrSweeps x (residual, inner init, update); each
     // Chebyshev mass solve: kChebSweeps x (residual, init, kChebSteps steps, update)
     const int ir_fixed = mixed ? 1 + 3 * kIrSweeps +
                                      (3 + kChebSteps) * kChebSweeps * ((lumped ? 0 : 1) + (p.chi && !lumped ? 1 : 0))
                                : 0;
-    const int pt_fixed = p.restrict_mode == CGP_RESTRICT_PT ? 1 + (s.lf - s.lc) : 0;   // k_div + the P^T levels
+    const int pt_fixed = (p.restrict_mode == CGP_RESTRICT_PT ? 1 + (s.lf - s.lc) : 0) +   // k_div + the P^T levels
+                         (p.bc_kind == CGP_BC_JOBELIN_OPEN ? 1 : 0);                     // k_coarse_lift
     const int fixed =
         4 + 1 + coarse_fixed + (s.lf - s.lc) + 1 + (lumped ? 0 : 2) + (p.chi ? 1 + (lumped ? 0 : 2) : 0) + 1 + ir_fixed +
         pt_fixed;
@@ -1286,8 +1359,11 @@ extern "C" int cgp_record_pairs(cgp_solver* h, int32_t n_steps, double* rhs, dou
     cudaStream_t st = (cudaStream_t)stream;
     const size_t nc = s.nc, bytes = sizeof(double) * nc;
     for (int k = 0; k < n_steps; ++k) {
-        CGP_TRY(copy_out(prev + k * nc, s.phi, bytes, where, st));
+        // the network's second input: the projection guess of the step where the solver forms
+        // one (copied during the step), else the increment before the step
+        if (!s.proj) CGP_TRY(copy_out(prev + k * nc, s.phi, bytes, where, st));
         CGP_TRY(cgp_step(h, 1, stream));
+        if (s.proj) CGP_TRY(copy_out(prev + k * nc, s.phi_q, bytes, where, st));
         CGP_TRY(copy_out(rhs + k * nc, s.rc, bytes, where, st));
         CGP_TRY(copy_out(target + k * nc, s.phi, bytes, where, st));
     }
@@ -1433,6 +1509,60 @@ extern "C" int cgp_set_vector(cgp_solver* h, int32_t which, const double* in, in
     cudaStream_t st = (cudaStream_t)stream;
     CGP_TRY(copy_in(dst, in, n * sizeof(double), where, st));
     if (where == CGP_HOST) CGP_CUDA(cudaStreamSynchronize(st));
+    return CGP_OK;
+}
+
+// closed-form fields of a manufactured problem kind on every fine vertex
+__global__ void k_exact_fields(int n, const double* __restrict__ xy, BcParams bc, double t, double* __restrict__ U,
+                               double* __restrict__ P) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        double u = 0.0, v = 0.0, p = 0.0;
+        exact_field(bc, xy[2 * i], xy[2 * i + 1], t, u, v, p);
+        if (U) reinterpret_cast<double2*>(U)[i] = make_double2(u, v);
+        if (P) P[i] = p;
+    }
+}
+
+extern "C" int cgp_exact_fields(cgp_solver* h, double t, double* U, double* P, int32_t where, cgp_stream_t stream) {
+    clear_error();
+    if (!h || (!U && !P) || (where != CGP_HOST && where != CGP_DEVICE)) {
+        set_error("cgp_exact_fields: bad arguments");
+        return CGP_EINVAL;
+    }
+    Solver& s = h->s;
+    const BcParams bc = bc_of(s);
+    if (bc.kind != CGP_BC_TG && bc.kind != CGP_BC_TG_PERIODIC && bc.kind != CGP_BC_JOBELIN_OPEN &&
+        bc.kind != CGP_BC_JOBELIN_DISK) {
+        set_error("cgp_exact_fields: the problem kind has no closed-form solution");
+        return CGP_EINVAL;
+    }
+    const Level& F = s.mesh->lev[s.lf];
+    cudaStream_t st = (cudaStream_t)stream;
+    double* dU = U;
+    double* dP = P;
+    if (where == CGP_HOST) {
+        // staged through the extrapolation and history vectors of Eq. 21, which every step
+        // forms anew before reading them
+        dU = U ? s.w : nullptr;
+        dP = P ? s.h : nullptr;
+    }
+    k_exact_fields<<<grid_rows(s, F.nv, 1), kBlock, 0, st>>>(F.nv, F.xy, bc, t, dU, dP);
+    CGP_LAUNCH_CHECK();
+    if (where == CGP_HOST) {
+        if (U) CGP_CUDA(cudaMemcpyAsync(U, dU, sizeof(double) * 2 * F.nv, cudaMemcpyDeviceToHost, st));
+        if (P) CGP_CUDA(cudaMemcpyAsync(P, dP, sizeof(double) * F.nv, cudaMemcpyDeviceToHost, st));
+        CGP_CUDA(cudaStreamSynchronize(st));
+    }
+    return CGP_OK;
+}
+
+extern "C" int cgp_set_wait_test(cgp_solver* h, int32_t on) {
+    clear_error();
+    if (!h) {
+        set_error("null solver");
+        return CGP_EINVAL;
+    }
+    h->s.wait_test = on ? 1 : 0;
     return CGP_OK;
 }
 

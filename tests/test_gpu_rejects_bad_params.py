@@ -13,7 +13,7 @@ pytestmark = pytest.mark.gpu
 BAD = [("Re", 0.0), ("Re", float("nan")), ("dt", -1.0), ("chi", 2), ("k", -1), ("k", 3),
        ("tol_mom", 0.0), ("tol_poisson", 0.0), ("tol_mass", 0.0), ("max_it_mom", 0),
        ("max_it_poisson", 0), ("max_it_mass", 0), ("bc_kind", 99), ("restrict_mode", 2),
-       ("precond", 3), ("precision", 7), ("guess", 3), ("mass_mode", 9), ("coarse_mode", 99),
+       ("precond", 3), ("precision", 7), ("guess", 4), ("mass_mode", 9), ("coarse_mode", 99),
        ("cluster_size", 17), ("tol_inner", 1.0)]
 
 

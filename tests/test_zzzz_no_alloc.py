@@ -1,19 +1,22 @@
-"""The allocation-free solve entry point (cgp_pcg_sell_noalloc) against the solver's own
-coarse Poisson solve (cgp_poisson_solve), through the C ABI.
+"""The allocation-free solve entry point (cgp_pcg_sell_noalloc) through the C ABI, against
+the solver's own coarse Poisson solve (cgp_poisson_solve) and the oracle's direct solve.
 
 Callers that cannot allocate device memory hand this entry point only the operator, the
 right-hand side and the output buffers; its scratch is a fixed array inside the library.
 The test builds the coarse operator of Eq. 23 (with its phi = 0 rows eliminated) in the
 SELL-32 layout on the host, calls the entry point twice in a row on the same scratch (two
-right-hand sides), and compares each result with the existing entry point's.  This file
-is collected after the main suites so that a run stopping at the first failure has run
-them first.
+right-hand sides), and compares each result with the existing entry point's and with the
+oracle's; then a warm start (fewer iterations, the same solution) and an iteration cap
+(CGP_ENOTCONV with a finite iterate).  This file is collected last, so a run that stops at
+the first failure has run every other test first.
 """
 
 import numpy as np
 import pytest
 
 from workloads import channel_cylinder_mesh
+from oracle.cgp import CGPOracle
+from oracle import flows
 
 pytestmark = pytest.mark.gpu
 
@@ -63,7 +66,9 @@ def test_noalloc_solve_matches_poisson_entry_point(lib):
     dev = lambda a: torch.as_tensor(np.ascontiguousarray(a), device="cuda")
     d_ptr, d_col, d_val, d_dinv = dev(sptr), dev(scol), dev(sval), dev(dinv)
     info = torch.zeros(2, dtype=torch.int32, device="cuda")
+    o = CGPOracle(base, 2, 1, 20.0, 0.01, 0, flows.BC_CHANNEL, bc_param=(0.3, 0.41, 0, 0))
     rng = np.random.default_rng(3)
+    b = None
     for call in range(2):                      # two calls in a row share the scratch array
         b = rng.standard_normal(n)
         b[z] = 0.0
@@ -76,6 +81,23 @@ def test_noalloc_solve_matches_poisson_entry_point(lib):
         got = x.cpu().numpy()
         assert status == 0 and 0 < it < 20000, (call, it, status)
         assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < 1e-8, call
+        exact = o.poisson(b)
+        assert np.linalg.norm(got - exact) / np.linalg.norm(exact) < 1e-8, call
+    # warm start: x on entry is the initial guess (the solution slightly perturbed)
+    x0 = exact + 1e-6 * np.linalg.norm(exact) / np.sqrt(n) * rng.standard_normal(n)
+    x0[z] = 0.0
+    x = dev(x0)
+    cg.cgp_pcg_sell_noalloc(n, ns, d_ptr, d_col, d_val, d_dinv, dev(b), x, 1e-11, 20000, info)
+    torch.cuda.synchronize()
+    it_warm, status = info.cpu().tolist()
+    assert status == 0 and it_warm < it, (it_warm, it)
+    assert np.linalg.norm(x.cpu().numpy() - exact) / np.linalg.norm(exact) < 1e-8
+    # iteration cap: the solve stops with CGP_ENOTCONV and a finite iterate
+    x = torch.zeros(n, dtype=torch.float64, device="cuda")
+    cg.cgp_pcg_sell_noalloc(n, ns, d_ptr, d_col, d_val, d_dinv, dev(b), x, 1e-11, 5, info)
+    torch.cuda.synchronize()
+    it_cap, status = info.cpu().tolist()
+    assert status == cg.CGP_ENOTCONV and it_cap <= 5 and torch.isfinite(x).all()
     s.close()
     mesh.close()
 

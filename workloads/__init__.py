@@ -18,9 +18,9 @@ only the homogeneous Neumann condition for phi of Eq. 13 applies).
 """
 
 from .meshes import (VEL_DIR, PHI_ZERO, square_mesh, crisscross_mesh,
-                     channel_cylinder_mesh, BaseMesh)
+                     channel_cylinder_mesh, open_square_mesh, disk_mesh, BaseMesh)
 from .configs import WORKLOADS, Workload, batch_instances
 
 __all__ = ["VEL_DIR", "PHI_ZERO", "square_mesh", "crisscross_mesh",
-           "channel_cylinder_mesh", "BaseMesh", "WORKLOADS", "Workload",
+           "channel_cylinder_mesh", "open_square_mesh", "disk_mesh", "BaseMesh", "WORKLOADS", "Workload",
            "batch_instances"]

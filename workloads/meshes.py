@@ -269,3 +269,47 @@ def channel_cylinder_mesh(seed=0, h=0.0084, L=2.2, H=0.41, xc=0.2, yc=0.2, r=0.0
                     name="channel_seed%d" % seed,
                     meta={"area": area, "h": h, "L": L, "H": H, "xc": xc, "yc": yc,
                           "r": r, "n_cyl": nc, "seed": seed})
+
+
+def open_square_mesh(n):
+    """The open-boundary vortex domain of Section 3.2: [0,1]^2 as n x n squares of four
+    triangles (crisscross_mesh), velocity Dirichlet data on x = 1, y = 0 and y = 1, the
+    traction boundary on the y-axis x = 0 (PHI_ZERO; its two corners carry both flags)."""
+    m = crisscross_mesh(n, boundary_flags=0)
+    x, y = m.xy[:, 0], m.xy[:, 1]
+    tag = np.zeros(m.n_vert, np.uint8)
+    tag[(x == 1.0) | (y == 0.0) | (y == 1.0)] |= VEL_DIR
+    tag[x == 0.0] |= PHI_ZERO
+    m.tag = tag
+    m.name = "open_square%d" % n
+    return m
+
+
+def disk_mesh(n_boundary=96, n_interior=1105, r=0.5):
+    """The disk of Section 3.3 (x^2 + y^2 < r^2) as an unstructured Delaunay mesh: n_boundary
+    vertices on the circle and n_interior vertices inside on a Vogel (golden-angle) spiral,
+    so that a triangulation of the convex boundary polygon has exactly
+    2 (n_boundary + n_interior) - n_boundary - 2 triangles.  The defaults give the paper's
+    Fig. 1 counts: 1201 vertices and 2304 triangles, refined once 4705 / 9216, twice 18,625 /
+    36,864.  Every boundary vertex carries VEL_DIR (Dirichlet data on the whole boundary)."""
+    from scipy.spatial import Delaunay
+
+    th = 2.0 * np.pi * np.arange(n_boundary) / n_boundary
+    bnd = np.stack([r * np.cos(th), r * np.sin(th)], 1)
+    # interior radius capped a bit inside the circle, spacing comparable to the boundary's
+    k = np.arange(n_interior) + 0.5
+    rho = (r - 0.5 * np.pi * r / n_boundary) * np.sqrt(k / n_interior)
+    phi = k * np.pi * (3.0 - np.sqrt(5.0))
+    inner = np.stack([rho * np.cos(phi), rho * np.sin(phi)], 1)
+    pts = np.concatenate([bnd, inner])
+    tri = Delaunay(pts).simplices.astype(np.int64)
+    a2 = _signed_area2(pts, tri)
+    flip = a2 < 0
+    tri[flip] = tri[flip][:, [0, 2, 1]]
+    if np.abs(a2).min() <= 1e-12:
+        raise RuntimeError("degenerate triangle in the disk mesh")
+    tag = np.zeros(len(pts), np.uint8)
+    tag[:n_boundary] = VEL_DIR
+    area = 0.5 * n_boundary * r * r * np.sin(2.0 * np.pi / n_boundary)
+    return BaseMesh(pts.astype(np.float64), tri.astype(np.int32), tag, name="disk%d" % len(pts),
+                    meta={"area": area, "r": r, "n_boundary": n_boundary})
