@@ -314,11 +314,18 @@ def run_gpu(args, rank, world):
     # midpoint average of two parents (indices and values) at the new ones, phi written
     lv = [mesh.info(l)[0] for l in range(w.n_levels - w.k, w.n_levels + 1)]
     prolong_bytes = sum(8 * lv[i] + 16 * (lv[i + 1] - lv[i]) + 8 * lv[i + 1] for i in range(len(lv) - 1))
+    kind, ctas, cl = s.coarse_info()
+    its_c = max(1, s.fields()[3]["it_poisson"])          # inner iterations of the profiled step's coarse solve
+    mixed_c = kind in (cg.CGP_COARSE_ONCHIP,) or ("mixed" in head_form and kind == cg.CGP_COARSE_PERSISTENT_MEM)
     for name, (cnt, tot) in prof.items():
         n, z, t = (nv_c, nnz_c, nt_c) if level_of(name) == "coarse" else (nv_f, nnz_f, nt_f)
         b = kernel_bytes(name, n, z, t)
         if name == "prolong":
             b = prolong_bytes / max(1, w.k)   # per launch (one per level)
+        if name == "pois_onelaunch":
+            # one-launch coarse PCG: the algorithmic bytes of its iterations (FP32 inner:
+            # 8 nnz + 56 N per iteration; FP64: 12 nnz + 108 N), whether or not they leave chip
+            b = its_c * ((8 * nnz_c + 56 * nv_c) if mixed_c else (12 * nnz_c + 108 * nv_c))
         avg = tot / cnt
         kern[name] = {"launches": cnt, "total_ms": round(tot, 4), "avg_us": round(1000 * avg, 2),
                       "GBps": round(b / (avg * 1e-3) / 1e9, 1) if b else None}
@@ -329,17 +336,23 @@ def run_gpu(args, rank, world):
             traffic_tab = json.load(open(tr_path)).get(args.workload, {})
         except Exception:
             traffic_tab = {}
-    # the dominant kernel with an HBM byte model, against the measured copy bandwidth
+    # the dominant kernel (largest share of the profiled step) with its algorithmic HBM bytes,
+    # against the measured copy bandwidth
     dom = max(kern, key=lambda k: kern[k]["total_ms"] if kern[k]["GBps"] is not None else -1)
     n, z, t = (nv_c, nnz_c, nt_c) if level_of(dom) == "coarse" else (nv_f, nnz_f, nt_f)
-    roof_hbm = {"kernel": dom, "bound": "hbm", "achieved": kern[dom]["GBps"], "peak": peak, "unit": "GB/s",
+    bpl = (its_c * ((8 * nnz_c + 56 * nv_c) if mixed_c else (12 * nnz_c + 108 * nv_c)) if dom == "pois_onelaunch"
+           else kernel_bytes(dom, n, z, t))
+    roof_hbm = {"kernel": "k_pcg_onchip" if (dom == "pois_onelaunch" and kind == cg.CGP_COARSE_ONCHIP) else dom,
+                "bound": "hbm", "achieved": kern[dom]["GBps"], "peak": peak, "unit": "GB/s",
                 "frac": round(kern[dom]["GBps"] / peak, 4), "traffic": traffic_tab.get(dom),
-                "bytes_per_launch": kernel_bytes(dom, n, z, t), "avg_launch_us": kern[dom]["avg_us"],
-                "peak_source": peak_kind}
+                "bytes_per_launch": bpl, "avg_launch_us": kern[dom]["avg_us"],
+                "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)"}
+    if dom == "pois_onelaunch":
+        roof_hbm.update({"inner_iterations": its_c, "us_per_iteration": round(kern[dom]["avg_us"] / its_c, 3)})
     roof = roof_hbm
-    # the one-launch coarse solve, when it dominates and runs on chip: its data lives in
-    # shared memory, so its roofline is the shared-memory bandwidth of the cluster's SMs
-    kind, ctas, cl = s.coarse_info()
+    roof_smem = None
+    # the on-chip coarse solve keeps its data in shared memory: its other roofline is the
+    # shared-memory bandwidth of the cluster's SMs (a derived peak)
     top = max(kern, key=lambda k: kern[k]["total_ms"])
     if top == "pois_onelaunch" and kind == cg.CGP_COARSE_ONCHIP:
         _, _, _, stp, _ = s.fields()
@@ -349,7 +362,7 @@ def run_gpu(args, rank, world):
         sm_mhz = head["clocks"].get("sm_mhz") or 2070.0
         smem_peak = 128.0 * cl * sm_mhz * 1e6 / 1e9       # GB/s: 128 B per clock per SM
         ach = smem_bytes / avg_s / 1e9
-        roof = {"kernel": "k_pcg_onchip", "bound": "smem", "achieved": round(ach, 1), "peak": round(smem_peak, 1),
+        roof_smem = {"kernel": "k_pcg_onchip", "bound": "smem", "achieved": round(ach, 1), "peak": round(smem_peak, 1),
                 "unit": "GB/s", "frac": round(ach / smem_peak, 4), "traffic": traffic_tab.get(top),
                 "bytes_per_launch": smem_bytes, "avg_launch_us": kern[top]["avg_us"], "inner_iterations": its,
                 "us_per_iteration": round(kern[top]["avg_us"] / its, 3), "cluster_ctas": cl,
@@ -391,9 +404,9 @@ def run_gpu(args, rank, world):
                    "coarse_vertices": nv_c, "k": w.k, "chi": w.chi, "Re": w.Re, "dt": w.dt,
                    "tol": w.tol_poisson, "mass": args.mass, "parallelism": "replicas" if world > 1 else "single",
                    "l2": "working set %.2f GB > 129 MB L2 (no flush)" % (1e-9 * ws_bytes)},
-        "e2e": e2e, "gpu_launches": int(head["launches"]), "clocks": head["clocks"], "roofline": roof, "roofline_hbm": roof_hbm,
-        "forms": forms, "kernels": kern, "setup_s": {"mesh": round(t_mesh, 3), "assemble": round(head["assemble_s"], 3)},
-        "pcg_hbm": pcg, "batch": batch,
+        "e2e": e2e, "gpu_launches": int(head["launches"]), "clocks": head["clocks"], "roofline": roof,
+        "kernels": kern, "setup_s": {"mesh": round(t_mesh, 3), "assemble": round(head["assemble_s"], 3)},
+        "pcg_hbm": pcg, "batch": batch, "roofline_smem": roof_smem, "forms": forms,
     }
     # the metric's comparison, decomposed: plain FP64 (Jacobi coarse PCG), then FP32 inner /
     # FP64 outer with Jacobi, + the subdomain coarse correction, + the projection guess,
@@ -403,12 +416,13 @@ def run_gpu(args, rank, world):
         out["vs_fp64"] = {k: round(sps[k], 1) for k in ("fp64", "mixed_jacobi", "mixed", "mixed_zero", "mixed_proj",
                                                         "mixed_learned") if k in sps}
         out["vs_fp64"]["headline_over_fp64"] = round(sps[head_form] / sps["fp64"], 3)
-    if cpu_base is not None:
-        out["parity"] = parity
-        out["cpu_baseline"] = cpu_base
     if learned:
         out["learned"] = learned["info"]
         cg.cgp_mlp_destroy(learned["net"])
+    # last, so that a reader of the line's tail sees them
+    if cpu_base is not None:
+        out["parity"] = parity
+        out["cpu_baseline"] = cpu_base
     return out, (w, base)
 
 
@@ -596,6 +610,118 @@ def e1_grid(cg, torch, steps=800, form="fp64"):
     return rows
 
 
+def jobelin_tables(cg, torch, steps=100):
+    """The paper's Sections 3.2-3.3 (Tables 5 and 7) on the GPU: the open-boundary vortex on
+    [0,1]^2 (1024 * 4^j triangles, four per square; standard form, the paper's SCGP) and the
+    vortex on the disk (unstructured, 2304 * 4^j triangles as in Fig. 1; rotational form, the
+    paper's RCGP), Re = 10, dt = 0.01, to t = 1; errors at t = 1, device time per step and
+    speedup = time(k = 0) / time(k) on the same fine mesh."""
+    from workloads import open_square_mesh, disk_mesh
+    rows = []
+    cases = [("open", open_square_mesh(16), cg.CGP_BC_JOBELIN_OPEN, 0, [(2, (0, 1, 2)), (1, (0, 1)), (0, (0,))]),
+             ("disk", disk_mesh(), cg.CGP_BC_JOBELIN_DISK, 1, [(2, (0, 1, 2)), (1, (0, 1))])]
+    for name, base, bc, chi, grid in cases:
+        for lv, ks in grid:
+            t0 = None
+            for k in ks:
+                r = manufactured_run(cg, torch, base, lv, k, 10.0, 0.01, chi, bc, steps)
+                t0 = r["ms_per_step"] if k == 0 else t0
+                r.update({"vortex": name, "M:N": "%d:%d" % (r["fine_triangles"], r["poisson_triangles"]),
+                          "chi": chi, "k": k, "speedup": round(t0 / r["ms_per_step"], 3)})
+                rows.append(r)
+    return rows
+
+
+def c5_study(cg, torch, total_pairs=20000, train_iters=4000, eval_steps=200, eval_seeds=(100, 101, 102, 103)):
+    """The learned initial guess trained and judged as the fifth workload states: 20,000
+    (rhs, guess, increment) triples recorded by the solver (mixed form, projection guess) on
+    the channel with seeds 0-7 (80 %) and on the 512^2 cavity with the pressure 1-3 levels
+    coarser (20 %), one network trained across all of those meshes (Adam, batch 8), then the
+    channel with the held-out seeds 100-103: coarse iterations per step and steps/s over
+    `eval_steps` steps (after 5) for the zero, previous-increment, projection and learned
+    guesses, the coarse solve's device time from one profiled step, and how far the learned
+    form's final fields are from the projection form's (both stop at the same residual)."""
+    from workloads import WORKLOADS, channel_cylinder_mesh
+    from paper_1812_00185_gb300.forms import workload_params
+    from paper_1812_00185_gb300.learned import PairStore, MultiMeshTrainer, init_params
+    ch = WORKLOADS["channel1m_k2"]
+    h = ch.extra.get("h", 0.0084)
+    per_ch = int(0.8 * total_pairs) // 8
+    per_cav = (total_pairs - 8 * per_ch) // 3
+    sources = [(ch, channel_cylinder_mesh(seed=s, h=h), per_ch, "channel seed %d" % s) for s in range(8)]
+    sources += [(WORKLOADS["cavity512_k%d" % k], None, per_cav, "cavity512 k=%d" % k) for k in (1, 2, 3)]
+    t0 = time.time()
+    trainer = MultiMeshTrainer(init_params(0), batch=8)
+    meshes, stores, rec_info = [], [], []
+    for w, base, n, label in sources:
+        base = base if base is not None else w.base_mesh()
+        mesh = cg.Mesh(base.xy, base.tri, base.tag, w.n_levels)
+        rec = cg.Solver(mesh, workload_params(w, "mixed_proj"))
+        store = PairStore(rec.nc, n)
+        store.record(rec, n)
+        rec.close()
+        trainer.add(mesh.handle, w.n_levels - w.k, store)
+        meshes.append(mesh)
+        stores.append(store)
+        rec_info.append({"source": label, "pairs": n, "coarse_vertices": rec.nc})
+    torch.cuda.synchronize()
+    t_rec = time.time() - t0
+    t0 = time.time()
+    hist = trainer.train(train_iters, lr=1e-3, log_every=max(1, train_iters // 8))
+    torch.cuda.synchronize()
+    t_train = time.time() - t0
+    params = trainer.get_params()
+    trainer.close()
+    del stores
+    for m in meshes:
+        m.close()
+    torch.cuda.empty_cache()
+    evals = []
+    for seed in eval_seeds:
+        base = channel_cylinder_mesh(seed=seed, h=h)
+        mesh = cg.Mesh(base.xy, base.tri, base.tag, ch.n_levels)
+        net = cg.cgp_mlp_create(mesh.handle, ch.n_levels - ch.k, 1)
+        cg.cgp_mlp_set_params(net, params)
+        row = {"seed": seed}
+        fields = {}
+        for form in ("mixed_zero", "mixed", "mixed_proj", "mixed_learned"):
+            s = cg.Solver(mesh, workload_params(ch, form))
+            if form == "mixed_learned":
+                cg.cgp_guess_set(s.handle, net)
+            s.step(5)
+            st0 = s.fields()[3]
+            st = torch.cuda.current_stream()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(st)
+            s.step(eval_steps)
+            e1.record(st)
+            torch.cuda.synchronize()
+            U, P, t, st1, rc = s.fields()
+            prof = cg.cgp_profile_step(s.handle)
+            pois = prof.get("pois_onelaunch")
+            row[form] = {"steps_per_s": round(1000.0 * eval_steps / e0.elapsed_time(e1), 1),
+                         "coarse_iters_per_step": round((st1["sum_it_poisson"] - st0["sum_it_poisson"]) / eval_steps, 2),
+                         "coarse_solve_us": round(1000.0 * pois[1] / pois[0], 1) if pois else None,
+                         "status": int(rc)}
+            if form == "mixed_learned":
+                mlp = prof.get("mlp_forward")
+                row[form]["network_us"] = round(1000.0 * mlp[1] / mlp[0], 1) if mlp else None
+            fields[form] = (U, P)
+            s.close()
+        Uj, Pj = fields["mixed_proj"]
+        Ul, Pl = fields["mixed_learned"]
+        row["learned_vs_proj_rel_l2"] = [float(np.linalg.norm(Ul - Uj) / np.linalg.norm(Uj)),
+                                         float(np.linalg.norm(Pl - Pj) / np.linalg.norm(Pj))]
+        evals.append(row)
+        cg.cgp_mlp_destroy(net)
+        mesh.close()
+    return {"metric": "learned initial guess: training on the solver's own pairs, held-out evaluation",
+            "pairs": sum(r["pairs"] for r in rec_info), "record_s": round(t_rec, 1), "train_iters": train_iters,
+            "train_s": round(t_train, 1), "loss": [(int(i), int(k), round(float(l), 5)) for i, k, l in hist],
+            "sources": rec_info, "eval_steps": eval_steps, "eval": evals}
+
+
 def lumped_accuracy(cg, torch, steps=200):
     """Eq. 27 against Eq. 20: the rotational update with the lumped mass matrix (and the
     lumped velocity correction) against the consistent one, on the periodic-forced
@@ -689,6 +815,10 @@ def main():
                     help="print only the paper's Taylor-Green study (Tables 1-4) run on the GPU, one JSON line")
     ap.add_argument("--accuracy", action="store_true",
                     help="print only the Eq. 27 (lumped) against Eq. 20 (consistent) accuracy comparison")
+    ap.add_argument("--jobelin", action="store_true",
+                    help="print only the paper's Jobelin vortex studies (Tables 5 and 7) run on the GPU")
+    ap.add_argument("--c5", action="store_true",
+                    help="print only the learned-guess study: 20k recorded pairs, training, held-out seeds")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "gpu":
         args.warmup = 3
@@ -718,7 +848,7 @@ def main():
         w, _ = workload_problem(args.workload)
         print(json.dumps(mlp_forward_time(cg, torch, w, args.steps)), flush=True)
         return 0
-    if args.e1 or args.accuracy:
+    if args.e1 or args.accuracy or args.jobelin or args.c5:
         if rank != 0:
             return 0
         import torch
@@ -731,6 +861,11 @@ def main():
         if args.accuracy:
             print(json.dumps({"metric": "Eq. 27 vs Eq. 20 accuracy (periodic Taylor-Green 512^2)",
                               "rows": lumped_accuracy(cg, torch)}), flush=True)
+        if args.jobelin:
+            print(json.dumps({"metric": "Jobelin vortex errors and CGP speedup (paper Sections 3.2-3.3)",
+                              "rows": jobelin_tables(cg, torch)}), flush=True)
+        if args.c5:
+            print(json.dumps(c5_study(cg, torch)), flush=True)
         return 0
     if args.pcg_only:
         if rank != 0:

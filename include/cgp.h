@@ -62,9 +62,10 @@ enum {
     CGP_BC_JOBELIN_OPEN = 5, /* Section 3.2 vortex, u = sin x sin(y+t), v = cos x cos(y+t), p = cos x sin(y+t), with
                                 its body force: velocity data on the VEL_DIR vertices, and on the PHI_ZERO
                                 vertices (the traction boundary, the y-axis x = 0 of [0,1]^2) the traction of
-                                Eq. 4 and the pressure from the closed form: Eq. 21 gains
-                                dt * int_{Gamma_N} t psi_i ds (t linear on each boundary edge), Eq. 23 takes
-                                phi = p(t^{n+1}) - P^n there (restrict_mode INJECT only) */
+                                Eq. 4 and the pressure from the closed form, Eq. 11 read at t^{n+1}: Eq. 21
+                                gains dt * int_{Gamma_N} (t + (p^{n+1} - P^n) n) psi_i ds (linear on each
+                                boundary edge), Eq. 23 takes phi = p^{n+1} - P^n there (restrict_mode
+                                INJECT only) */
     CGP_BC_JOBELIN_DISK = 6  /* Section 3.3 vortex, u = sin(x+t) sin(y+t), v = cos(x+t) cos(y+t), p = cos(x-y+t),
                                 with its body force; velocity data on the VEL_DIR vertices (the whole
                                 boundary of the disk) */

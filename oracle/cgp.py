@@ -29,12 +29,16 @@ Readings of points the paper leaves open (listed with the design notes):
 * The mean of nothing else is touched: P carries whatever constant the
   Phi updates give.
 * Traction data on the natural boundary Gamma_N (Eq. 11; nonzero only for the open-boundary
-  vortex of Section 3.2): Eq. 21's right-hand side gains dt * int_{Gamma_N} t psi_i ds, with
-  t interpolated linearly between the vertices of each boundary edge (the boundary mass
-  matrix l/6 [[2, 1], [1, 2]] of the edge times the nodal values).  Where the problem
-  prescribes the pressure on Gamma_N, Eq. 14 is read with that data: phi = p(t^{n+1}) - p^n
-  at the coarse Gamma_N vertices (lifted into the right-hand side of Eq. 23), so that the
-  pressure follows the prescribed values; otherwise phi = 0 there.
+  vortex of Section 3.2).  Eq. 11 leaves the time level of its pressure open; it is read at
+  t^{n+1}, -p^{n+1} n + grad u~ . n / Re = t^{n+1}, with p^{n+1} the pressure prescribed on
+  Gamma_N.  The weak pressure term of Eq. 21 carries p^n, so Eq. 21's right-hand side gains
+  dt * int_{Gamma_N} (t + (p^{n+1} - p^n) n) psi_i ds, the integrand interpolated linearly
+  between the vertices of each boundary edge (the boundary mass matrix l/6 [[2, 1], [1, 2]]
+  of the edge times the nodal values).  (With p^n in Eq. 11 the scheme stays first order in
+  time there; at t^{n+1} the velocity error on the paper's mesh falls ~25x.)  Eq. 14 is read
+  with the same data: phi = p(t^{n+1}) - p^n at the coarse Gamma_N vertices (lifted into the
+  right-hand side of Eq. 23), so that the pressure follows the prescribed values; where no
+  pressure is prescribed, phi = 0 there and t = 0 (the channel's outflow).
 
 Solves use scipy's sparse LU (a library primitive), so each result is the
 exact discrete solution up to rounding.
@@ -137,6 +141,9 @@ class CGPOracle:
         F = flows.body_force(self.bc, f.xy, t_new, Re, self.bc_param)
         hist = 2.0 * U - 0.5 * Uprev
         T = flows.traction(self.bc, f.xy, t_new, Re, self.bc_param)
+        pn = flows.natural_pressure(self.bc, f.xy, t_new, Re, self.bc_param)
+        if pn is not None:
+            T = T + (pn - P)[:, None] * flows.natural_normal(self.bc, f.xy)
         bx = dt * (Cx.T @ P) + M @ (dt * F[:, 0] + hist[:, 0]) + dt * (self.BN @ T[:, 0])
         by = dt * (Cy.T @ P) + M @ (dt * F[:, 1] + hist[:, 1]) + dt * (self.BN @ T[:, 1])
         uD = flows.dirichlet_value(self.bc, f.xy, t_new, Re, self.bc_param)

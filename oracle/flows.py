@@ -125,6 +125,14 @@ def traction(kind, xy, t, Re, bc_param=(1.0, 0.0, 0.0, 0.0)):
     return out
 
 
+def natural_normal(kind, xy):
+    """Outward unit normal on the natural boundary (the y-axis of the open-boundary vortex)."""
+    n = np.zeros((xy.shape[0], 2))
+    if kind == BC_JOBELIN_OPEN:
+        n[:, 0] = -1.0
+    return n
+
+
 def natural_pressure(kind, xy, t, Re, bc_param=(1.0, 0.0, 0.0, 0.0)):
     """Pressure prescribed on the natural boundary at time t, or None (then it stays 0 there,
     as on the channel's outflow)."""

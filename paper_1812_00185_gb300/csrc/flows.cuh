@@ -158,6 +158,12 @@ __device__ __forceinline__ double natural_pressure(const BcParams& bc, double x,
     return jobelin_point(CGP_BC_JOBELIN_OPEN, x, y, t).p;
 }
 
+// outward unit normal of Gamma_N (the y-axis)
+__device__ __forceinline__ void natural_normal(const BcParams& bc, double x, double y, double& nx, double& ny) {
+    nx = -1.0;
+    ny = 0.0;
+}
+
 inline BcParams bc_from(const cgp_params& p) {
     BcParams b;
     b.kind = p.bc_kind;

@@ -471,8 +471,9 @@ void MlpBuffers::carve(Carve& cv, int n_, int batch) {
     params = cv.take<float>(kMlpParams);
 }
 
-int mlp_forward(const MlpBuffers& B, const Level& L, const double* r, const double* q, int batch, double* pred,
-                cudaStream_t st) {
+// the training forward pass: every activation kept (feature-major) for mlp_backward
+static int mlp_forward_train(const MlpBuffers& B, const Level& L, const double* r, const double* q, int batch,
+                             double* pred, cudaStream_t st) {
     const int n = B.n;
     const int64_t nb = (int64_t)n * batch;
     const int g = blocks_for(nb);
@@ -562,6 +563,14 @@ extern "C" int cgp_mlp_create(const cgp_mesh* mesh, int32_t level, int32_t max_b
         delete m;
         return CGP_ECUDA;
     }
+    {
+        const int rc = mlp_infer_setup();
+        if (rc != CGP_OK) {
+            cudaFree(m->mem);
+            delete m;
+            return rc;
+        }
+    }
     *out = m;
     return CGP_OK;
 }
@@ -638,7 +647,7 @@ static int mlp_backward(cgp_mlp* m, const double* r, const double* q, const doub
     MlpBuffers& B = m->B;
     const int n = B.n;
     const int64_t nb = (int64_t)n * batch;
-    CGP_TRY(mlp_forward(B, L, r, q, batch, nullptr, st));
+    CGP_TRY(mlp_forward_train(B, L, r, q, batch, nullptr, st));
     const int g = blocks_for(nb), g128 = blocks_for(nb, 128);
     const int nblk = (int)((nb + kRowsPerBlock - 1) / kRowsPerBlock);
     int gl = (int)(nb / kBlock + 1);

@@ -36,8 +36,11 @@ struct MlpBuffers {
     static size_t bytes(int n, int batch);
 };
 
-// forward pass for `batch` samples of (r, q) (each n doubles, consecutive); pred may be null
+// inference forward pass (mlp_infer.cu, tensor-core 64 -> 64 layer) for `batch` samples of
+// (r, q) (each n doubles, consecutive) into pred; mlp_infer_setup (once per process, before
+// any capture) raises the shared-memory limit of its layer-2 kernel
 int mlp_forward(const MlpBuffers& B, const Level& L, const double* r, const double* q, int batch, double* pred,
                 cudaStream_t st);
+int mlp_infer_setup();
 
 }  // namespace cgp

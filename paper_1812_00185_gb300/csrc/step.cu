@@ -56,7 +56,9 @@ __global__ void k_mom_prep(int nf, const double* __restrict__ U, const double* _
         double2 u = reinterpret_cast<const double2*>(U)[i];
         double2 up = reinterpret_cast<const double2*>(Uprev)[i];
         double fx = 0.0, fy = 0.0;
-        if (bc.kind == CGP_BC_TG_PERIODIC || bc.kind == CGP_BC_USER) body_force(bc, i, xy[2 * i], xy[2 * i + 1], tn, fx, fy);
+        if (bc.kind == CGP_BC_TG_PERIODIC || bc.kind == CGP_BC_USER || bc.kind == CGP_BC_JOBELIN_OPEN ||
+            bc.kind == CGP_BC_JOBELIN_DISK)
+            body_force(bc, i, xy[2 * i], xy[2 * i + 1], tn, fx, fy);
         reinterpret_cast<double2*>(w)[i] = make_double2(2.0 * u.x - up.x, 2.0 * u.y - up.y);
         reinterpret_cast<double2*>(h)[i] =
             make_double2(dt * fx + (2.0 * u.x - 0.5 * up.x), dt * fy + (2.0 * u.y - 0.5 * up.y));
@@ -148,12 +150,23 @@ __global__ void __launch_bounds__(kBlock) k_mom_assemble(int nf, const int32_t* 
             dinv[i] = 1.0 / A[e0 + 32 * diag_slot];
         }
         if ((tag[i] & CGP_PHI_ZERO) && has_natural_data(bc)) {
-            // traction boundary (Eq. 11): dt int_{Gamma_N} t psi_i ds over the boundary edges
-            // (i, j), j on Gamma_N too, an edge being on the boundary when one triangle has it;
-            // t linear on the edge: l/6 (2 t_i + t_j)
+            // traction boundary (Eq. 11 at t^{n+1}: -p^{n+1} n + grad u~ . n / Re = t, with the
+            // prescribed p^{n+1}; the weak pressure term above carries P^n): dt int_{Gamma_N}
+            // (t + (p^{n+1} - P^n) n) psi_i ds over the boundary edges (i, j), j on Gamma_N
+            // too, an edge being on the boundary when one triangle has it; the integrand linear
+            // on the edge: l/6 (2 t_i + t_j)
+            auto tr = [&](int v, double& tx, double& ty) {
+                const double xv = xy[2 * v], yv = xy[2 * v + 1];
+                double nx, ny;
+                natural_traction(bc, xv, yv, tn, tx, ty);
+                natural_normal(bc, xv, yv, nx, ny);
+                const double dp = natural_pressure(bc, xv, yv, tn) - P[v];
+                tx += dp * nx;
+                ty += dp * ny;
+            };
             const double xi = xy[2 * i], yi = xy[2 * i + 1];
             double ti_x, ti_y;
-            natural_traction(bc, xi, yi, tn, ti_x, ti_y);
+            tr(i, ti_x, ti_y);
             for (int q = rb; q < re; ++q) {
                 const int j = col[q];
                 if (j == i || !(tag[j] & CGP_PHI_ZERO)) continue;
@@ -165,7 +178,7 @@ __global__ void __launch_bounds__(kBlock) k_mom_assemble(int nf, const int32_t* 
                 if (owners != 1) continue;
                 const double xj = xy[2 * j], yj = xy[2 * j + 1];
                 double tj_x, tj_y;
-                natural_traction(bc, xj, yj, tn, tj_x, tj_y);
+                tr(j, tj_x, tj_y);
                 const double c = dt * hypot(xj - xi, yj - yi) / 6.0;
                 bx += c * (2.0 * ti_x + tj_x);
                 by += c * (2.0 * ti_y + tj_y);

@@ -73,3 +73,60 @@ def init_params(seed=0):
         p[o:o + w.size] = w.ravel()
         o += w.size + fout          # biases stay zero
     return p
+
+
+class MultiMeshTrainer:
+    """One network trained on pairs recorded on several meshes: one cgp_mlp per mesh level
+    (each owns that level's adjacency and activation buffers); before every Adam step the
+    weights and the Adam state move to the network of the mesh the batch comes from
+    (cgp_mlp_copy_state), so the sequence of steps is that of a single network."""
+
+    def __init__(self, params, batch=8):
+        self.batch = batch
+        self.params = params
+        self.nets, self.stores = [], []
+        self.current = None
+
+    def add(self, mesh_handle, level, store):
+        net = cg.cgp_mlp_create(mesh_handle, level, self.batch)
+        cg.cgp_mlp_set_params(net, self.params)
+        self.nets.append(net)
+        self.stores.append(store)
+        if self.current is None:
+            self.current = 0
+
+    def train(self, iters, lr=1e-3, seed=0, log_every=0):
+        """Adam steps on random batches; a batch's mesh is drawn in proportion to its pairs."""
+        import torch
+        rng = np.random.default_rng(seed)
+        counts = np.array([s.count for s in self.stores], dtype=np.float64)
+        prob = counts / counts.sum()
+        bufs = {}
+        hist = []
+        for it in range(iters):
+            k = int(rng.choice(len(self.stores), p=prob))
+            st = self.stores[k]
+            if k != self.current:
+                cg.cgp_mlp_copy_state(self.nets[k], self.nets[self.current])
+                self.current = k
+            if st.n not in bufs:
+                rb = torch.empty((self.batch, st.n), dtype=torch.float64, device="cuda")
+                bufs[st.n] = (rb, torch.empty_like(rb), torch.empty_like(rb))
+            rb, qb, tb = bufs[st.n]
+            idx = torch.as_tensor(rng.integers(0, st.count, size=self.batch), device="cuda")
+            torch.index_select(st.r[:st.count], 0, idx, out=rb)
+            torch.index_select(st.q[:st.count], 0, idx, out=qb)
+            torch.index_select(st.t[:st.count], 0, idx, out=tb)
+            want = (log_every and it % log_every == 0) or it == iters - 1
+            loss = cg.cgp_mlp_train_step(self.nets[k], rb, qb, tb, self.batch, lr, want_loss=want)
+            if want:
+                hist.append((it, k, loss))
+        return hist
+
+    def get_params(self):
+        return cg.cgp_mlp_get_params(self.nets[self.current])
+
+    def close(self):
+        for net in self.nets:
+            cg.cgp_mlp_destroy(net)
+        self.nets = []

@@ -9,11 +9,9 @@
 * The CGP step converges to the closed forms, and with the pressure increment one level
   coarser the errors stay close to the k = 0 ones (the paper's Tables 5 and 7 report
   changes below 1 % on finer meshes; the bounds below are this small mesh's).  Disk
-  (Dirichlet data everywhere):
-  velocity error falling at second order under refinement.  Open boundary: the standard
-  incremental scheme with a traction boundary is first order in time (the splitting error
-  of the boundary pressure), so the velocity error falls in proportion to dt on a fine mesh
-  and the pressure error (its mean removed) falls under refinement at a small dt.
+  (Dirichlet data everywhere): velocity error falling at second order under refinement.
+  Open boundary (the traction condition read at t^{n+1} with the prescribed pressure): both
+  errors falling under refinement at a small dt, the velocity's at nearly second order.
 """
 
 import numpy as np
@@ -96,17 +94,17 @@ def _errors(base, n_levels, k, kind, chi, steps, dt=0.01, Re=10.0):
 
 def test_open_boundary_vortex_converges_and_keeps_accuracy_under_coarsening():
     base = open_square_mesh(4)                     # 64 triangles; levels 1..3: 256..4096
-    et = np.array([_errors(base, 3, 0, flows.BC_JOBELIN_OPEN, 0, n, dt=0.1 / n) for n in (10, 20, 40)])
-    rate_t = np.log2(et[:-1] / et[1:])
-    assert (rate_t[:, 0] > 0.8).all(), (et, rate_t)          # velocity: first order in dt
     eh = np.array([_errors(base, lv, 0, flows.BC_JOBELIN_OPEN, 0, 40, dt=0.0025) for lv in (1, 2, 3)])
-    assert eh[0, 1] > eh[1, 1] > eh[2, 1], eh                # pressure falls under refinement
-    # one level of coarsening on this small mesh (4096:1024): velocity within 15 %; the
-    # pressure (whose Gamma_N values at the fine midpoints are prolonged coarse data) within 60 %
-    for chi in (0, 1):
+    rate = np.log2(eh[:-1] / eh[1:])
+    assert (rate[:, 0] > 1.5).all(), (eh, rate)              # velocity: nearly second order
+    assert (rate[:, 1] > 1.4).all(), (eh, rate)              # pressure
+    # one level of coarsening on this small mesh (4096:1024): the rotational form keeps both
+    # errors within 10 %; the standard form the velocity within 25 % and the pressure (whose
+    # Gamma_N values at the fine midpoints are prolonged coarse data) within 70 %
+    for chi, bu, bp in ((0, 1.25, 1.7), (1, 1.1, 1.1)):
         e0 = np.array(_errors(base, 3, 0, flows.BC_JOBELIN_OPEN, chi, 20, dt=0.005))
         e1 = np.array(_errors(base, 3, 1, flows.BC_JOBELIN_OPEN, chi, 20, dt=0.005))
-        assert e1[0] < 1.15 * e0[0] and e1[1] < 1.6 * e0[1], (chi, e1, e0)
+        assert e1[0] < bu * e0[0] and e1[1] < bp * e0[1], (chi, e1, e0)
 
 
 def test_disk_vortex_converges_and_keeps_accuracy_under_coarsening():
