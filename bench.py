@@ -525,9 +525,11 @@ def batch_throughput(cg, torch, n_inst, steps, warmup):
     t0 = time.time()
     b = cg.cgp_batch_create(solvers)
     info = cg.cgp_batch_info(b)
+    mode = "whole step" if cg.cgp_batch_mode(b) == cg.CGP_BATCH_WHOLE_STEP else "graph branches"
     t_tune = time.time() - t0
     cg.cgp_batch_step(b, warmup)
     torch.cuda.synchronize()
+    st_before = [s.fields()[3] for s in solvers]
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record()
     cg.cgp_batch_step(b, steps)
@@ -536,9 +538,24 @@ def batch_throughput(cg, torch, n_inst, steps, warmup):
     ms = ev0.elapsed_time(ev1) / steps
     its = [s.fields()[3] for s in solvers]
     bad = sum(1 for st in its if st["status"] != 0)
-    out = {"instances": n_inst, "fine_vertices": nf_tot, "coarse_vertices": nc_tot, "steps": steps,
+    # aggregate algorithmic HBM bytes of the timed steps, from the per-kernel models above
+    # (BiCGStab iteration 24 z + 392 n; assembly 44 z + 364 n; coarse FP32-inner PCG iteration
+    # 8 z_c + 56 n_c; Chebyshev step 12 z + 96 n (two components) / 12 z + 48 n (one);
+    # right-hand sides, prolongation and the update 40 z + 150 n), per instance and step
+    tot_bytes = 0.0
+    for s, st0, st1 in zip(solvers, st_before, its):
+        nf, nc, zf, zc = cg.cgp_solver_info(s.handle)
+        per = lambda k: (st1["sum_it_" + k] - st0["sum_it_" + k])
+        tot_bytes += per("mom") * (24 * zf + 392 * nf) + per("poisson") * (8 * zc + 56 * nc)
+        tot_bytes += per("corr") * (12 * zf + 96 * nf) + per("mass") * (12 * zf + 48 * nf)
+        tot_bytes += (st1["steps"] - st0["steps"]) * (84 * zf + 514 * nf)
+    peak, _ = _peaks()
+    gbps = tot_bytes / (ms * steps * 1e-3) / 1e9
+    out = {"instances": n_inst, "form": mode, "fine_vertices": nf_tot, "coarse_vertices": nc_tot, "steps": steps,
            "ms_per_batch_step": round(ms, 4), "instance_steps_per_s": round(1000.0 * n_inst / ms, 1),
            "fine_vertex_steps_per_s": round(1000.0 * nf_tot / ms, 1), "autotune": info,
+           "roofline": {"bound": "hbm", "achieved": round(gbps, 1), "peak": peak, "unit": "GB/s",
+                        "frac": round(gbps / peak, 4), "bytes_per_batch_step": round(tot_bytes / steps)},
            "setup_s": round(t_setup, 2), "tune_and_capture_s": round(t_tune, 2), "instances_not_converged": bad}
     cg.cgp_batch_destroy(b)
     for s in solvers:
@@ -793,7 +810,7 @@ def main():
                     choices=["fp64", "mixed", "learned", "mixed_learned", "mixed_zero", "mixed_jacobi", "mixed_proj",
                              "fp64_proj"])
     ap.add_argument("--batch", type=int, default=256, help="instances of the batched form (0: skip)")
-    ap.add_argument("--batch-steps", type=int, default=10)
+    ap.add_argument("--batch-steps", type=int, default=100)
     ap.add_argument("--train-pairs", type=int, default=150)
     ap.add_argument("--train-iters", type=int, default=400)
     ap.add_argument("--pcg-n", type=int, nargs="+", default=[1024, 2048, 4096],

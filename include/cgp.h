@@ -289,18 +289,33 @@ void cgp_solver_destroy(cgp_solver* s);
 
 /* ---- batches of independent instances (not in the paper) ----
  * cgp_batch_create groups assembled solvers (any meshes and parameters; each keeps its own
- * workspace and state) into one CUDA graph per step: every instance's momentum solve and
- * coarse right-hand side on its own stream, then ONE persistent launch that solves all the
- * coarse Poisson problems (thread-block clusters take instances from a queue, largest
- * first, and reduce through distributed shared memory), then every instance's correction
- * and pressure update.  cluster_size (0 = autotune, else 1, 2, 4, 8) and threads (0 =
- * autotune, else 256, 512, 1024) fix the persistent launch's shape; the autotuner times
- * each candidate on the instances' first coarse problems, restoring their state after each
- * trial.  The batch allocates its own device memory (launch arguments, a queue counter and
- * the saved coarse state); the solvers must outlive it.  Synchronises `stream`. */
+ * workspace and state).  Two forms:
+ *  - whole step (CGP_BATCH_WHOLE_STEP, the default when every instance qualifies: injection
+ *    restriction, a zero or previous-increment coarse guess, a one-launch coarse solver):
+ *    every batched step is ONE persistent launch in which thread-block clusters take
+ *    instances from a queue, largest first, and run each instance's whole step of Eqs. 21-26
+ *    (momentum rows and FP64 BiCGStab, coarse right-hand side and the instance's coarse PCG,
+ *    prolongation, Chebyshev mass solves of Eqs. 25-26 with the eigenvalue bounds [1/2, 2] of
+ *    Jacobi-scaled P1 mass matrices, pressure update), reducing through distributed shared
+ *    memory; the launch is captured in a CUDA graph;
+ *  - graph branches (CGP_BATCH_BRANCHES): one CUDA graph per step with every instance's
+ *    momentum solve and coarse right-hand side on its own stream, ONE persistent launch for
+ *    all the coarse Poisson problems, then every instance's correction and update.
+ * cluster_size (0 = autotune, else 1, 2, 4, 8) and threads (0 = autotune, else 256, 512,
+ * 1024) fix the persistent launch's shape; the autotuner times each candidate on the
+ * instances' first step (whole step) or first coarse problems (branches), restoring their
+ * state after each trial.  The batch allocates its own device memory (launch arguments, a
+ * queue counter and the saved state); the solvers must outlive it.  Synchronises `stream`. */
 typedef struct cgp_batch cgp_batch;
+enum { CGP_BATCH_AUTO = 0, CGP_BATCH_WHOLE_STEP = 1, CGP_BATCH_BRANCHES = 2 };
 int cgp_batch_create(cgp_solver* const* solvers, int32_t n, int32_t cluster_size, int32_t threads,
                      cgp_stream_t stream, cgp_batch** out);
+/* The same with the form chosen (CGP_BATCH_*); CGP_EINVAL if WHOLE_STEP is asked for and an
+ * instance does not qualify. */
+int cgp_batch_create_mode(cgp_solver* const* solvers, int32_t n, int32_t cluster_size, int32_t threads, int32_t mode,
+                          cgp_stream_t stream, cgp_batch** out);
+/* The form a batch runs (CGP_BATCH_WHOLE_STEP or CGP_BATCH_BRANCHES). */
+int cgp_batch_mode(const cgp_batch* b, int32_t* mode);
 /* n_steps batched steps (graph launches on `stream`); per-instance results and stats via
  * cgp_get_fields on each solver. */
 int cgp_batch_step(cgp_batch* b, int32_t n_steps, cgp_stream_t stream);

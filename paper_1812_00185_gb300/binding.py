@@ -19,6 +19,7 @@ CGP_OK, CGP_EINVAL, CGP_ENOTCONV, CGP_EBREAKDOWN, CGP_ENONFINITE, CGP_ETIMEOUT, 
 CGP_VEL_DIR, CGP_PHI_ZERO = 1, 2
 CGP_BC_CAVITY, CGP_BC_CHANNEL, CGP_BC_TG, CGP_BC_TG_PERIODIC, CGP_BC_USER = 0, 1, 2, 3, 4
 CGP_BC_JOBELIN_OPEN, CGP_BC_JOBELIN_DISK = 5, 6
+CGP_BATCH_AUTO, CGP_BATCH_WHOLE_STEP, CGP_BATCH_BRANCHES = 0, 1, 2
 CGP_RESTRICT_INJECT, CGP_RESTRICT_PT = 0, 1
 CGP_PRECOND_AUTO, CGP_PRECOND_JACOBI, CGP_PRECOND_COARSE = 0, 1, 2
 CGP_FP64, CGP_MIXED = 0, 1
@@ -110,6 +111,8 @@ _SIGS = {
     "cgp_guess_set": (c_int32, [c_void_p, c_void_p, c_void_p]),
     "cgp_mlp_destroy": (None, [c_void_p]),
     "cgp_batch_create": (c_int32, [c_void_p, c_int32, c_int32, c_int32, c_void_p, POINTER(c_void_p)]),
+    "cgp_batch_create_mode": (c_int32, [c_void_p, c_int32, c_int32, c_int32, c_int32, c_void_p, POINTER(c_void_p)]),
+    "cgp_batch_mode": (c_int32, [c_void_p, POINTER(c_int32)]),
     "cgp_batch_step": (c_int32, [c_void_p, c_int32, c_void_p]),
     "cgp_batch_info": (c_int32, [c_void_p, POINTER(c_int32), POINTER(c_int32), POINTER(c_int32), c_void_p,
                                  c_int32]),
@@ -392,11 +395,24 @@ def cgp_pcg_sell_noalloc(n, nslices, sell_ptr, sell_col, val, dinv, b, x, tol, m
 
 
 # ---------------------------------------------------------------- batches
-def cgp_batch_create(solvers, cluster_size=0, threads=0, stream=None):
+def cgp_batch_create(solvers, cluster_size=0, threads=0, stream=None, mode=None):
+    """mode: None = the library's default (CGP_BATCH_AUTO), else CGP_BATCH_WHOLE_STEP or
+    CGP_BATCH_BRANCHES."""
     arr = (c_void_p * len(solvers))(*[s.handle if hasattr(s, "handle") else s for s in solvers])
     out = c_void_p()
-    _check(load().cgp_batch_create(arr, len(solvers), int(cluster_size), int(threads), _stream(stream), byref(out)))
+    if mode is None:
+        _check(load().cgp_batch_create(arr, len(solvers), int(cluster_size), int(threads), _stream(stream),
+                                       byref(out)))
+    else:
+        _check(load().cgp_batch_create_mode(arr, len(solvers), int(cluster_size), int(threads), int(mode),
+                                            _stream(stream), byref(out)))
     return out
+
+
+def cgp_batch_mode(batch):
+    m = c_int32()
+    _check(load().cgp_batch_mode(batch, byref(m)))
+    return m.value
 
 
 def cgp_batch_step(batch, n_steps, stream=None):

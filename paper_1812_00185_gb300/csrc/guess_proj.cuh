@@ -11,8 +11,8 @@
 // pairs, one new row per step.  The window slides (the oldest pair is replaced).
 //
 // Per step: one kernel forms f = X^T b (and stores b in the slot the new pair will take) and,
-// in its last block, solves the small system with a truncated pseudo-inverse of G in FP64 on
-// one thread (see proj_solve_small); one kernel forms x0 = X c; after the solve, one kernel stores the new
+// in its last block, solves the small system by a pivoted, truncated Cholesky factorisation
+// in FP64 on one thread (see proj_solve_small); one kernel forms x0 = X c; after the solve, one kernel stores the new
 // solution and adds its row of G.  CGP_GUESS_LEARNED uses the same x0 as the network's
 // second input and as the first of the two guesses the one-launch solve combines.
 #pragma once
@@ -32,60 +32,62 @@ struct ProjState {
     int pad[2];
 };
 
-// c = G^+ f over the first m slots (one thread): G (symmetrised) = V diag(lambda) V^T by
-// cyclic Jacobi rotations, then c = sum over lambda_i > thr of v_i (v_i^T f) / lambda_i.  The
+// c = a truncated solution of G c = f over the first m slots (one thread), by a Cholesky
+// factorisation with diagonal pivoting: each step takes the slot whose Schur-complement
+// diagonal is largest and stops once that is <= thr = max(tol, 1e-12) * max_i G_ii.  The
 // stored G equals X^T K X only to the solve's tolerance (b_j = K x_j + r_j), and consecutive
-// increments are nearly dependent, so directions with lambda_i <= thr = max(tol, 1e-12)
-// lambda_max are noise and are dropped (a truncated pseudo-inverse, not a shifted solve).
+// increments are nearly dependent, so the slots left out are those the kept ones already
+// span to within that noise (a rank-revealing truncation); their coefficients are 0.  About
+// m^3 / 3 operations on registers and local arrays of 8 x 8.
 __device__ inline void proj_solve_small(ProjState* ps, const double* f, int m, double tol) {
-    double a[kProjL][kProjL], v[kProjL][kProjL];
-    for (int i = 0; i < kProjL; ++i)
+    double g[kProjL][kProjL], L[kProjL][kProjL], y[kProjL], c[kProjL], d[kProjL];
+    int piv[kProjL], used[kProjL];
+    double dmax = 0.0;
+    for (int i = 0; i < kProjL; ++i) {
         for (int j = 0; j < kProjL; ++j) {
-            a[i][j] = (i < m && j < m) ? 0.5 * (ps->G[i][j] + ps->G[j][i]) : 0.0;
-            v[i][j] = i == j ? 1.0 : 0.0;
+            g[i][j] = (i < m && j < m) ? 0.5 * (ps->G[i][j] + ps->G[j][i]) : 0.0;
+            L[i][j] = 0.0;
         }
-    for (int sweep = 0; sweep < 12; ++sweep) {
-        double off = 0.0, dia = 0.0;
-        for (int i = 0; i < m; ++i) {
-            dia += a[i][i] * a[i][i];
-            for (int j = i + 1; j < m; ++j) off += a[i][j] * a[i][j];
-        }
-        if (!(off > 1e-30 * dia)) break;
-        for (int p = 0; p < m; ++p)
-            for (int q = p + 1; q < m; ++q) {
-                if (a[p][q] == 0.0) continue;
-                // rotation that zeroes a[p][q] (the smaller root of t^2 + 2 theta t - 1 = 0)
-                const double theta = (a[q][q] - a[p][p]) / (2.0 * a[p][q]);
-                const double t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
-                const double c = 1.0 / sqrt(t * t + 1.0), s = t * c;
-                for (int k = 0; k < m; ++k) {
-                    const double akp = a[k][p], akq = a[k][q];
-                    a[k][p] = c * akp - s * akq;
-                    a[k][q] = s * akp + c * akq;
-                }
-                for (int k = 0; k < m; ++k) {
-                    const double apk = a[p][k], aqk = a[q][k];
-                    a[p][k] = c * apk - s * aqk;
-                    a[q][k] = s * apk + c * aqk;
-                }
-                for (int k = 0; k < m; ++k) {
-                    const double vkp = v[k][p], vkq = v[k][q];
-                    v[k][p] = c * vkp - s * vkq;
-                    v[k][q] = s * vkp + c * vkq;
-                }
-            }
+        used[i] = i >= m;
+        c[i] = 0.0;
+        d[i] = g[i][i];   // Schur-complement diagonal, updated as columns are taken
+        if (i < m) dmax = fmax(dmax, g[i][i]);
     }
-    double lmax = 0.0;
-    for (int i = 0; i < m; ++i) lmax = fmax(lmax, a[i][i]);
-    const double thr = fmax(tol, 1e-12) * lmax;
-    double c[kProjL];
-    for (int i = 0; i < kProjL; ++i) c[i] = 0.0;
-    for (int e = 0; e < m; ++e) {
-        if (!(a[e][e] > thr)) continue;
-        double w = 0.0;
-        for (int i = 0; i < m; ++i) w += v[i][e] * f[i];
-        w /= a[e][e];
-        for (int i = 0; i < m; ++i) c[i] += v[i][e] * w;
+    const double thr = fmax(tol, 1e-12) * dmax;
+    int r = 0;
+    for (int k = 0; k < m; ++k) {
+        int best = -1;
+        double bd = thr;
+        for (int i = 0; i < m; ++i) {
+            if (!used[i] && d[i] > bd) {
+                bd = d[i];
+                best = i;
+            }
+        }
+        if (best < 0) break;
+        used[best] = 1;
+        piv[k] = best;
+        const double lkk = sqrt(bd);
+        L[best][k] = lkk;
+        for (int i = 0; i < m; ++i) {
+            if (used[i]) continue;
+            double s = g[i][best];
+            for (int p = 0; p < k; ++p) s -= L[i][p] * L[best][p];
+            L[i][k] = s / lkk;
+            d[i] -= L[i][k] * L[i][k];
+        }
+        r = k + 1;
+    }
+    // (L L^T) restricted to the pivots: forward then back substitution
+    for (int k = 0; k < r; ++k) {
+        double s = f[piv[k]];
+        for (int p = 0; p < k; ++p) s -= L[piv[k]][p] * y[p];
+        y[k] = s / L[piv[k]][k];
+    }
+    for (int k = r - 1; k >= 0; --k) {
+        double s = y[k];
+        for (int p = k + 1; p < r; ++p) s -= L[piv[p]][k] * c[piv[p]];
+        c[piv[k]] = s / L[piv[k]][k];
     }
     for (int i = 0; i < kProjL; ++i) ps->c[i] = isfinite(c[i]) ? c[i] : 0.0;
 }

@@ -141,6 +141,13 @@ void fill_coarse_args(Solver& s, void* dst);
 int batch_clusters(int csize, int threads, int* nclusters);
 int launch_batch_coarse(const void* d_args, int ninst, unsigned int* queue, int csize, int threads, int nclusters,
                         cudaStream_t st);
+// the batched whole step (batch_step.cuh): one persistent clustered launch for every phase
+size_t batch_step_args_size();
+bool batch_step_eligible(const Solver& s);
+void fill_batch_step_args(Solver& s, void* dst);
+int batch_step_clusters(int csize, int threads, int* nclusters);
+int launch_batch_step(const void* d_args, int ninst, unsigned int* queue, int csize, int threads, int nclusters,
+                      cudaStream_t st);
 int choose_coarse_solver(Solver& s, cudaStream_t st);
 int init_state(Solver* s, cudaStream_t st);
 

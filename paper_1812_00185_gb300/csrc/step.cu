@@ -10,6 +10,8 @@
 #include "flows.cuh"
 #include "guess_proj.cuh"
 #include "solver.cuh"
+#include "step_rows.cuh"
+#include "batch_step.cuh"
 
 namespace cgp {
 
@@ -65,18 +67,7 @@ __global__ void k_mom_prep(int nf, const double* __restrict__ U, const double* _
     }
 }
 
-// Row i of the momentum system of Eq. 21:
-//   A = 3/2 M + dt N(w) + dt/Re K,  N_ij = sum_T |T|/12 (W_T + w_i) . grad psi_j
-//   b = dt (Cx^T P, Cy^T P) + M h     (pressure term in weak form, see the readings)
-// Dirichlet rows: s_ii times the identity row, b = s_ii u_D(t^{n+1}), with s_ii the diagonal
-// of S = 3/2 M + dt/Re K at that row: the same solution as the plain identity row, but rows
-// of one scale, so that the relative residual test ||b - A x|| <= tol ||b|| measures the
-// interior equations (with identity rows the O(1) boundary values dominate ||b|| against
-// interior rows of the size of the mass matrix, O(h^2), and the test passes while the
-// interior equations hold only to ~1e-4).  Also x0 = w (u_D on Dirichlet rows), dinv.
-// Rows of at most kAsmRow entries are accumulated in shared memory ([entry][thread], so the
-// lanes of a warp hit distinct banks) and written to A once; longer rows add into A directly.
-constexpr int kAsmRow = 16;
+// Eq. 21's matrix and right-hand side, one thread per row (step_rows.cuh)
 __global__ void __launch_bounds__(kBlock) k_mom_assemble(int nf, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
                                const int32_t* __restrict__ sell_ptr, const int32_t* __restrict__ vt_ptr, const int32_t* __restrict__ vt_list,
                                const int32_t* __restrict__ tri, const double* __restrict__ geo,
@@ -89,104 +80,9 @@ __global__ void __launch_bounds__(kBlock) k_mom_assemble(int nf, const int32_t* 
                                double* __restrict__ dinv, double* __restrict__ b, double* __restrict__ x0) {
     __shared__ double arow[kAsmRow][kBlock];
     const double tn = *tdev + dt;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nf; i += gridDim.x * blockDim.x) {
-        const int rb = rowptr[i], re = rowptr[i + 1];
-        const int64_t e0 = sell_pos(sell_ptr, i, 0);   // entry k of the row is at e0 + 32 k
-        const bool local = re - rb <= kAsmRow;
-        if (tag[i] & CGP_VEL_DIR) {
-            double sii = 1.0;
-            for (int q = rb; q < re; ++q)
-                if (col[q] == i) sii = S[e0 + 32 * (q - rb)];
-            if (!(sii > 0.0)) sii = 1.0;
-            for (int q = rb; q < re; ++q) A[e0 + 32 * (q - rb)] = col[q] == i ? sii : 0.0;
-            dinv[i] = 1.0 / sii;
-            double u, v;
-            dirichlet_value(bc, i, xy[2 * i], xy[2 * i + 1], tn, u, v);
-            reinterpret_cast<double2*>(b)[i] = make_double2(sii * u, sii * v);
-            reinterpret_cast<double2*>(x0)[i] = make_double2(u, v);
-            continue;
-        }
-        double bx = 0.0, by = 0.0;
-        for (int q = rb; q < re; ++q) {
-            const int64_t e = e0 + 32 * (q - rb);
-            if (local)
-                arow[q - rb][threadIdx.x] = S[e];
-            else
-                A[e] = S[e];
-            const int j = col[q];
-            const double2 hj = reinterpret_cast<const double2*>(h)[j];
-            const double pj = P[j];
-            bx += dt * CxT[e] * pj + M[e] * hj.x;
-            by += dt * CyT[e] * pj + M[e] * hj.y;
-        }
-        const double2 wi = reinterpret_cast<const double2*>(w)[i];
-        int diag_slot = 0;
-        for (int m = vt_ptr[i]; m < vt_ptr[i + 1]; ++m) {
-            const int t = vt_list[m];
-            const int packed = vtslot[m];
-            const double* gt = geo + 7 * (int64_t)t;
-            const int a0 = tri[3 * t], a1 = tri[3 * t + 1], a2 = tri[3 * t + 2];
-            const double2 w0 = reinterpret_cast<const double2*>(w)[a0];
-            const double2 w1 = reinterpret_cast<const double2*>(w)[a1];
-            const double2 w2 = reinterpret_cast<const double2*>(w)[a2];
-            const double c = gt[0] * (1.0 / 12.0);
-            const double cx = c * (w0.x + w1.x + w2.x + wi.x), cy = c * (w0.y + w1.y + w2.y + wi.y);
-            const int li = packed & 3;
-#pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                const int slot = (packed >> (8 * (k + 1))) & 255;
-                const double v = dt * (cx * gt[1 + 2 * k] + cy * gt[2 + 2 * k]);
-                if (local)
-                    arow[slot][threadIdx.x] += v;
-                else
-                    A[e0 + 32 * slot] += v;
-                if (k == li) diag_slot = slot;
-            }
-        }
-        if (local) {
-            for (int q = 0; q < re - rb; ++q) A[e0 + 32 * q] = arow[q][threadIdx.x];
-            dinv[i] = 1.0 / arow[diag_slot][threadIdx.x];
-        } else {
-            dinv[i] = 1.0 / A[e0 + 32 * diag_slot];
-        }
-        if ((tag[i] & CGP_PHI_ZERO) && has_natural_data(bc)) {
-            // traction boundary (Eq. 11 at t^{n+1}: -p^{n+1} n + grad u~ . n / Re = t, with the
-            // prescribed p^{n+1}; the weak pressure term above carries P^n): dt int_{Gamma_N}
-            // (t + (p^{n+1} - P^n) n) psi_i ds over the boundary edges (i, j), j on Gamma_N
-            // too, an edge being on the boundary when one triangle has it; the integrand linear
-            // on the edge: l/6 (2 t_i + t_j)
-            auto tr = [&](int v, double& tx, double& ty) {
-                const double xv = xy[2 * v], yv = xy[2 * v + 1];
-                double nx, ny;
-                natural_traction(bc, xv, yv, tn, tx, ty);
-                natural_normal(bc, xv, yv, nx, ny);
-                const double dp = natural_pressure(bc, xv, yv, tn) - P[v];
-                tx += dp * nx;
-                ty += dp * ny;
-            };
-            const double xi = xy[2 * i], yi = xy[2 * i + 1];
-            double ti_x, ti_y;
-            tr(i, ti_x, ti_y);
-            for (int q = rb; q < re; ++q) {
-                const int j = col[q];
-                if (j == i || !(tag[j] & CGP_PHI_ZERO)) continue;
-                int owners = 0;
-                for (int m = vt_ptr[i]; m < vt_ptr[i + 1]; ++m) {
-                    const int t = vt_list[m];
-                    owners += (tri[3 * t] == j) + (tri[3 * t + 1] == j) + (tri[3 * t + 2] == j);
-                }
-                if (owners != 1) continue;
-                const double xj = xy[2 * j], yj = xy[2 * j + 1];
-                double tj_x, tj_y;
-                tr(j, tj_x, tj_y);
-                const double c = dt * hypot(xj - xi, yj - yi) / 6.0;
-                bx += c * (2.0 * ti_x + tj_x);
-                by += c * (2.0 * ti_y + tj_y);
-            }
-        }
-        reinterpret_cast<double2*>(b)[i] = make_double2(bx, by);
-        reinterpret_cast<double2*>(x0)[i] = wi;
-    }
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nf; i += gridDim.x * blockDim.x)
+        mom_assemble_row<true>(i, rowptr, col, sell_ptr, vt_ptr, vt_list, tri, geo, vtslot, S, M, CxT, CyT, P, w, h,
+                               tag, xy, bc, tn, dt, A, dinv, b, x0, arow);
 }
 
 // Eqs. 22-23: r_i = -3/(2 dt) (Cx_c u~ + Cy_c v~)_i at coarse vertex i (the injected
@@ -1284,6 +1180,114 @@ int launch_batch_coarse(const void* d_args, int ninst, unsigned int* queue, int 
     cfg.gridDim = dim3(csize * nclusters, 1, 1);
     cfg.blockDim = dim3(threads, 1, 1);
     CGP_CUDA(cudaLaunchKernelEx(&cfg, k_pcg_batch, (const CoarsePcgArgs*)d_args, ninst, queue));
+    return CGP_OK;
+}
+
+// ---------------------------------------------------------------- batched whole step
+size_t batch_step_args_size() { return sizeof(BatchStepArgs); }
+
+bool batch_step_eligible(const Solver& s) {
+    return s.prm.restrict_mode == CGP_RESTRICT_INJECT &&
+           (s.prm.guess == CGP_GUESS_ZERO || s.prm.guess == CGP_GUESS_PREV) && s.coarse_kind != CGP_COARSE_KERNELS;
+}
+
+void fill_batch_step_args(Solver& s, void* dst) {
+    const Level& F = s.mesh->lev[s.lf];
+    const Level& C = s.mesh->lev[s.lc];
+    BatchStepArgs a{};
+    a.nf = F.nv;
+    a.Af = sell_of(F);
+    a.rowptr = F.rowptr;
+    a.col = F.col;
+    a.sell_ptr = F.sell_ptr;
+    a.vt_ptr = F.vt_ptr;
+    a.vt_list = F.vt_list;
+    a.tri = F.tri;
+    a.vtslot = s.vtslot;
+    a.geo = s.geo;
+    a.xy = F.xy;
+    a.S = s.S;
+    a.M = s.M;
+    a.M0 = s.M0;
+    a.CxT = s.CxT;
+    a.CyT = s.CyT;
+    a.Cx = s.Cx;
+    a.Cy = s.Cy;
+    a.dinvM0 = s.dinvM0;
+    a.dinvM = s.dinvM;
+    a.mlumpF = s.mlumpF;
+    a.tag = F.tag;
+    a.U = s.U;
+    a.Uprev = s.Uprev;
+    a.P = s.P;
+    a.Ut = s.Ut;
+    a.w = s.w;
+    a.h = s.h;
+    a.A = s.A;
+    a.dinvA = s.dinvA;
+    a.b = s.b;
+    a.g = s.g;
+    a.delta = s.delta;
+    a.div = s.div;
+    a.qrot = s.qrot;
+    a.phi = s.phi;
+    a.bv = s.bv;
+    a.c0 = s.kr;
+    a.c1 = s.kz;
+    a.c2 = s.kp0;
+    a.Ac = sell_of(C);
+    a.Cxc = s.Cxc;
+    a.Cyc = s.Cyc;
+    a.Kc = s.Kc;
+    a.cxy = C.xy;
+    a.ctag = C.tag;
+    a.coarse = coarse_args(s);
+    a.pure_neumann = s.pure_neumann;
+    a.nlev = s.lf - s.lc + 1;
+    for (int l = 0; l < a.nlev; ++l) {
+        a.nv[l] = s.mesh->lev[s.lc + l].nv;
+        a.parents[l] = l + 1 < a.nlev ? s.mesh->lev[s.lc + l + 1].parents : nullptr;
+    }
+    a.bc = bc_of(s);
+    a.dt = s.prm.dt;
+    a.inv_re = 1.0 / s.prm.Re;
+    a.tol_mom2 = s.prm.tol_mom * s.prm.tol_mom;
+    a.chi = s.prm.chi;
+    a.lumped = s.prm.mass_mode == CGP_MASS_LUMPED;
+    a.max_it_mom = s.prm.max_it_mom;
+    a.cheb_steps = cheb_steps_for(s.prm.tol_mass);
+    a.tdev = s.tdev;
+    a.stats = s.stats;
+    a.ks = s.ks;
+    memcpy(dst, &a, sizeof(a));
+}
+
+int batch_step_clusters(int csize, int threads, int* nclusters) {
+    static bool attr_set = false;
+    if (!attr_set) {
+        CGP_CUDA(cudaFuncSetAttribute(k_batch_step, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+        attr_set = true;
+    }
+    cudaLaunchAttribute attr[1];
+    cudaLaunchConfig_t cfg = cluster_config(csize, nullptr, attr);
+    cfg.blockDim = dim3(threads, 1, 1);
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, k_batch_step, &cfg) != cudaSuccess) {
+        cudaGetLastError();
+        n = 0;
+    }
+    *nclusters = n;
+    return CGP_OK;
+}
+
+int launch_batch_step(const void* d_args, int ninst, unsigned int* queue, int csize, int threads, int nclusters,
+                      cudaStream_t st) {
+    CGP_CUDA(cudaMemsetAsync(queue, 0, sizeof(unsigned int), st));
+    cudaLaunchAttribute attr[1];
+    cudaLaunchConfig_t cfg = cluster_config(csize, st, attr);
+    cfg.gridDim = dim3(csize * nclusters, 1, 1);
+    cfg.blockDim = dim3(threads, 1, 1);
+    CGP_CUDA(cudaLaunchKernelEx(&cfg, k_batch_step, (const BatchStepArgs*)d_args, ninst, queue));
     return CGP_OK;
 }
 
