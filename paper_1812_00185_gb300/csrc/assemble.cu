@@ -165,6 +165,7 @@ static int layout(Solver& s, void* base, size_t* bytes) {
     if (s.prm.guess == CGP_GUESS_LEARNED) {
         s.phi_guess = cv.take<double>(nc);
         s.mlp.carve(cv, (int)nc, 1);
+        s.mlp_gate = cv.take<int>(4);
     }
     if (s.prm.guess == CGP_GUESS_LEARNED || s.prm.guess == CGP_GUESS_PROJ) {
         s.hist_x = cv.take<double>((size_t)kProjL * nc);
@@ -369,7 +370,8 @@ extern "C" int cgp_assemble(const cgp_mesh* mesh, const cgp_params* params, void
         (s.user_ud && cudaMemsetAsync(s.user_ud, 0, sizeof(double) * 2 * s.nf, st) != cudaSuccess) ||
         (s.user_f && cudaMemsetAsync(s.user_f, 0, sizeof(double) * 2 * s.nf, st) != cudaSuccess) ||
         cudaMemsetAsync(s.scal, 0, sizeof(double) * 16, st) != cudaSuccess ||
-        (s.proj && cudaMemsetAsync(s.proj, 0, sizeof(ProjState), st) != cudaSuccess)) {
+        (s.proj && cudaMemsetAsync(s.proj, 0, sizeof(ProjState), st) != cudaSuccess) ||
+        (s.mlp_gate && cudaMemsetAsync(s.mlp_gate, 0, 4 * sizeof(int), st) != cudaSuccess)) {
         set_error("workspace initialisation failed");
         return fail(CGP_ECUDA);
     }

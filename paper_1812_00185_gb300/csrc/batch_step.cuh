@@ -6,7 +6,8 @@
 // another.
 //
 //   Eq. 21     the rows of the momentum system (step_rows.cuh), then FP64 BiCGStab with
-//              Jacobi for both velocity components (three cluster sums per iteration)
+//              Jacobi for both velocity components (three cluster sums per iteration;
+//              restarted from the true residual after a breakdown)
 //   Eqs. 22-23 the injected coarse right-hand side (with the range projection of a
 //              pure-Neumann problem and the lifted phi data of a traction boundary), then the
 //              instance's one-launch coarse PCG (coarse_pcg_body: FP64, or FP32 inner / FP64
@@ -210,148 +211,157 @@ static __global__ void __launch_bounds__(512, 1) k_batch_step(const BatchStepArg
                                     a.M, a.CxT, a.CyT, a.P, a.w, a.h, a.tag, a.xy, bc, tn, dt, a.A, a.dinvA, a.b,
                                     a.Ut, nullptr);
         cl.sync();
-        // ---- BiCGStab (two components), x = U~ from w
+        // ---- BiCGStab (two components), x = U~ from w; a breakdown (rho or omega vanishing
+        // before convergence) restarts from the true residual, at most kRestarts times
         const BicgVecs V = a.bv;
-        double rho[2], alpha[2] = {0.0, 0.0}, omega[2] = {0.0, 0.0}, beta[2] = {0.0, 0.0}, bb[2], rr[2];
-        int done[2], it = 0, status = 0;
-        {
-            double acc[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
-            for (int sl = crank * nwarp + wid; sl < a.Af.nslices; sl += csize * nwarp) {
-                const int i = sl * 32 + lane;
-                double ax[2];
-                spmv2_row(a.Af, a.A, V.x, sl, lane, ax);
-                if (i < nf) {
-#pragma unroll
-                    for (int c = 0; c < 2; ++c) {
-                        const double bv = a.b[2 * i + c], rv = bv - ax[c];
-                        V.r[2 * i + c] = rv;
-                        V.rhat[2 * i + c] = rv;
-                        V.p[2 * i + c] = 0.0;
-                        V.v[2 * i + c] = 0.0;
-                        acc[c] += rv * rv;
-                        acc[4 + c] += bv * bv;
-                    }
-                }
-            }
-            acc[2] = acc[0];
-            acc[3] = acc[1];
-            double tot[6];
-            cs.sum(acc, tot);
-            for (int c = 0; c < 2; ++c) {
-                rho[c] = tot[c];
-                rr[c] = tot[2 + c];
-                bb[c] = tot[4 + c];
-                done[c] = !(rr[c] > a.tol_mom2 * bb[c]);
-            }
-        }
-        while (!(done[0] && done[1]) && it < a.max_it_mom) {
-            // p = r + beta (p - omega v), y = D^-1 p
-            for (int i = tid; i < nf; i += nthr) {
-                const double di = a.dinvA[i];
-#pragma unroll
-                for (int c = 0; c < 2; ++c) {
-                    if (done[c]) continue;
-                    const double pv = V.r[2 * i + c] + beta[c] * (V.p[2 * i + c] - omega[c] * V.v[2 * i + c]);
-                    V.p[2 * i + c] = pv;
-                    V.y[2 * i + c] = di * pv;
-                }
-            }
-            cl.sync();
-            {   // v = A y, alpha = rho / <rhat, v>
-                double acc[2] = {0.0, 0.0};
-                for (int sl = crank * nwarp + wid; sl < a.Af.nslices; sl += csize * nwarp) {
-                    const int i = sl * 32 + lane;
-                    double ax[2];
-                    spmv2_row(a.Af, a.A, V.y, sl, lane, ax);
-                    if (i < nf) {
-#pragma unroll
-                        for (int c = 0; c < 2; ++c) {
-                            if (done[c]) continue;
-                            V.v[2 * i + c] = ax[c];
-                            acc[c] += V.rhat[2 * i + c] * ax[c];
-                        }
-                    }
-                }
-                double tot[2];
-                cs.sum(acc, tot);
-                for (int c = 0; c < 2; ++c) {
-                    if (done[c]) continue;
-                    if (tot[c] != 0.0 && isfinite(tot[c])) {
-                        alpha[c] = rho[c] / tot[c];
-                    } else {
-                        done[c] = 1;
-                        status = isfinite(tot[c]) ? CGP_EBREAKDOWN : CGP_ENONFINITE;
-                    }
-                }
-            }
-            // s = r - alpha v, z = D^-1 s
-            for (int i = tid; i < nf; i += nthr) {
-                const double di = a.dinvA[i];
-#pragma unroll
-                for (int c = 0; c < 2; ++c) {
-                    if (done[c]) continue;
-                    const double sv = V.r[2 * i + c] - alpha[c] * V.v[2 * i + c];
-                    V.s[2 * i + c] = sv;
-                    V.z[2 * i + c] = di * sv;
-                }
-            }
-            cl.sync();
-            {   // t = A z, omega = <t, s> / <t, t>
+        double rho[2], alpha[2] = {0.0, 0.0}, omega[2] = {0.0, 0.0}, beta[2] = {0.0, 0.0}, bb[2] = {0.0, 0.0};
+        double rr[2] = {0.0, 0.0};
+        int done[2] = {0, 0}, it = 0, status = 0;
+        constexpr int kRestarts = 4;
+        for (int restart = 0; restart <= kRestarts; ++restart) {
+            {   // r = b - A x, rhat = r, p = v = 0
                 double acc[4] = {0.0, 0.0, 0.0, 0.0};
                 for (int sl = crank * nwarp + wid; sl < a.Af.nslices; sl += csize * nwarp) {
                     const int i = sl * 32 + lane;
                     double ax[2];
-                    spmv2_row(a.Af, a.A, V.z, sl, lane, ax);
+                    spmv2_row(a.Af, a.A, V.x, sl, lane, ax);
                     if (i < nf) {
 #pragma unroll
                         for (int c = 0; c < 2; ++c) {
-                            if (done[c]) continue;
-                            V.t[2 * i + c] = ax[c];
-                            acc[c] += ax[c] * V.s[2 * i + c];
-                            acc[2 + c] += ax[c] * ax[c];
+                            const double bv = a.b[2 * i + c], rv = bv - ax[c];
+                            V.r[2 * i + c] = rv;
+                            V.rhat[2 * i + c] = rv;
+                            V.p[2 * i + c] = 0.0;
+                            V.v[2 * i + c] = 0.0;
+                            acc[c] += rv * rv;
+                            acc[2 + c] += bv * bv;
                         }
                     }
                 }
                 double tot[4];
                 cs.sum(acc, tot);
-                for (int c = 0; c < 2; ++c) omega[c] = (!done[c] && tot[2 + c] > 0.0 && isfinite(tot[2 + c]))
-                                                           ? tot[c] / tot[2 + c] : 0.0;
+                for (int c = 0; c < 2; ++c) {
+                    rho[c] = tot[c];
+                    rr[c] = tot[c];
+                    if (restart == 0) bb[c] = tot[2 + c];
+                    done[c] = !(rr[c] > a.tol_mom2 * bb[c]);
+                    alpha[c] = omega[c] = beta[c] = 0.0;
+                }
             }
-            {   // x += alpha y + omega z, r = s - omega t, <rhat, r>, <r, r>
-                double acc[4] = {0.0, 0.0, 0.0, 0.0};
+            bool broke = false;
+            while (!(done[0] && done[1]) && it < a.max_it_mom && !broke) {
+                // p = r + beta (p - omega v), y = D^-1 p
                 for (int i = tid; i < nf; i += nthr) {
+                    const double di = a.dinvA[i];
 #pragma unroll
                     for (int c = 0; c < 2; ++c) {
                         if (done[c]) continue;
-                        V.x[2 * i + c] += alpha[c] * V.y[2 * i + c] + omega[c] * V.z[2 * i + c];
-                        const double rv = V.s[2 * i + c] - omega[c] * V.t[2 * i + c];
-                        V.r[2 * i + c] = rv;
-                        acc[c] += V.rhat[2 * i + c] * rv;
-                        acc[2 + c] += rv * rv;
+                        const double pv = V.r[2 * i + c] + beta[c] * (V.p[2 * i + c] - omega[c] * V.v[2 * i + c]);
+                        V.p[2 * i + c] = pv;
+                        V.y[2 * i + c] = di * pv;
                     }
                 }
-                double tot[4];
-                cs.sum(acc, tot);
-                for (int c = 0; c < 2; ++c) {
-                    if (done[c]) continue;
-                    if (!isfinite(tot[c]) || !isfinite(tot[2 + c])) {
-                        status = CGP_ENONFINITE;
-                        done[c] = 1;
-                        continue;
+                cl.sync();
+                {   // v = A y, alpha = rho / <rhat, v>
+                    double acc[2] = {0.0, 0.0};
+                    for (int sl = crank * nwarp + wid; sl < a.Af.nslices; sl += csize * nwarp) {
+                        const int i = sl * 32 + lane;
+                        double ax[2];
+                        spmv2_row(a.Af, a.A, V.y, sl, lane, ax);
+                        if (i < nf) {
+#pragma unroll
+                            for (int c = 0; c < 2; ++c) {
+                                if (done[c]) continue;
+                                V.v[2 * i + c] = ax[c];
+                                acc[c] += V.rhat[2 * i + c] * ax[c];
+                            }
+                        }
                     }
-                    rr[c] = tot[2 + c];
-                    if (rr[c] <= a.tol_mom2 * bb[c]) {
-                        done[c] = 1;
-                    } else if (omega[c] == 0.0 || rho[c] == 0.0) {
-                        done[c] = 1;
-                        status = CGP_EBREAKDOWN;
-                    } else {
-                        beta[c] = (tot[c] / rho[c]) * (alpha[c] / omega[c]);
-                        rho[c] = tot[c];
+                    double tot[2];
+                    cs.sum(acc, tot);
+                    for (int c = 0; c < 2; ++c) {
+                        if (done[c]) continue;
+                        if (!isfinite(tot[c])) {
+                            done[c] = 1;
+                            status = CGP_ENONFINITE;
+                        } else if (tot[c] != 0.0) {
+                            alpha[c] = rho[c] / tot[c];
+                        } else {
+                            broke = true;
+                        }
                     }
                 }
+                if (broke) break;
+                // s = r - alpha v, z = D^-1 s
+                for (int i = tid; i < nf; i += nthr) {
+                    const double di = a.dinvA[i];
+#pragma unroll
+                    for (int c = 0; c < 2; ++c) {
+                        if (done[c]) continue;
+                        const double sv = V.r[2 * i + c] - alpha[c] * V.v[2 * i + c];
+                        V.s[2 * i + c] = sv;
+                        V.z[2 * i + c] = di * sv;
+                    }
+                }
+                cl.sync();
+                {   // t = A z, omega = <t, s> / <t, t>
+                    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+                    for (int sl = crank * nwarp + wid; sl < a.Af.nslices; sl += csize * nwarp) {
+                        const int i = sl * 32 + lane;
+                        double ax[2];
+                        spmv2_row(a.Af, a.A, V.z, sl, lane, ax);
+                        if (i < nf) {
+#pragma unroll
+                            for (int c = 0; c < 2; ++c) {
+                                if (done[c]) continue;
+                                V.t[2 * i + c] = ax[c];
+                                acc[c] += ax[c] * V.s[2 * i + c];
+                                acc[2 + c] += ax[c] * ax[c];
+                            }
+                        }
+                    }
+                    double tot[4];
+                    cs.sum(acc, tot);
+                    for (int c = 0; c < 2; ++c)
+                        omega[c] = (!done[c] && tot[2 + c] > 0.0 && isfinite(tot[2 + c])) ? tot[c] / tot[2 + c] : 0.0;
+                }
+                {   // x += alpha y + omega z, r = s - omega t, <rhat, r>, <r, r>
+                    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+                    for (int i = tid; i < nf; i += nthr) {
+#pragma unroll
+                        for (int c = 0; c < 2; ++c) {
+                            if (done[c]) continue;
+                            V.x[2 * i + c] += alpha[c] * V.y[2 * i + c] + omega[c] * V.z[2 * i + c];
+                            const double rv = V.s[2 * i + c] - omega[c] * V.t[2 * i + c];
+                            V.r[2 * i + c] = rv;
+                            acc[c] += V.rhat[2 * i + c] * rv;
+                            acc[2 + c] += rv * rv;
+                        }
+                    }
+                    double tot[4];
+                    cs.sum(acc, tot);
+                    for (int c = 0; c < 2; ++c) {
+                        if (done[c]) continue;
+                        if (!isfinite(tot[c]) || !isfinite(tot[2 + c])) {
+                            status = CGP_ENONFINITE;
+                            done[c] = 1;
+                            continue;
+                        }
+                        rr[c] = tot[2 + c];
+                        if (rr[c] <= a.tol_mom2 * bb[c]) {
+                            done[c] = 1;
+                        } else if (omega[c] == 0.0 || tot[c] == 0.0) {
+                            broke = true;
+                        } else {
+                            beta[c] = (tot[c] / rho[c]) * (alpha[c] / omega[c]);
+                            rho[c] = tot[c];
+                        }
+                    }
+                }
+                ++it;
             }
-            ++it;
+            if (!broke) break;
+            if (restart == kRestarts) status = CGP_EBREAKDOWN;
         }
         if (!(done[0] && done[1]) && !status) status = CGP_ENOTCONV;
         // ---- Eqs. 22-23: r = -3/(2 dt) (Cx_c u~ + Cy_c v~) at the coarse vertices (the fine

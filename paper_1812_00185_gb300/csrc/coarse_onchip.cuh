@@ -424,11 +424,14 @@ static __global__ void __launch_bounds__(kOnchipThreads, 1) k_pcg_onchip(CoarseP
     int iters = 0, status = 0, outer = 0, used_alt = 0;
     bool converged = false;
     double tot[4];
-    if (a.x_alt && !a.zero_x) {
+    // the judge of the learned guess: while gate[0] > 0 the network was not evaluated this step
+    const bool alt_on = a.x_alt && !a.zero_x && !(a.gate && ldcg(a.gate) > 0);
+    double rr_x = 0.0;   // ||b - A x||^2 of the first guess alone (warp 0; for the judge)
+    if (alt_on) {
         // second initial guess y (the learned prediction): start from the combination
         // c1 x + c2 y that minimises the A-norm of the error over span{x, y} (a 2x2 Galerkin
         // system), which is what CG's work depends on; never worse than x or y alone
-        double g[3] = {0.0, 0.0, 0.0}, f[2] = {0.0, 0.0};   // xAx, xAy, yAy; x.b, y.b
+        double g[4] = {0.0, 0.0, 0.0, 0.0}, f[2] = {0.0, 0.0};   // xAx, xAy, yAy, |b - Ax|^2; x.b, y.b
 #pragma unroll
         for (int t = 0; t < kOnchipRows; ++t) {
             if (t >= nrow) break;
@@ -439,12 +442,14 @@ static __global__ void __launch_bounds__(kOnchipThreads, 1) k_pcg_onchip(CoarseP
                 g[0] += xi * ax;
                 g[1] += xi * ay;
                 g[2] += yi * ay;
+                g[3] += (bi - ax) * (bi - ax);
                 f[0] += xi * bi;
                 f[1] += yi * bi;
             }
         }
         cred64(g, tot);
         double gt[3] = {tot[0], tot[1], tot[2]};
+        rr_x = tot[3];
         cred64(f, tot);
         if (threadIdx.x == 0) {
             const double a11 = gt[0], a12 = gt[1], a22 = gt[2], f1 = tot[0], f2 = tot[1];
@@ -496,7 +501,24 @@ static __global__ void __launch_bounds__(kOnchipThreads, 1) k_pcg_onchip(CoarseP
         }
         cred64(acc, tot);
         if (wid == 0) {
-            if (outer == 0) bb = tot[1];
+            if (outer == 0) {
+                bb = tot[1];
+                // judge: did the network's direction lower the starting residual by 5 %?
+                if (a.gate && lane == 0 && rank == 0) {
+                    if (alt_on) {
+                        const bool useful = tot[0] < 0.9025 * rr_x;
+                        const int miss = useful ? 0 : ldcg(a.gate + 1) + 1;
+                        if (miss >= 8) {
+                            a.gate[0] = 64;
+                            a.gate[1] = 0;
+                        } else {
+                            a.gate[1] = miss;
+                        }
+                    } else if (ldcg(a.gate) > 0) {
+                        a.gate[0] = ldcg(a.gate) - 1;
+                    }
+                }
+            }
             rr_final = tot[0];
             int act = kInner;
             if (!isfinite(tot[0])) act = kNonfinite;

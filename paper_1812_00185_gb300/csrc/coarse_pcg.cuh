@@ -69,6 +69,10 @@ struct CoarsePcgArgs {
     // signal that nothing sends, under a limit of milliseconds, so the solve ends with
     // CGP_ETIMEOUT without a fault or a hang
     int wait_test;
+    // the learned guess's judge (on-chip solve only; null otherwise): gate[0] = steps left in
+    // which the network is not evaluated, gate[1] = consecutive steps in which its direction
+    // lowered the starting residual by less than 5 %
+    int* gate;
 };
 
 template <class T>

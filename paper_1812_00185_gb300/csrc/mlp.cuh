@@ -40,7 +40,7 @@ struct MlpBuffers {
 // (r, q) (each n doubles, consecutive) into pred; mlp_infer_setup (once per process, before
 // any capture) raises the shared-memory limit of its layer-2 kernel
 int mlp_forward(const MlpBuffers& B, const Level& L, const double* r, const double* q, int batch, double* pred,
-                cudaStream_t st);
+                cudaStream_t st, const int* gate = nullptr);
 int mlp_infer_setup();
 
 }  // namespace cgp

@@ -13,6 +13,9 @@
 //             stays within ~1e-5 of FP32 arithmetic; h2 = relu(a2 + b2), vertex-major FP32
 //   layer 3   one warp per vertex: [h2_i; mean h2_j] . W3 + b3 (warp sum), Phi0 = q + s_q out
 //
+// In a step, the kernels return at once while the coarse solve's judge has switched the
+// network off (gate[0] > 0: its direction bought under 5 % of the starting residual in eight
+// steps in a row; it is tried again after 64 steps).
 // The 1-ring means add neighbours in CSR order and multiply by 1/deg, as the training path does.
 #include <cuda_bf16.h>
 
@@ -34,7 +37,8 @@ __global__ void __launch_bounds__(128) k_inf_layer1(int n, const int32_t* __rest
                                                     const double* __restrict__ q, const double* __restrict__ xy,
                                                     const float* __restrict__ scale,
                                                     const __nv_bfloat16* __restrict__ W1, const float* __restrict__ b1,
-                                                    float* __restrict__ h1) {
+                                                    float* __restrict__ h1, const int* __restrict__ gate) {
+    if (gate && *gate > 0) return;   // the solve's judge has switched the network off for now
     __shared__ float w[kHid][8];
     __shared__ float bias[kHid];
     for (int e = threadIdx.x; e < kHid * 8; e += blockDim.x) w[e / 8][e % 8] = __bfloat162float(W1[e]);
@@ -103,7 +107,9 @@ __device__ __forceinline__ void mma_bf16(float (&c)[4], const uint32_t (&a)[4], 
 __global__ void __launch_bounds__(256) k_inf_layer2(int n, const int32_t* __restrict__ rowptr,
                                                     const int32_t* __restrict__ col, const float* __restrict__ h1,
                                                     const __nv_bfloat16* __restrict__ W2,
-                                                    const float* __restrict__ b2, float* __restrict__ h2) {
+                                                    const float* __restrict__ b2, float* __restrict__ h2,
+                                                    const int* __restrict__ gate) {
+    if (gate && *gate > 0) return;
     extern __shared__ __align__(16) unsigned char smem[];
     __nv_bfloat16* ahi = reinterpret_cast<__nv_bfloat16*>(smem);
     __nv_bfloat16* alo = ahi + kL2Rows * kL2Ld;
@@ -221,7 +227,9 @@ __global__ void __launch_bounds__(256) k_inf_layer3(int n, const int32_t* __rest
                                                     const int32_t* __restrict__ col, const float* __restrict__ h2,
                                                     const __nv_bfloat16* __restrict__ W3,
                                                     const float* __restrict__ b3, const float* __restrict__ scale,
-                                                    const double* __restrict__ q, double* __restrict__ pred) {
+                                                    const double* __restrict__ q, double* __restrict__ pred,
+                                                    const int* __restrict__ gate) {
+    if (gate && *gate > 0) return;
     const int lane = threadIdx.x & 31;
     const int i = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
     if (i >= n) return;
@@ -258,7 +266,7 @@ int mlp_infer_setup() {
 }
 
 int mlp_forward(const MlpBuffers& B, const Level& L, const double* r, const double* q, int batch, double* pred,
-                cudaStream_t st) {
+                cudaStream_t st, const int* gate) {
     const int n = B.n;
     // activations: h1 in hv, h2 in m1 (both [vertex][64] FP32 here)
     for (int b = 0; b < batch; ++b) {
@@ -268,12 +276,12 @@ int mlp_forward(const MlpBuffers& B, const Level& L, const double* r, const doub
         k_mlp_scales<<<dim3(kScaleBlocks, 1), kBlock, 0, st>>>(n, rb, qb, B.spart);
         k_mlp_scales_fin<<<1, 32, 0, st>>>(n, kScaleBlocks, B.spart, sc);
         k_inf_layer1<<<blocks_for(n, 128), 128, 0, st>>>(n, L.rowptr, L.col, rb, qb, L.xy, sc, B.params_bf + kOffW1,
-                                                         B.params + kOffB1, B.hv);
+                                                         B.params + kOffB1, B.hv, gate);
         k_inf_layer2<<<blocks_for(n, kL2Rows), 256, kL2Smem, st>>>(n, L.rowptr, L.col, B.hv, B.params_bf + kOffW2,
-                                                                   B.params + kOffB2, B.m1);
+                                                                   B.params + kOffB2, B.m1, gate);
         if (pred)
             k_inf_layer3<<<blocks_for((int64_t)n * 32, 256), 256, 0, st>>>(
-                n, L.rowptr, L.col, B.m1, B.params_bf + kOffW3, B.params + kOffB3, sc, qb, pred + (size_t)b * n);
+                n, L.rowptr, L.col, B.m1, B.params_bf + kOffW3, B.params + kOffB3, sc, qb, pred + (size_t)b * n, gate);
     }
     CGP_LAUNCH_CHECK();
     return CGP_OK;

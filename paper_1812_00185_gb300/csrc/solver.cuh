@@ -67,6 +67,7 @@ struct Solver {
     double *hist_x = nullptr, *hist_b = nullptr, *phi_q = nullptr;
     ProjState* proj = nullptr;
     double* phi_guess = nullptr;  // n_c: the network's prediction of Phi_c
+    int* mlp_gate = nullptr;      // the coarse solve's judge of the network (see CoarsePcgArgs::gate)
     double* cw64 = nullptr;       // coarse one-launch solver work: 8 FP64 vectors of n_c
     float* cw32 = nullptr;        // and 9 FP32 vectors of n_c
     int coarse_kind = 0;          // CGP_COARSE_KERNELS / _CLUSTER / _PERSISTENT (AUTO resolved)

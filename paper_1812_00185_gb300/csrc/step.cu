@@ -882,6 +882,7 @@ CoarsePcgArgs coarse_args(Solver& s) {
     a.bar_err = s.bar_err;
     a.partials = s.coarse_partials;
     a.wait_test = s.wait_test;
+    a.gate = s.onchip_bytes ? s.mlp_gate : nullptr;
     return a;
 }
 
@@ -890,7 +891,8 @@ static int learned_guess(Ctx& c) {
     Solver& s = *c.s;
     if (s.prm.guess == CGP_GUESS_LEARNED && s.guess_ready) {
         const Level& Cl = s.mesh->lev[s.lc];
-        PL(c, CGP_PROF_MLP, CGP_TRY(mlp_forward(s.mlp, Cl, s.rc, s.phi, 1, s.phi_guess, c.st)));
+        PL(c, CGP_PROF_MLP,
+           CGP_TRY(mlp_forward(s.mlp, Cl, s.rc, s.phi, 1, s.phi_guess, c.st, s.onchip_bytes ? s.mlp_gate : nullptr)));
     }
     return CGP_OK;
 }
