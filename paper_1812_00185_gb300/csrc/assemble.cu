@@ -191,7 +191,11 @@ static int layout(Solver& s, void* base, size_t* bytes) {
         s.oc_send_lr = cv.take<int32_t>(nnzc);     // sends <= entries with a remote column
         s.oc_send_dst = cv.take<int32_t>(nnzc);
         s.oc_hsub = cv.take<uint8_t>((size_t)kOnchipMaxCluster * (nc < 65535 ? nc : 65535));
+        s.oc_hrow = cv.take<int32_t>((size_t)kOnchipMaxCluster * (nc < 65535 ? nc : 65535));
+        s.oc_send_woff = cv.take<int32_t>((size_t)kOnchipMaxCluster * (kOnchipWarps + 1));
         s.oc_einv = cv.take<float>((size_t)kOnchipMaxCluster * kOnchipMaxSubPerCta * kOnchipMaxCluster * kOnchipMaxSubPerCta);
+        s.oc_need = cv.take<uint8_t>((size_t)kOnchipMaxCluster * kOnchipMaxCluster * kOnchipMaxSubPerCta);
+        s.oc_need_n = cv.take<int32_t>(kOnchipMaxCluster);
         s.Af = cv.take<float>(nnzf);
         s.M0f = cv.take<float>(nnzf);
         s.Mf = cv.take<float>(nnzf);

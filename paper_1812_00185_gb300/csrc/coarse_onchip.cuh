@@ -9,31 +9,32 @@
 //   * z for its own rows followed by a halo: z of the other CTAs' rows that its rows use;
 //   * its rows of the FP32 matrix, 32-row slices, each entry as (index of its column's z,
 //     value), widths padded to whole 4-entry steps;
-//   * a send list: after z changes, every CTA stores the z its neighbours need straight
-//     into their halos (remote shared-memory stores) with the reduction that follows, so
-//     every gather of the SpMV is a local shared-memory load;
-//   * the slots of the cluster reductions: every CTA stores its partial sums into every
+//   * for the halo rows, r, q and D^{-1}, and two receive buffers;
+//   * a send list: every warp stores A z of its rows that neighbours use straight into their
+//     receive buffers (remote shared-memory stores);
+//   * the slots of the cluster exchanges: every CTA stores its partial sums into every
 //     other CTA's slot array and each CTA adds the slots in the same fixed order (identical
 //     scalars everywhere);
-//   * E^+ of the preconditioner's coarse space (below).
-// The inner iteration is classical PCG with the SpMV applied to z: w = A z, p = z + beta p,
-// q = w + beta q (= A p), so z is the only vector that travels; the other vectors (e, r, z,
-// p, q, D^{-1}) live in registers.  Two reductions per iteration (<p, q>, then <r, z> and
-// <r, r>), all in FP32 on the residual scaled to unit norm, so the inner scalars stay well
-// inside the FP32 range.  The FP64 outer loop (true residual, its norm, the convergence
-// test, x += ||r|| e) reads the FP64 matrix and x from global memory a few times per solve;
-// only warp 0 of each CTA does its FP64 scalar work.
+//   * the rows of E^+ (below) for the subdomains it corrects.
+// The inner iteration is PCG in the one-exchange form of Chronopoulos and Gear: w = A z,
+// then a single exchange carries <r, z>, <z, w>, <r, r>, the halo copy of w and the coarse
+// sums; alpha and beta follow from those, and each CTA advances q, r and z of its halo rows
+// with the same recurrences (and bit for bit the same values) as their owners, so z of the
+// halo never travels.  The vectors e, r, z, p, q of the own rows live in registers.  All
+// inner arithmetic is FP32 on the residual scaled to unit norm.  The FP64 outer loop (true
+// residual, its norm, the convergence test, x += ||r|| e) reads the FP64 matrix and x from
+// global memory a few times per solve; only warp 0 of each CTA does its FP64 scalar work.
 //
 // Preconditioner: Jacobi, or Jacobi plus an additive subdomain coarse correction,
 //     z = D^{-1} r + Z E^+ Z^T r,   E = Z^T A Z,
 // where column j of Z is the indicator of subdomain j (a group of sibling warp patches; phi =
-// 0 rows belong to none) and E^+ is the pseudo-inverse of the small Galerkin matrix, held by
-// every CTA.  M^{-1} stays symmetric positive definite, so the iteration is still PCG; the
-// coarse space removes the smooth error components Jacobi damps slowest (the iteration
-// count drops several-fold on the coarse Poisson systems of CGP).  Its cost rides on the
-// existing reductions: Z^T r is a set of warp sums that travels with <r, D^{-1} r>, every
-// CTA forms mu = E^+ Z^T r, and <r, z> = <r, D^{-1} r> + (Z^T r)^T mu needs no extra
-// exchange; z of the halo rows is corrected by the receiver (mu is identical everywhere).
+// 0 rows belong to none) and E^+ is the pseudo-inverse of the small Galerkin matrix.
+// M^{-1} stays symmetric positive definite, so the iteration is still PCG; the coarse space
+// removes the smooth error components Jacobi damps slowest (the iteration count drops
+// several-fold on the coarse Poisson systems of CGP).  s = Z^T r follows its own recurrence
+// s = Z^T r_prev - alpha Z^T q, from the subdomain sums (warp sums) of r and w that travel
+// with the exchange, so it needs no exchange of its own; each CTA forms mu = E^+ s only for
+// its own subdomains and those of its halo rows.
 #pragma once
 
 #include <cooperative_groups.h>
@@ -96,48 +97,6 @@ __device__ __forceinline__ void oc_st_async(uint32_t addr, float v, uint32_t mba
 constexpr long long kOnchipWaitCycles = 4000000000LL;   // ~2 s: a wait this long means a lost signal
 constexpr long long kOnchipWaitCyclesTest = 20000000LL; // ~10 ms, under the wait test hook
 
-// R rows of mu = E^+ s in one warp: lane l holds s of columns l*cpl .. l*cpl+cpl-1 (cpl =
-// 4, 2 or 1; `has` = those columns exist) and forms the partial sums of all R rows over them
-// (one 16-, 8- or 4-byte load per row: the warp reads each row once, conflict-free); a
-// transpose reduction then halves the rows held per lane with each xor shuffle (offsets 16,
-// 8, ...) and sums the rest, leaving row `row`'s total in every lane.
-template <int R, int cpl>
-__device__ __forceinline__ float oc_mu_rows(const float* er, int m, bool has, const float (&sv)[4], int lane, int& row) {
-    float v[R];
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-        const float* e = er + r * m + lane * cpl;
-        float a = 0.0f;
-        if (has) {
-            if constexpr (cpl == 4) {
-                const float4 x = *reinterpret_cast<const float4*>(e);
-                a = fmaf(x.x, sv[0], fmaf(x.y, sv[1], fmaf(x.z, sv[2], x.w * sv[3])));
-            } else if constexpr (cpl == 2) {
-                const float2 x = *reinterpret_cast<const float2*>(e);
-                a = fmaf(x.x, sv[0], x.y * sv[1]);
-            } else {
-                a = e[0] * sv[0];
-            }
-        }
-        v[r] = a;
-    }
-    row = 0;
-#pragma unroll
-    for (int h = R, o = 16; h > 1; h >>= 1, o >>= 1) {
-        const bool up = (lane & o) != 0;
-        if (up) row += h / 2;
-#pragma unroll
-        for (int i = 0; i < h / 2; ++i) {
-            const float keep = up ? v[i + h / 2] : v[i];
-            const float send = up ? v[i] : v[i + h / 2];
-            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
-        }
-    }
-#pragma unroll
-    for (int o = 16 / R; o > 0; o >>= 1) v[0] += __shfl_xor_sync(0xffffffffu, v[0], o);
-    return v[0];
-}
-
 // what warp 0 tells its CTA after an FP64 reduction
 struct OnchipScalars {
     int act;
@@ -145,39 +104,57 @@ struct OnchipScalars {
     double inv, norm, mu;      // 1 / ||r||, ||r|| of the outer residual; mean of the Neumann fix
 };
 
-// MR: rows of mu = E^+ s per warp (nsub / 16, at least 1), 0 without the coarse correction
+// MR: nsub / 16 (at least 1) with the coarse correction, 0 without; it fixes how many columns
+// of an E^+ row a lane holds (4, 2 or 1)
 template <int MR>
 static __global__ void __launch_bounds__(kOnchipThreads, 1) k_pcg_onchip(CoarsePcgArgs a, OnchipPlan pl) {
     namespace cg = cooperative_groups;
     cg::cluster_group cluster = cg::this_cluster();
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ double wsum[kOnchipWarps][4];
-    __shared__ float wsum32[kOnchipWarps][4];
+    __shared__ float wsum32[kOnchipWarps][6];
     __shared__ OnchipScalars sc;
-    __shared__ __align__(8) uint64_t mbar[2];     // FP32 reductions, alternating
+    __shared__ __align__(8) uint64_t mbar[2];     // exchanges, alternating
     __shared__ uint32_t mbar_remote[kOnchipMaxCluster][2];
     __shared__ float tot32[4];
     __shared__ int abort_flag;
     const int rank = (int)cluster.block_rank(), ncl = (int)cluster.num_blocks();
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = kOnchipWarps;
     const SellView& A = a.A;
-    const int rows_max = pl.rows_max, zn = rows_max + pl.halo_max, m = pl.nsub;
-    float* zl = reinterpret_cast<float*>(smem);
-    double* red64 = reinterpret_cast<double*>(smem + onchip_z_bytes(rows_max, pl.halo_max));
+    const int rows_max = pl.rows_max, hm = onchip_hm(pl.halo_max), m = pl.nsub, m4 = (m + 3) & ~3;
+    float* zl = reinterpret_cast<float*>(smem);   // z: own rows, then the halo
+    float* wl = zl + rows_max + hm;               // own rows: A z (the values sent out), or r at a restart
+    float* dl = wl + rows_max;                    // own rows: D^{-1}
+    float* recv = dl + rows_max;                  // [2][hm]: halo values received, by exchange parity
+    float* rh = recv + 2 * hm;                    // halo rows: r, q and D^{-1}
+    float* qh = rh + hm;
+    float* dh = qh + hm;
+    double* red64 = reinterpret_cast<double*>(dh + hm);
     float* red32 = reinterpret_cast<float*>(red64 + 128);
-    float* einv = red32 + 2 * 16 * kOnchipSlot;
-    float* mu = einv + m * m;                     // mu[m] = 0: rows outside the coarse space
-    float* qf = mu + ((m + 4) & ~3);
-    uint8_t* hsub = reinterpret_cast<uint8_t*>(qf + 16);
-    uint2* send = reinterpret_cast<uint2*>(hsub + ((pl.halo_max + 15) & ~15));
+    float* einv = red32 + 2 * 16 * kOnchipSlot;   // the rows of E^+ of the subdomains in `needl`
+    float* mu = einv + pl.need_max * m;           // mu[m] = 0: rows outside the coarse space
+    float* zq = mu + m4 + 4;                      // [2][m4]: Z^T q, double-buffered
+    uint8_t* hsub = reinterpret_cast<uint8_t*>(zq + 2 * m4);
+    uint8_t* needl = hsub + ((pl.halo_max + 15) & ~15);
+    uint2* send = reinterpret_cast<uint2*>(needl + ((pl.need_max + 15) & ~15));
     uint2* cent = send + pl.send_max;             // (local index of z, value bits)
     const int q0 = __ldg(pl.soff + rank), npos = __ldg(pl.soff + rank + 1) - q0;
     const int eb0 = npos > 0 ? __ldg(pl.ebase + q0) : 0;
     const int halo_self = __ldg(pl.halo_n + rank);
-    for (int i = threadIdx.x; i < zn; i += blockDim.x) zl[i] = 0.0f;
-    for (int i = threadIdx.x; i < m * m; i += blockDim.x) einv[i] = __ldg(pl.einv + i);
-    for (int i = threadIdx.x; i < ((m + 4) & ~3); i += blockDim.x) mu[i] = 0.0f;
-    for (int h = threadIdx.x; h < halo_self; h += blockDim.x) hsub[h] = __ldg(pl.hsub + (size_t)rank * pl.halo_max + h);
+    const int need_n = m ? __ldg(pl.need_n + rank) : 0;
+    for (int i = threadIdx.x; i < 3 * rows_max + hm; i += blockDim.x) zl[i] = 0.0f;   // z, w, D^{-1}
+    for (int i = threadIdx.x; i < 4 * hm; i += blockDim.x) recv[i] = 0.0f;            // recv, r_h, q_h
+    for (int h = threadIdx.x; h < hm; h += blockDim.x) {
+        const bool in = h < halo_self;
+        dh[h] = in ? __ldg(a.dinvf + __ldg(pl.hrow + (size_t)rank * pl.halo_max + h)) : 0.0f;
+        if (h < pl.halo_max) hsub[h] = in ? __ldg(pl.hsub + (size_t)rank * pl.halo_max + h) : (uint8_t)m;
+    }
+    for (int i = threadIdx.x; i < need_n * m; i += blockDim.x) {
+        const int idx = i / m;
+        einv[i] = __ldg(pl.einv + (size_t)__ldg(pl.need + (size_t)rank * pl.need_max + idx) * m + (i - idx * m));
+    }
+    for (int i = threadIdx.x; i < need_n; i += blockDim.x) needl[i] = __ldg(pl.need + (size_t)rank * pl.need_max + i);
+    for (int i = threadIdx.x; i < 3 * m4 + 4; i += blockDim.x) mu[i] = 0.0f;        // mu, zq
     // ---- rows of this thread: slice t of its warp is list position wid + nw * t of its CTA;
     // their matrix entries are copied to shared memory by the owning warp
     int nrow = 0;
@@ -207,13 +184,17 @@ static __global__ void __launch_bounds__(kOnchipThreads, 1) k_pcg_onchip(CoarseP
     auto in_space = [&](int t) { return grow_[t] >= 0; };
     auto lrow_of = [&](int t) { return 32 * (wid + nw * t) + lane; };
     const int spc = m ? nw / pl.wpg : 0;                       // subdomains per CTA
+    const int sh = m ? __ffs(spc) - 1 : 0;
     const int my_sub = m ? (rank * nw + wid) / pl.wpg : m;     // this warp's subdomain
+    // sends: the receive slot's cluster address (parity 0); warp w sends entries ws0 .. ws1 - 1
     const int ns0 = __ldg(pl.send_off + rank), nsend = __ldg(pl.send_off + rank + 1) - ns0;
     for (int i = threadIdx.x; i < nsend; i += blockDim.x) {
         const int d = __ldg(pl.send_dst + ns0 + i);   // x: local row | destination rank << 16
         send[i] = make_uint2((uint32_t)__ldg(pl.send_lr + ns0 + i) | ((uint32_t)(d >> 16) << 16),
-                             oc_map(zl + rows_max + (d & 0xFFFF), d >> 16));
+                             oc_map(recv + (d & 0xFFFF), d >> 16));
     }
+    const int ws0 = __ldg(pl.send_woff + rank * (nw + 1) + wid) - ns0;
+    const int ws1 = __ldg(pl.send_woff + rank * (nw + 1) + wid + 1) - ns0;
     if (threadIdx.x == 0) {
         oc_mbar_init(&mbar[0], 1);
         oc_mbar_init(&mbar[1], 1);
@@ -227,13 +208,13 @@ static __global__ void __launch_bounds__(kOnchipThreads, 1) k_pcg_onchip(CoarseP
     // remote slot addresses of the reductions: lane l < ncl stores into CTA l
     const uint32_t red64_remote = oc_map(red64, lane < ncl ? lane : 0);
     const uint32_t red32_remote = oc_map(red32, lane < ncl ? lane : 0);
-    // Cluster sums.  Partial sums go warp -> CTA (warp 0) -> every CTA's slot array, one
-    // hardware cluster barrier, then the ncl slots are added; all in a fixed order, so every
-    // CTA gets the same totals.  Consecutive reductions alternate between two slot sets, so a
-    // slot is rewritten only after the barrier that follows every read of it.
+    auto aborted_now = [&]() { return *reinterpret_cast<volatile int*>(&abort_flag) != 0; };
+    // FP64 cluster sums (outer loop).  Partial sums go warp -> CTA (warp 0) -> every CTA's
+    // slot array, one hardware cluster barrier, then the ncl slots are added; all in a fixed
+    // order, so every CTA gets the same totals, in every lane of warp 0, which alone does the
+    // FP64 scalar work (the FP64 pipe is narrow) and hands results to the CTA through `sc` and
+    // a __syncthreads.  Consecutive reductions alternate between two slot sets.
     int slot = 0;
-    // FP64: totals in every lane of warp 0, which alone does the FP64 scalar work (the FP64
-    // pipe is narrow) and hands results to the CTA through `sc` and a __syncthreads.
     auto cred64 = [&](auto& v, double (&tot)[4]) {
         constexpr int NR = sizeof(v) / sizeof(double);
 #pragma unroll
@@ -257,155 +238,167 @@ static __global__ void __launch_bounds__(kOnchipThreads, 1) k_pcg_onchip(CoarseP
         }
         slot ^= 1;
     };
-    // FP32 (inner iterations): the CTA partials travel as st.async stores into every CTA's
-    // slots, each completing bytes on that CTA's mbarrier (two, used alternately: data for
-    // reduction m+2 can only be sent once every CTA has contributed to m+1, that is after this
-    // CTA finished m); warp 0 waits (bounded) and adds the slots, the CTA reads the totals
-    // after a __syncthreads.  With `publish`, the CTA's new z goes to the neighbours' halos the
-    // same way (every CTA expects its halo size in bytes).  With `subs`, the warp sums of
-    // `subv` are added per subdomain and the spc subdomain sums of every CTA travel too; they
-    // stay in the slots (set `last_par`) for the coarse correction.  A wait that runs out sets
-    // the abort flag of every CTA; the solve then stops with CGP_ETIMEOUT.
-    int mred = 0, last_par = 0;
-    auto cred32 = [&](float (&v)[2], int nr, float subv, float (&tot)[2], bool publish, bool subs) -> bool {
-        const int ns = subs ? spc : 0;
-        for (int k = 0; k < nr; ++k) {
-            const float s = warp_sum(v[k]);
-            if (lane == 0) wsum32[wid][k] = s;
-        }
-        if (ns) {
-            const float s = warp_sum(subv);
-            if (lane == 0) wsum32[wid][nr] = s;
-        }
-        __syncthreads();
+    // One exchange of the FP32 inner iteration.  Each warp sends its rows of wl to the
+    // neighbours' receive buffers (parity par) as soon as it has them; the CTA's sums of v
+    // (three scalars) and, with the coarse space, the subdomain sums of tw (A z) and ur (r)
+    // go from warp 0 to every CTA's slots.  Every remote store completes bytes on the
+    // receiver's mbarrier of that parity (two, used alternately: data for exchange m + 2 can
+    // only be sent once every CTA has contributed to m + 1, so after this CTA finished m);
+    // warp 0 waits (bounded) for all of them, adds the scalar slots in a fixed order
+    // (identical totals in every CTA) and hands them to the CTA with the verdict through a
+    // __syncthreads.  A wait that runs out sets the abort flag of every CTA; the call then
+    // returns false in every thread of the CTA.
+    int mred = 0;
+    auto exchange = [&](const float (&v)[3], float tw, float ur, float (&tot)[3]) -> bool {
         const int par = mred & 1;
         const uint32_t phase = (uint32_t)(mred >> 1) & 1u;
         ++mred;
-        last_par = par;
-        const bool live = abort_flag == 0;
-        if (publish && live) {
-            for (int i = threadIdx.x; i < nsend; i += blockDim.x) {
+        __syncwarp();   // the warp's wl stores before its sends read them
+        if (!aborted_now()) {
+            const uint32_t hoff = (uint32_t)(4 * par * hm);
+            for (int i = ws0 + lane; i < ws1; i += 32) {
                 const uint2 sd = send[i];
-                oc_st_async(sd.y, zl[sd.x & 0xFFFF], mbar_remote[sd.x >> 16][par]);
+                oc_st_async(sd.y + hoff, wl[sd.x & 0xFFFF], mbar_remote[sd.x >> 16][par]);
             }
         }
+        constexpr int nv = MR > 0 ? 5 : 3;
+        const float x[5] = {v[0], v[1], v[2], tw, ur};
+#pragma unroll
+        for (int k = 0; k < nv; ++k) {
+            const float s = warp_sum(x[k]);
+            if (lane == 0) wsum32[wid][k] = s;
+        }
+        __syncthreads();
         if (wid == 0) {
-            float cs[2] = {0.0f, 0.0f};
-            for (int k = 0; k < nr; ++k) cs[k] = __shfl_sync(0xffffffffu, warp_sum(lane < nw ? wsum32[lane][k] : 0.0f), 0);
-            // subdomain g of this CTA = warps g * wpg .. g * wpg + wpg - 1
-            float gs = (ns && lane < nw) ? wsum32[lane][nr] : 0.0f;
-            for (int o = 1; o < (ns ? pl.wpg : 1); o <<= 1) gs += __shfl_down_sync(0xffffffffu, gs, o);
+            const bool live = !aborted_now();
+            float cs[3];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) cs[k] = __shfl_sync(0xffffffffu, warp_sum(lane < nw ? wsum32[lane][k] : 0.0f), 0);
             const bool sender = live && lane < ncl;
             const uint32_t dst = red32_remote + (uint32_t)(4 * ((par * 16 + rank) * kOnchipSlot));
-            if (sender)
-                for (int k = 0; k < nr; ++k) oc_st_async(dst + 4 * k, cs[k], mbar_remote[lane][par]);
-            // the subdomain sums, four at a time (16-byte stores; unused ones are zero)
-            const int nv4 = (ns + 3) >> 2;
-            for (int g = 0; g < nv4; ++g) {
-                float x[4];
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const int gg = 4 * g + u;
-                    const float y = __shfl_sync(0xffffffffu, gs, (gg < ns ? gg : 0) * (ns ? pl.wpg : 1));
-                    x[u] = gg < ns ? y : 0.0f;
+            const uint32_t mb = mbar_remote[lane < ncl ? lane : 0][par];
+            if (sender) oc_st_async4(dst, cs[0], cs[1], cs[2], 0.0f, mb);
+            if constexpr (MR > 0) {
+                // subdomain g of this CTA = warps g wpg .. g wpg + wpg - 1; its sums go out as
+                // eight values per vector (unused ones zero), four to a 16-byte store
+                float gt = lane < nw ? wsum32[lane][3] : 0.0f, gu = lane < nw ? wsum32[lane][4] : 0.0f;
+                for (int o = 1; o < pl.wpg; o <<= 1) {
+                    gt += __shfl_down_sync(0xffffffffu, gt, o);
+                    gu += __shfl_down_sync(0xffffffffu, gu, o);
                 }
-                if (sender)
-                    oc_st_async4(dst + 4 * (kOnchipSubOff + 4 * g), x[0], x[1], x[2], x[3], mbar_remote[lane][par]);
+                float tv[kOnchipMaxSubPerCta], uv[kOnchipMaxSubPerCta];
+#pragma unroll
+                for (int g = 0; g < kOnchipMaxSubPerCta; ++g) {
+                    const int from = (g < spc ? g : 0) * pl.wpg;
+                    const float y1 = __shfl_sync(0xffffffffu, gt, from), y2 = __shfl_sync(0xffffffffu, gu, from);
+                    tv[g] = g < spc ? y1 : 0.0f;
+                    uv[g] = g < spc ? y2 : 0.0f;
+                }
+                if (sender) {
+                    oc_st_async4(dst + 4 * kOnchipSubW, tv[0], tv[1], tv[2], tv[3], mb);
+                    oc_st_async4(dst + 4 * kOnchipSubW + 16, tv[4], tv[5], tv[6], tv[7], mb);
+                    oc_st_async4(dst + 4 * kOnchipSubR, uv[0], uv[1], uv[2], uv[3], mb);
+                    oc_st_async4(dst + 4 * kOnchipSubR + 16, uv[4], uv[5], uv[6], uv[7], mb);
+                }
             }
             // (the wait test hook expects 4 bytes more than anyone sends)
             if (lane == 0)
-                oc_mbar_arrive_expect(&mbar[par], (uint32_t)(ncl * (4 * nr + 16 * nv4) + (publish ? 4 * halo_self : 0) +
+                oc_mbar_arrive_expect(&mbar[par], (uint32_t)(ncl * (MR > 0 ? 4 * kOnchipSlot : 16) + 4 * halo_self +
                                                              (a.wait_test ? 4 : 0)));
             bool ok = live;
             if (ok) {
                 const long long t0 = clock64();
                 const long long limit = a.wait_test ? kOnchipWaitCyclesTest : kOnchipWaitCycles;
                 while (!oc_mbar_try(&mbar[par], phase)) {
-                    if (abort_flag || clock64() - t0 > limit) {
+                    if (aborted_now() || clock64() - t0 > limit) {
                         ok = false;
                         break;
                     }
                 }
             }
             ok = __all_sync(0xffffffffu, ok);
-            for (int k = 0; k < nr; ++k) {
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
                 const float t = __shfl_sync(0xffffffffu, warp_sum(lane < ncl ? red32[(par * 16 + lane) * kOnchipSlot + k] : 0.0f), 0);
                 if (lane == 0) tot32[k] = t;
             }
             if (!ok && lane < ncl) asm volatile("st.shared::cluster.u32 [%0], 1;" ::"r"(oc_map(&abort_flag, lane)) : "memory");
+            if (lane == 0) tot32[3] = (ok && !aborted_now()) ? 1.0f : 0.0f;
         }
         __syncthreads();
-        for (int k = 0; k < nr; ++k) tot[k] = tot32[k];
-        return abort_flag == 0;
-    };
-    // Coarse correction after a reduction that carried the subdomain sums s = Z^T r (slot set
-    // `par`): warp w forms rows w R .. w R + R - 1 of mu = E^+ s (R = m / 16, at least 1),
-    // then z += mu[subdomain] in the own rows and the halo.  Returns s^T mu, the coarse part
-    // of <r, z>; identical in every CTA.
-    float z_[kOnchipRows];
-    constexpr int mrows = MR > 0 ? MR : 1, cpl = MR == 8 ? 4 : (MR == 4 ? 2 : 1);
-    auto coarse_fix = [&](int par) -> float {
-        const float* sl = red32 + par * 16 * kOnchipSlot + kOnchipSubOff;
-        const int sh = __ffs(spc) - 1;
-        auto s_at = [&](int j) -> const float& { return sl[(j >> sh) * kOnchipSlot + (j & (spc - 1))]; };
-        const int c0 = lane * cpl;
-        const bool has = c0 < m;
-        float sv[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-        if (has) {   // cpl > 1 only with spc >= 4: the columns lie in one CTA's slot
-            if constexpr (cpl == 4) {
-                const float4 x = *reinterpret_cast<const float4*>(&s_at(c0));
-                sv[0] = x.x; sv[1] = x.y; sv[2] = x.z; sv[3] = x.w;
-            } else if constexpr (cpl == 2) {
-                const float2 x = *reinterpret_cast<const float2*>(&s_at(c0));
-                sv[0] = x.x; sv[1] = x.y;
-            } else {
-                sv[0] = s_at(c0);
-            }
-        }
-        const int row0 = wid * mrows;
-        float part = 0.0f;
-        if (row0 < m) {
-            int r = 0;
-            const float acc = oc_mu_rows<mrows, cpl>(einv + row0 * m, m, has, sv, lane, r);
-            if ((lane & (32 / mrows - 1)) == 0) {
-                mu[row0 + r] = acc;
-                part = s_at(row0 + r) * acc;
-            }
-        }
-        part = warp_sum(part);
-        if (lane == 0) qf[wid] = part;
-        __syncthreads();
-        static_assert(kOnchipWarps == 16, "the partials of s^T mu are summed as four float4");
-        const float4* q4 = reinterpret_cast<const float4*>(qf);   // 16 warp partials, fixed-order tree
-        const float4 qa = q4[0], qb = q4[1], qc = q4[2], qd = q4[3];
-        const float q = (((qa.x + qa.y) + (qa.z + qa.w)) + ((qb.x + qb.y) + (qb.z + qb.w))) +
-                        (((qc.x + qc.y) + (qc.z + qc.w)) + ((qd.x + qd.y) + (qd.z + qd.w)));
-        const float mw = mu[my_sub];
 #pragma unroll
-        for (int t = 0; t < kOnchipRows; ++t) {
-            if (t >= nrow) break;
-            if (in_space(t)) z_[t] += mw;
-            zl[lrow_of(t)] = z_[t];
+        for (int k = 0; k < 3; ++k) tot[k] = tot32[k];
+        return tot32[3] != 0.0f;
+    };
+    // The coarse correction after exchange `par`: s = Z^T r of the current r, from the slot sums
+    // of that exchange (u = Z^T r and t = Z^T A z of the previous iterate): s = u - al zn with
+    // zn = t + be zq the new Z^T q (first call of a restart: s = u); mu = E^+ s for the
+    // subdomains this CTA corrects (one warp per row of E^+), then z += mu[subdomain] in the
+    // own rows and the halo, which hold D^{-1} r.  Ends with the CTA's z in shared memory.
+    float z_[kOnchipRows];
+    int zpar = 0;
+    auto coarse = [&](int par, float al, float be, bool first) {
+        if constexpr (MR > 0) {
+            constexpr int cpl = MR == 8 ? 4 : (MR == 4 ? 2 : 1);
+            const int c0 = lane * cpl;
+            float sv[cpl];
+#pragma unroll
+            for (int c = 0; c < cpl; ++c) sv[c] = 0.0f;
+            if (c0 < m) {   // cpl > 1 only with spc >= cpl: the columns lie in one CTA's slot
+                const float* sl = red32 + (par * 16 + (c0 >> sh)) * kOnchipSlot + (c0 & (spc - 1));
+                const float* zo = zq + zpar * m4 + c0;
+                float* zn_out = zq + (zpar ^ 1) * m4 + c0;
+#pragma unroll
+                for (int c = 0; c < cpl; ++c) {
+                    const float zn = first ? 0.0f : fmaf(be, zo[c], sl[kOnchipSubW + c]);
+                    sv[c] = fmaf(-al, zn, sl[kOnchipSubR + c]);
+                    if (wid == 0) zn_out[c] = zn;
+                }
+            }
+            zpar ^= 1;
+            for (int idx = wid; idx < need_n; idx += nw) {
+                float acc = 0.0f;
+                if (c0 < m) {
+                    const float* er = einv + idx * m + c0;
+#pragma unroll
+                    for (int c = 0; c < cpl; ++c) acc = fmaf(er[c], sv[c], acc);
+                }
+                acc = warp_sum(acc);
+                if (lane == 0) mu[needl[idx]] = acc;
+            }
+            __syncthreads();
+            const float mw = mu[my_sub];
+#pragma unroll
+            for (int t = 0; t < kOnchipRows; ++t) {
+                if (t >= nrow) break;
+                if (in_space(t)) z_[t] += mw;
+                zl[lrow_of(t)] = z_[t];
+            }
+            for (int h = threadIdx.x; h < halo_self; h += blockDim.x) zl[rows_max + h] += mu[hsub[h]];
+        } else {
+#pragma unroll
+            for (int t = 0; t < kOnchipRows; ++t) {
+                if (t >= nrow) break;
+                zl[lrow_of(t)] = z_[t];
+            }
         }
-        for (int h = threadIdx.x; h < halo_self; h += blockDim.x) zl[rows_max + h] += mu[hsub[h]];
         __syncthreads();
-        return q;
     };
     const double mean = a.project ? a.st->mean : 0.0;
     const double tol2 = a.tol2;
     double* xv = a.x;
-    float e_[kOnchipRows], r_[kOnchipRows], p_[kOnchipRows], q_[kOnchipRows], d_[kOnchipRows];
+    float e_[kOnchipRows], r_[kOnchipRows], p_[kOnchipRows], q_[kOnchipRows];
 #pragma unroll
     for (int t = 0; t < kOnchipRows; ++t) {
-        e_[t] = r_[t] = z_[t] = p_[t] = q_[t] = d_[t] = 0.0f;
+        e_[t] = r_[t] = z_[t] = p_[t] = q_[t] = 0.0f;
         const int i = row_of(t);
         if (i >= 0) {
-            d_[t] = __ldg(a.dinvf + i);
+            dl[lrow_of(t)] = __ldg(a.dinvf + i);
             if (a.project) a.b[i] -= mean;
             if (a.zero_x) __stcg(xv + i, 0.0);
         }
     }
-    oc_barrier();   // matrix and sends loaded, z zeroed, b projected and x zeroed where asked
+    oc_barrier();   // matrix, plan and D^{-1} loaded, b projected and x zeroed where asked
     // FP64 row of A times a global vector (`ro`: v is read-only during the launch), from the
     // SELL-32 arrays: entry k of row i sits at ptr[i / 32] + 32 k + i % 32 (padding: value 0)
     auto row_a = [&](int t, const double* v, bool ro) {
@@ -550,107 +543,135 @@ static __global__ void __launch_bounds__(kOnchipThreads, 1) k_pcg_onchip(CoarseP
             }
         }
         const float inv = (float)sc.inv;
-        // ---- inner classical PCG in FP32 on the scaled residual; every warp carries the same
-        // scalars (rz, beta, rr_best), computed from the same totals.  Pass k = -1 only forms
-        // the first z (the scaled residual, its Jacobi part, its reduction and the coarse
-        // correction), so each reduction and the coarse correction have a single call site.
-        float beta = 0.0f, rr_best = INFINITY, rz = 0.0f;
         const float stop2 = sc.stop2;
+        // ---- inner PCG in FP32 on the scaled residual, in the one-exchange form (Chronopoulos
+        // and Gear): each iteration forms w = A z, then one exchange carries <r, z>, <z, w>,
+        // <r, r>, Z^T w, Z^T r and the halo copy of w; alpha and beta follow from those
+        // (alpha = <r, z> / (<z, w> - beta <r, z> / alpha_prev)), every CTA updates q, r and z
+        // of its halo rows by the same recurrences as their owners (so z of the halo needs no
+        // second exchange), and Z^T r of the next iterate by its own recurrence.  Every warp
+        // carries the same scalars, computed from the same totals.
+        float gam_prev = 1.0f, alp_prev = 1.0f, rr_best = INFINITY;
         int best_k = 0;
         bool drift = false, aborted = false;
-        for (int k = -1;; ++k) {
-            float acc2[2] = {0.0f, 0.0f}, s2 = 0.0f;
-            if (k < 0) {
+        {
+            // the scaled residual: its halo copy and Z^T r travel in the first exchange
+            float ur = 0.0f;
 #pragma unroll
-                for (int t = 0; t < kOnchipRows; ++t) {
-                    if (row_of(t) >= 0) {
-                        r_[t] *= inv;
-                        z_[t] = d_[t] * r_[t];
-                        e_[t] = 0.0f;
-                        p_[t] = 0.0f;
-                        q_[t] = 0.0f;
-                        zl[lrow_of(t)] = z_[t];
-                        acc2[0] = fmaf(r_[t], z_[t], acc2[0]);
-                        acc2[1] = fmaf(r_[t], r_[t], acc2[1]);
-                        if (in_space(t)) s2 += r_[t];
-                    }
+            for (int t = 0; t < kOnchipRows; ++t) {
+                if (t >= nrow) break;
+                e_[t] = p_[t] = q_[t] = 0.0f;
+                if (row_of(t) >= 0) {
+                    r_[t] *= inv;
+                    if (in_space(t)) ur += r_[t];
+                } else {
+                    r_[t] = 0.0f;
                 }
+                wl[lrow_of(t)] = r_[t];
+            }
+            const float v0[3] = {0.0f, 0.0f, 0.0f};
+            float t0[3];
+            if (!exchange(v0, 0.0f, ur, t0)) {
+                aborted = true;
             } else {
-                if (iters >= a.maxit) break;
-                // phase A: w = A z (local gathers), p = z + beta p, q = w + beta q, <p, q>
-                const float be = beta;
-                float pq_acc[2] = {0.0f, 0.0f};
+                const float* rv = recv + ((mred - 1) & 1) * hm;
+                for (int h = threadIdx.x; h < halo_self; h += blockDim.x) {
+                    const float x = rv[h];
+                    rh[h] = x;
+                    qh[h] = 0.0f;
+                    zl[rows_max + h] = dh[h] * x;
+                }
 #pragma unroll
                 for (int t = 0; t < kOnchipRows; ++t) {
                     if (t >= nrow) break;
-                    const uint2* ce = cent + base_[t] + lane;
-                    const int w = width_[t];
-                    float s = 0.0f;
-                    for (int k = 0; k < w; k += 4) {
-                        const uint2 e0 = ce[32 * k], e1 = ce[32 * (k + 1)], e2 = ce[32 * (k + 2)], e3 = ce[32 * (k + 3)];
-                        const float g0 = zl[e0.x], g1 = zl[e1.x], g2 = zl[e2.x], g3 = zl[e3.x];
-                        s = fmaf(__uint_as_float(e0.y), g0, s);
-                        s = fmaf(__uint_as_float(e1.y), g1, s);
-                        s = fmaf(__uint_as_float(e2.y), g2, s);
-                        s = fmaf(__uint_as_float(e3.y), g3, s);
-                    }
-                    if (row_of(t) >= 0) {
-                        p_[t] = fmaf(be, p_[t], z_[t]);
-                        q_[t] = fmaf(be, q_[t], s);
-                        pq_acc[0] = fmaf(p_[t], q_[t], pq_acc[0]);
-                    }
+                    z_[t] = dl[lrow_of(t)] * r_[t];
                 }
-                float pq[2];
-                if (!cred32(pq_acc, 1, 0.0f, pq, false, false)) {
-                    aborted = true;
-                    break;
-                }
-                if (!(pq[0] != 0.0f) || !isfinite(pq[0])) break;   // restart from the true residual
-                const float al = rz / pq[0];
-                // phase B (own rows): e += alpha p, r -= alpha q, z = D^{-1} r (+ the coarse
-                // correction once Z^T r is known)
+                coarse((mred - 1) & 1, 0.0f, 0.0f, true);
+            }
+        }
+        for (int k = 0; !aborted; ++k) {
+            if (iters >= a.maxit) break;
+            // w = A z (local gathers) and the sums of this iterate
+            float v[3] = {0.0f, 0.0f, 0.0f}, tw = 0.0f, ur = 0.0f;
 #pragma unroll
-                for (int t = 0; t < kOnchipRows; ++t) {
-                    if (row_of(t) >= 0) {
-                        e_[t] = fmaf(al, p_[t], e_[t]);
-                        r_[t] = fmaf(-al, q_[t], r_[t]);
-                        z_[t] = d_[t] * r_[t];
-                        zl[lrow_of(t)] = z_[t];
-                        acc2[0] = fmaf(r_[t], z_[t], acc2[0]);
-                        acc2[1] = fmaf(r_[t], r_[t], acc2[1]);
-                        if (in_space(t)) s2 += r_[t];
+            for (int t = 0; t < kOnchipRows; ++t) {
+                if (t >= nrow) break;
+                const uint2* ce = cent + base_[t] + lane;
+                const int w = width_[t];
+                float s = 0.0f;
+                for (int k = 0; k < w; k += 4) {
+                    const uint2 e0 = ce[32 * k], e1 = ce[32 * (k + 1)], e2 = ce[32 * (k + 2)], e3 = ce[32 * (k + 3)];
+                    const float g0 = zl[e0.x], g1 = zl[e1.x], g2 = zl[e2.x], g3 = zl[e3.x];
+                    s = fmaf(__uint_as_float(e0.y), g0, s);
+                    s = fmaf(__uint_as_float(e1.y), g1, s);
+                    s = fmaf(__uint_as_float(e2.y), g2, s);
+                    s = fmaf(__uint_as_float(e3.y), g3, s);
+                }
+                wl[lrow_of(t)] = s;
+                if (row_of(t) >= 0) {
+                    v[0] = fmaf(r_[t], z_[t], v[0]);
+                    v[1] = fmaf(z_[t], s, v[1]);
+                    v[2] = fmaf(r_[t], r_[t], v[2]);
+                    if (in_space(t)) {
+                        tw += s;
+                        ur += r_[t];
                     }
                 }
             }
-            // <r, D^{-1} r>, <r, r> and Z^T r; the new z goes to every halo with them
-            float t2[2];
-            if (!cred32(acc2, 2, s2, t2, true, MR > 0)) {
+            float tt[3];
+            if (!exchange(v, tw, ur, tt)) {
                 aborted = true;
                 break;
             }
-            if (k >= 0) ++iters;
-            if (!isfinite(t2[0]) || !isfinite(t2[1])) {
+            const int par = (mred - 1) & 1;
+            const float gam = tt[0], del = tt[1], rho = tt[2];
+            if (!isfinite(gam) || !isfinite(del) || !isfinite(rho)) {
                 drift = true;
                 break;
             }
-            if (k >= 0 && (t2[1] <= stop2 || t2[1] == 0.0f)) break;
-            float rzn = t2[0];
-            if constexpr (MR > 0) rzn += coarse_fix(last_par);
-            if (!(rzn > 0.0f)) break;   // restart from the true residual
-            if (k >= 0) {
-                beta = rzn / rz;
-                if (t2[1] < 0.5f * rr_best) {
-                    rr_best = t2[1];
+            if (k >= 1) {   // rho = <r, r> of the iterate e holds
+                if (rho <= stop2 || rho == 0.0f) break;
+                if (rho < 0.5f * rr_best) {
+                    rr_best = rho;
                     best_k = k;
-                } else if (t2[1] > 1e4f * rr_best) {
+                } else if (rho > 1e4f * rr_best) {
                     drift = true;
                     break;
                 } else if (k - best_k > kStagnation32) {
-                    rz = rzn;
                     break;
                 }
             }
-            rz = rzn;
+            if (!(gam > 0.0f)) break;   // restart from the true residual
+            const float be = k >= 1 ? gam / gam_prev : 0.0f;
+            const float den = k >= 1 ? del - be * gam / alp_prev : del;
+            if (!(den > 0.0f) || !isfinite(den)) break;
+            const float al = gam / den;
+            gam_prev = gam;
+            alp_prev = al;
+            ++iters;
+            // p = z + beta p, q = w + beta q (= A p), e += alpha p, r -= alpha q, z = D^{-1} r
+#pragma unroll
+            for (int t = 0; t < kOnchipRows; ++t) {
+                if (t >= nrow) break;
+                if (row_of(t) >= 0) {
+                    const int l = lrow_of(t);
+                    p_[t] = fmaf(be, p_[t], z_[t]);
+                    q_[t] = fmaf(be, q_[t], wl[l]);
+                    e_[t] = fmaf(al, p_[t], e_[t]);
+                    r_[t] = fmaf(-al, q_[t], r_[t]);
+                    z_[t] = dl[l] * r_[t];
+                }
+            }
+            // the same for the halo rows, from the owners' w
+            const float* rv = recv + par * hm;
+            for (int h = threadIdx.x; h < halo_self; h += blockDim.x) {
+                const float qv = fmaf(be, qh[h], rv[h]);
+                const float r = fmaf(-al, qv, rh[h]);
+                qh[h] = qv;
+                rh[h] = r;
+                zl[rows_max + h] = dh[h] * r;
+            }
+            coarse(par, al, be, false);
         }
         if (aborted) {
             status = CGP_ETIMEOUT;

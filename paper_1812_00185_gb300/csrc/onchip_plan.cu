@@ -192,8 +192,37 @@ bool onchip_plan(int n, const std::vector<int32_t>& rowptr, const std::vector<in
     for (auto& e : li_of)
         if (e < 0) e = P.rows_max + (-1 - e);
     P.hsub.assign((size_t)ncl * P.halo_max, (uint8_t)P.nsub);
+    P.hrow.assign((size_t)ncl * P.halo_max, 0);
     for (int c = 0; c < ncl; ++c)
-        for (int h = 0; h < (int)halo_rows[c].size(); ++h) P.hsub[(size_t)c * P.halo_max + h] = (uint8_t)P.sub[halo_rows[c][h]];
+        for (int h = 0; h < (int)halo_rows[c].size(); ++h) {
+            P.hsub[(size_t)c * P.halo_max + h] = (uint8_t)P.sub[halo_rows[c][h]];
+            P.hrow[(size_t)c * P.halo_max + h] = halo_rows[c][h];
+        }
+    // the subdomains each CTA corrects: its own (in order), then those of its halo rows
+    std::vector<std::vector<int>> need(ncl);
+    if (P.nsub) {
+        for (int c = 0; c < ncl; ++c) {
+            std::vector<char> seen(P.nsub, 0);
+            for (int j = c * sub_per_cta; j < (c + 1) * sub_per_cta; ++j) {
+                seen[j] = 1;
+                need[c].push_back(j);
+            }
+            for (int i : halo_rows[c]) {
+                const int j = P.sub[i];
+                if (j < P.nsub && !seen[j]) {
+                    seen[j] = 1;
+                    need[c].push_back(j);
+                }
+            }
+            P.need_max = std::max(P.need_max, (int)need[c].size());
+        }
+    }
+    P.need.assign((size_t)ncl * P.need_max, 0);
+    P.need_n.assign(ncl, 0);
+    for (int c = 0; c < ncl; ++c) {
+        P.need_n[c] = (int32_t)need[c].size();
+        for (int k = 0; k < (int)need[c].size(); ++k) P.need[(size_t)c * P.need_max + k] = (uint8_t)need[c][k];
+    }
     // ---- entry order of every slice (bank-aware) and the local index of each entry
     P.li.assign(eb, 0);
     P.src.assign(eb, -1);
@@ -253,16 +282,27 @@ bool onchip_plan(int n, const std::vector<int32_t>& rowptr, const std::vector<in
                     }
                 }
         }
+    // sends grouped by the warp that owns their row (local row 32 (w + 16 t) + lane)
     P.send_off.assign(ncl + 1, 0);
+    P.send_woff.assign((size_t)ncl * (W + 1), 0);
     for (int c = 0; c < ncl; ++c) {
-        P.send_off[c + 1] = P.send_off[c] + (int)sends[c].size();
-        P.send_max = std::max(P.send_max, (int)sends[c].size());
-        for (auto& pr : sends[c]) {
+        auto& sc = sends[c];
+        std::stable_sort(sc.begin(), sc.end(), [&](const std::pair<int, int>& a, const std::pair<int, int>& b) {
+            return (a.first / 32) % W < (b.first / 32) % W;
+        });
+        P.send_off[c + 1] = P.send_off[c] + (int)sc.size();
+        P.send_max = std::max(P.send_max, (int)sc.size());
+        int k = 0;
+        for (int w = 0; w <= W; ++w) {
+            while (k < (int)sc.size() && (sc[k].first / 32) % W < w) ++k;
+            P.send_woff[(size_t)c * (W + 1) + w] = P.send_off[c] + k;
+        }
+        for (auto& pr : sc) {
             P.send_lr.push_back(pr.first);
             P.send_dst.push_back(pr.second);
         }
     }
-    P.bytes = onchip_smem_bytes(P.rows_max, P.halo_max, P.send_max, P.ent_max, P.nsub);
+    P.bytes = onchip_smem_bytes(P.rows_max, P.halo_max, P.send_max, P.ent_max, P.nsub, P.need_max);
     return P.bytes <= smem_limit;
 }
 

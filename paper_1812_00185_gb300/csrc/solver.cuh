@@ -83,6 +83,8 @@ struct Solver {
     int32_t *oc_grow = nullptr, *oc_soff = nullptr, *oc_ebase = nullptr, *oc_width = nullptr, *oc_li = nullptr;
     int32_t *oc_src = nullptr, *oc_send_lr = nullptr, *oc_send_dst = nullptr, *oc_send_off = nullptr, *oc_halo_n = nullptr;
     uint8_t* oc_hsub = nullptr;
+    int32_t *oc_hrow = nullptr, *oc_send_woff = nullptr, *oc_need_n = nullptr;
+    uint8_t* oc_need = nullptr;
     float* oc_einv = nullptr;
     OnchipPlan onchip{};
     unsigned int* bar_count = nullptr;   // grid barrier counter, followed by the error word

@@ -796,11 +796,15 @@ int choose_coarse_solver(Solver& s, cudaStream_t st) {
                     CGP_CUDA(up(s.oc_send_off, P.send_off));
                     CGP_CUDA(up(s.oc_halo_n, P.halo_n));
                     CGP_CUDA(up(s.oc_hsub, P.hsub));
+                    CGP_CUDA(up(s.oc_hrow, P.hrow));
+                    CGP_CUDA(up(s.oc_send_woff, P.send_woff));
                     CGP_CUDA(up(s.oc_einv, P.einv));
+                    CGP_CUDA(up(s.oc_need, P.need));
+                    CGP_CUDA(up(s.oc_need_n, P.need_n));
                     s.onchip = OnchipPlan{s.oc_grow, s.oc_soff, s.oc_ebase, s.oc_width, s.oc_li, s.oc_src,
-                                          s.oc_send_lr, s.oc_send_dst, s.oc_send_off, s.oc_halo_n, s.oc_hsub,
-                                          s.oc_einv, P.rows_max, P.halo_max, P.send_max, (int)P.ent_max,
-                                          P.nsub, P.wpg};
+                                          s.oc_send_lr, s.oc_send_dst, s.oc_send_off, s.oc_send_woff, s.oc_halo_n,
+                                          s.oc_hrow, s.oc_hsub, s.oc_einv, s.oc_need, s.oc_need_n, P.rows_max,
+                                          P.halo_max, P.send_max, (int)P.ent_max, P.nsub, P.wpg, P.need_max};
                     s.onchip_bytes = P.bytes;
                     s.cluster_size = cs;
                     break;

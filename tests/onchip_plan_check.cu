@@ -104,7 +104,35 @@ int main(int argc, char** argv) {
             }
             CHECK(halo[c][h] >= 0, "halo slot %d of CTA %d never sent", h, c);
             CHECK(hs == (P.nsub ? P.sub[halo[c][h]] : 0), "subdomain of halo slot %d of CTA %d", h, c);
+            CHECK(P.hrow[(size_t)c * P.halo_max + h] == halo[c][h], "global row of halo slot %d of CTA %d", h, c);
         }
+    // ---- the sends of each warp: a contiguous segment, rows the warp owns
+    CHECK((int)P.send_woff.size() == ncl * (W + 1), "send_woff size");
+    for (int c = 0; c < ncl; ++c) {
+        CHECK(P.send_woff[c * (W + 1)] == P.send_off[c] && P.send_woff[c * (W + 1) + W] == P.send_off[c + 1],
+              "send segments of CTA %d", c);
+        for (int w = 0; w < W; ++w) {
+            CHECK(P.send_woff[c * (W + 1) + w] <= P.send_woff[c * (W + 1) + w + 1], "send segment order");
+            for (int i = P.send_woff[c * (W + 1) + w]; i < P.send_woff[c * (W + 1) + w + 1]; ++i)
+                CHECK((P.send_lr[i] / 32) % W == w, "send %d of CTA %d not owned by warp %d", i, c, w);
+        }
+    }
+    // ---- the subdomains each CTA corrects: its own first, then every one of its halo rows,
+    // each once
+    CHECK((int)P.need_n.size() == ncl && (int)P.need.size() == ncl * P.need_max, "need sizes");
+    for (int c = 0; c < ncl && P.nsub; ++c) {
+        std::vector<int> cnt(P.nsub, 0);
+        CHECK(P.need_n[c] <= P.need_max, "need_n");
+        for (int k = 0; k < P.need_n[c]; ++k) {
+            const int j = P.need[(size_t)c * P.need_max + k];
+            CHECK(j < P.nsub && cnt[j]++ == 0, "need list of CTA %d", c);
+            if (k < spc) CHECK(j == c * spc + k, "own subdomains of CTA %d first", c);
+        }
+        for (int h = 0; h < P.halo_n[c]; ++h) {
+            const int j = P.hsub[(size_t)c * P.halo_max + h];
+            CHECK(j == P.nsub || cnt[j] == 1, "halo subdomain %d of CTA %d not corrected", j, c);
+        }
+    }
     // ---- every local entry: a real entry of its own row, or padding reading its own row
     std::vector<int> seen(ptr[S], 0);
     for (int c = 0; c < ncl; ++c) {
@@ -198,7 +226,8 @@ int main(int argc, char** argv) {
             }
         CHECK(r1 <= 1e-4 * emax && r2 <= 1e-4 * xmax, "pseudo-inverse identities: %g %g", r1 / emax, r2 / xmax);
     }
-    CHECK(P.bytes == onchip_smem_bytes(P.rows_max, P.halo_max, P.send_max, P.ent_max, P.nsub) && P.bytes <= limit,
+    CHECK(P.bytes == onchip_smem_bytes(P.rows_max, P.halo_max, P.send_max, P.ent_max, P.nsub, P.need_max) &&
+              P.bytes <= limit,
           "bytes");
     printf("OK %d %d %d %lld %d %zu\n", P.rows_max, P.halo_max, P.send_max, (long long)P.ent_max, P.nsub, P.bytes);
     return 0;

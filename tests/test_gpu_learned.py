@@ -146,3 +146,37 @@ def test_record_pairs_matches_the_step_by_step_record(cg):
         assert np.array_equal(rh[k], b.vector(cg.CGP_VEC_RHS_C))
         assert np.array_equal(tg[k], b.vector(cg.CGP_VEC_PHI_C)[:nc])
     a.close(); b.close(); mesh.close()
+
+
+def test_gate_turns_a_useless_network_off(cg):
+    """A network whose prediction is noise buys nothing over the projection start: after
+    eight such steps the coarse solve stops evaluating it (for 64 steps), the fields stay
+    those of the projection form, and the iteration count stays that of the projection."""
+    from paper_1812_00185_gb300.learned import init_params
+    common = dict(chi=1, k=1, bc_kind=cg.CGP_BC_CHANNEL, bc_param=(0.3, 0.41), tol_mom=1e-10, tol_poisson=1e-8,
+                  tol_mass=1e-10, precision=cg.CGP_MIXED)
+    base = channel_cylinder_mesh(seed=11, h=0.03)
+    mesh = cg.Mesh(base.xy, base.tri, base.tag, 2)
+    net = cg.cgp_mlp_create(mesh.handle, 1, 1)
+    p = init_params(5)
+    p[p.size - 129:p.size - 1] *= 1000.0        # a large, meaningless correction
+    cg.cgp_mlp_set_params(net, p)
+    out = {}
+    for mode in (cg.CGP_GUESS_PROJ, cg.CGP_GUESS_LEARNED):
+        s = cg.Solver(mesh, cg.make_params(1000.0, 0.002, guess=mode, **common))
+        if mode == cg.CGP_GUESS_LEARNED:
+            cg.cgp_guess_set(s.handle, net)
+        s.step(40)
+        U, P, t, st, rc = s.fields()
+        assert rc == 0
+        out[mode] = (U, P, st)
+        s.close()
+    (Up, Pp, sp), (Ul, Pl, sl) = out[cg.CGP_GUESS_PROJ], out[cg.CGP_GUESS_LEARNED]
+    print("noise network over 40 steps: learned start used in %d steps; coarse iterations %d (projection %d)"
+          % (sl["guess_used"], sl["sum_it_poisson"], sp["sum_it_poisson"]))
+    assert 1 <= sl["guess_used"] <= 9
+    assert sl["sum_it_poisson"] <= 1.05 * sp["sum_it_poisson"]
+    assert np.linalg.norm(Ul - Up) / np.linalg.norm(Up) < 1e-6
+    assert np.linalg.norm(Pl - Pp) / np.linalg.norm(Pp) < 1e-5
+    cg.cgp_mlp_destroy(net)
+    mesh.close()
