@@ -105,7 +105,7 @@ struct OnchipScalars {
 };
 
 // MR: nsub / 16 (at least 1) with the coarse correction, 0 without; it fixes how many columns
-// of an E^+ row a lane holds (4, 2 or 1)
+// of an E^+ row a lane holds (4, 2 or 1, interleaved across the lanes)
 template <int MR>
 static __global__ void __launch_bounds__(kOnchipThreads, 1) k_pcg_onchip(CoarsePcgArgs a, OnchipPlan pl) {
     namespace cg = cooperative_groups;
@@ -339,29 +339,30 @@ static __global__ void __launch_bounds__(kOnchipThreads, 1) k_pcg_onchip(CoarseP
     int zpar = 0;
     auto coarse = [&](int par, float al, float be, bool first) {
         if constexpr (MR > 0) {
+            // lane l holds columns l, l + 32, ... (consecutive lanes, consecutive words)
             constexpr int cpl = MR == 8 ? 4 : (MR == 4 ? 2 : 1);
-            const int c0 = lane * cpl;
             float sv[cpl];
+            const float* zo = zq + zpar * m4;
+            float* zn_out = zq + (zpar ^ 1) * m4;
 #pragma unroll
-            for (int c = 0; c < cpl; ++c) sv[c] = 0.0f;
-            if (c0 < m) {   // cpl > 1 only with spc >= cpl: the columns lie in one CTA's slot
-                const float* sl = red32 + (par * 16 + (c0 >> sh)) * kOnchipSlot + (c0 & (spc - 1));
-                const float* zo = zq + zpar * m4 + c0;
-                float* zn_out = zq + (zpar ^ 1) * m4 + c0;
-#pragma unroll
-                for (int c = 0; c < cpl; ++c) {
-                    const float zn = first ? 0.0f : fmaf(be, zo[c], sl[kOnchipSubW + c]);
-                    sv[c] = fmaf(-al, zn, sl[kOnchipSubR + c]);
-                    if (wid == 0) zn_out[c] = zn;
+            for (int c = 0; c < cpl; ++c) {
+                const int j = lane + 32 * c;
+                sv[c] = 0.0f;
+                if (j < m) {
+                    const float* sl = red32 + (par * 16 + (j >> sh)) * kOnchipSlot + (j & (spc - 1));
+                    const float zn = first ? 0.0f : fmaf(be, zo[j], sl[kOnchipSubW]);
+                    sv[c] = fmaf(-al, zn, sl[kOnchipSubR]);
+                    if (wid == 0) zn_out[j] = zn;
                 }
             }
             zpar ^= 1;
             for (int idx = wid; idx < need_n; idx += nw) {
+                const float* er = einv + idx * m;
                 float acc = 0.0f;
-                if (c0 < m) {
-                    const float* er = einv + idx * m + c0;
 #pragma unroll
-                    for (int c = 0; c < cpl; ++c) acc = fmaf(er[c], sv[c], acc);
+                for (int c = 0; c < cpl; ++c) {
+                    const int j = lane + 32 * c;
+                    if (j < m) acc = fmaf(er[j], sv[c], acc);
                 }
                 acc = warp_sum(acc);
                 if (lane == 0) mu[needl[idx]] = acc;
@@ -642,10 +643,11 @@ static __global__ void __launch_bounds__(kOnchipThreads, 1) k_pcg_onchip(CoarseP
                 }
             }
             if (!(gam > 0.0f)) break;   // restart from the true residual
-            const float be = k >= 1 ? gam / gam_prev : 0.0f;
-            const float den = k >= 1 ? del - be * gam / alp_prev : del;
+            // (fast divides: a few ulp in the step coefficients, identical in every CTA)
+            const float be = k >= 1 ? __fdividef(gam, gam_prev) : 0.0f;
+            const float den = k >= 1 ? del - be * __fdividef(gam, alp_prev) : del;
             if (!(den > 0.0f) || !isfinite(den)) break;
-            const float al = gam / den;
+            const float al = __fdividef(gam, den);
             gam_prev = gam;
             alp_prev = al;
             ++iters;
