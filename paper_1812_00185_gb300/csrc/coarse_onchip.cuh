@@ -271,9 +271,16 @@ static __global__ void __launch_bounds__(kOnchipThreads, 1) k_pcg_onchip(CoarseP
         __syncthreads();
         if (wid == 0) {
             const bool live = !aborted_now();
+            // 16 partials: xor rounds 8 .. 1 leave the total in lanes 0-15
+            static_assert(kOnchipWarps <= 16 && kOnchipMaxCluster <= 16, "16-lane sums");
             float cs[3];
 #pragma unroll
-            for (int k = 0; k < 3; ++k) cs[k] = __shfl_sync(0xffffffffu, warp_sum(lane < nw ? wsum32[lane][k] : 0.0f), 0);
+            for (int k = 0; k < 3; ++k) {
+                float x = lane < nw ? wsum32[lane][k] : 0.0f;
+#pragma unroll
+                for (int o = 8; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+                cs[k] = x;
+            }
             const bool sender = live && lane < ncl;
             const uint32_t dst = red32_remote + (uint32_t)(4 * ((par * 16 + rank) * kOnchipSlot));
             const uint32_t mb = mbar_remote[lane < ncl ? lane : 0][par];
@@ -318,9 +325,11 @@ static __global__ void __launch_bounds__(kOnchipThreads, 1) k_pcg_onchip(CoarseP
             }
             ok = __all_sync(0xffffffffu, ok);
 #pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                const float t = __shfl_sync(0xffffffffu, warp_sum(lane < ncl ? red32[(par * 16 + lane) * kOnchipSlot + k] : 0.0f), 0);
-                if (lane == 0) tot32[k] = t;
+            for (int k = 0; k < 3; ++k) {   // the ncl <= 16 slots, in a fixed order
+                float x = lane < ncl ? red32[(par * 16 + lane) * kOnchipSlot + k] : 0.0f;
+#pragma unroll
+                for (int o = 8; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+                if (lane == 0) tot32[k] = x;
             }
             if (!ok && lane < ncl) asm volatile("st.shared::cluster.u32 [%0], 1;" ::"r"(oc_map(&abort_flag, lane)) : "memory");
             if (lane == 0) tot32[3] = (ok && !aborted_now()) ? 1.0f : 0.0f;

@@ -116,8 +116,14 @@ static __global__ void __launch_bounds__(kBlock) k_proj_coef(int n, const double
 
 // x0 = X c (x keeps the previous increment while no solution is stored); xq, if given,
 // receives a copy (the input the network saw, for recording training pairs).
+// With `cond` (a graph's conditional handle, 0 otherwise) it also sets the IF condition of the
+// learned network that follows: run unless the coarse solve's judge has it off (gate[0] > 0).
 static __global__ void __launch_bounds__(kBlock) k_proj_combine(int n, const double* __restrict__ hx,
-                                                                const ProjState* ps, double* x, double* xq) {
+                                                                const ProjState* ps, double* x, double* xq,
+                                                                const int* gate = nullptr,
+                                                                unsigned long long cond = 0) {
+    if (cond && blockIdx.x == 0 && threadIdx.x == 0)
+        cudaGraphSetConditional((cudaGraphConditionalHandle)cond, __ldcg(gate) > 0 ? 0u : 1u);
     const int m = ps->count;
     double c[kProjL];
 #pragma unroll

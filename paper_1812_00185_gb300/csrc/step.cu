@@ -890,13 +890,42 @@ CoarsePcgArgs coarse_args(Solver& s) {
     return a;
 }
 
-// the learned prediction of Phi_c (before the coarse solve, which judges it)
-static int learned_guess(Ctx& c) {
+// the learned prediction of Phi_c (before the coarse solve, which judges it).  Captured into
+// a graph, the network's launches sit in an IF node whose condition the projection kernel
+// before it sets (`cond`), so while the judge has the network off a step skips its five grids.
+static int learned_guess(Ctx& c, unsigned long long cond) {
     Solver& s = *c.s;
-    if (s.prm.guess == CGP_GUESS_LEARNED && s.guess_ready) {
-        const Level& Cl = s.mesh->lev[s.lc];
-        PL(c, CGP_PROF_MLP,
-           CGP_TRY(mlp_forward(s.mlp, Cl, s.rc, s.phi, 1, s.phi_guess, c.st, s.onchip_bytes ? s.mlp_gate : nullptr)));
+    if (!(s.prm.guess == CGP_GUESS_LEARNED && s.guess_ready)) return CGP_OK;
+    const Level& Cl = s.mesh->lev[s.lc];
+    const int* gate = s.onchip_bytes ? s.mlp_gate : nullptr;
+    auto forward = [&](cudaStream_t st) { return mlp_forward(s.mlp, Cl, s.rc, s.phi, 1, s.phi_guess, st, gate); };
+    if (!cond) {
+        PL(c, CGP_PROF_MLP, CGP_TRY(forward(c.st)));
+        return CGP_OK;
+    }
+    const cudaGraphConditionalHandle handle = (cudaGraphConditionalHandle)cond;
+    cudaStreamCaptureStatus cs;
+    cudaGraph_t g = nullptr;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t ndeps = 0;
+    CGP_CUDA(cudaStreamGetCaptureInfo(c.st, &cs, nullptr, &g, &deps, nullptr, &ndeps));
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = handle;
+    cp.conditional.type = cudaGraphCondTypeIf;
+    cp.conditional.size = 1;
+    cudaGraphNode_t node;
+    CGP_CUDA(cudaGraphAddNode(&node, g, deps, nullptr, ndeps, &cp));
+    cudaGraph_t bodyg = cp.conditional.phGraph_out[0];
+    CGP_CUDA(cudaStreamUpdateCaptureDependencies(c.st, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+    CGP_CUDA(cudaStreamBeginCaptureToGraph(s.side, bodyg, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+    const int rc = forward(s.side);
+    cudaGraph_t outg = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(s.side, &outg);
+    if (rc != CGP_OK) return rc;
+    if (e != cudaSuccess) {
+        set_error("network capture failed: %s", cudaGetErrorString(e));
+        return CGP_ECUDA;
     }
     return CGP_OK;
 }
@@ -1006,15 +1035,26 @@ int step_pre(Ctx& c) {
                                            Ac, s.Kc, C.tag, C.xy, s.P, bc, s.tdev, p.dt, s.rc));
     }
     CGP_LAUNCH_CHECK();
+    // captured with the learned guess and its judge: the IF condition of the network's launches
+    unsigned long long cond = 0;
+    if (c.capture && s.proj && s.prm.guess == CGP_GUESS_LEARNED && s.guess_ready && s.onchip_bytes) {
+        cudaStreamCaptureStatus cs;
+        cudaGraph_t g = nullptr;
+        CGP_CUDA(cudaStreamGetCaptureInfo(c.st, &cs, nullptr, &g, nullptr, nullptr, nullptr));
+        cudaGraphConditionalHandle handle;
+        CGP_CUDA(cudaGraphConditionalHandleCreate(&handle, g, 0, cudaGraphCondAssignDefault));
+        cond = (unsigned long long)handle;
+    }
     if (s.proj) {
         // the projection guess of the coarse solve (and the network's second input)
         const int gc = grid_rows(s, C.nv, 1);
         PL(c, CGP_PROF_PROJ, k_proj_coef<<<gc, kBlock, 0, c.st>>>(C.nv, s.hist_x, s.hist_b, s.rc, &s.ks[KS_POIS],
                                                                    s.proj, p.tol_poisson, s.partials, s.tickets));
-        PL(c, CGP_PROF_PROJ, k_proj_combine<<<gc, kBlock, 0, c.st>>>(C.nv, s.hist_x, s.proj, s.phi, s.phi_q));
+        PL(c, CGP_PROF_PROJ, k_proj_combine<<<gc, kBlock, 0, c.st>>>(C.nv, s.hist_x, s.proj, s.phi, s.phi_q, s.mlp_gate,
+                                                                      cond));
         CGP_LAUNCH_CHECK();
     }
-    return learned_guess(c);
+    return learned_guess(c, cond);
 }
 
 // The rotational term of Eq. 26: M q = Cx u~ + Cy v~ (consistent M), or its lumped form.
