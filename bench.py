@@ -870,7 +870,8 @@ def main():
                     help="print only the MLP forward time of the learned guess on the workload's Poisson "
                          "level (--steps forward passes)")
     ap.add_argument("--pcg-only", action="store_true",
-                    help="print only the PCG bandwidth sweep (one JSON line per problem size)")
+                    help="print only the PCG bandwidth sweep (one JSON line per problem size), and the "
+                         "transfer kernels' bandwidth for sizes from 2048^2")
     ap.add_argument("--e1", action="store_true",
                     help="print only the paper's Taylor-Green study (Tables 1-4) run on the GPU, one JSON line")
     ap.add_argument("--accuracy", action="store_true",
@@ -935,6 +936,8 @@ def main():
         peak, _ = _peaks()
         for n in args.pcg_n:
             print(json.dumps(pcg_bandwidth(cg, torch, n, peak)), flush=True)
+            if n >= 2048:
+                print(json.dumps(transfer_bandwidth(cg, torch, n, peak)), flush=True)
         return 0
 
     if world > 1:
