@@ -5,9 +5,10 @@
 // synchronise with the hardware cluster barrier between phases; clusters never wait on one
 // another.
 //
-//   Eq. 21     the rows of the momentum system (step_rows.cuh), then FP64 BiCGStab with
-//              Jacobi for both velocity components (three cluster sums per iteration;
-//              restarted from the true residual after a breakdown)
+//   Eq. 21     the rows of the momentum system (step_rows.cuh), then BiCGStab with Jacobi
+//              for both velocity components (three cluster sums per iteration; restarted from
+//              the true residual after a breakdown): FP64, or for a mixed instance FP32 inner
+//              solves inside FP64 refinement, then FP64 only if the sweeps fell short
 //   Eqs. 22-23 the injected coarse right-hand side (with the range projection of a
 //              pure-Neumann problem and the lifted phi data of a traction boundary), then the
 //              instance's one-launch coarse PCG (coarse_pcg_body: FP64, or FP32 inner / FP64
@@ -19,6 +20,8 @@
 //              steps need no inner products and their number follows from the tolerance
 //              (error <= 4 * 3^-n of the initial one in the energy norm)
 //   Eq. 26     the rotational term (D U~, and the same Chebyshev solve on M) and the update
+// In a mixed instance the momentum BiCGStab's inner iterations run in FP32: on this GPU the
+// narrow FP64 pipe is the busiest unit of the cluster's FP64 iterations.
 #pragma once
 
 #include <cooperative_groups.h>
@@ -42,6 +45,12 @@ struct BatchStepArgs {
     double *U, *Uprev, *P, *Ut, *w, *h, *A, *dinvA, *b, *g, *delta, *div, *qrot, *phi;
     BicgVecs bv;
     double *c0, *c1, *c2;   // Chebyshev work: residual, two directions (2 nf each)
+    // mixed instances (null otherwise): FP32 copies of A (refreshed each step) and its Jacobi
+    // diagonal, FP32 work vectors (2 nf each); the momentum solve then runs FP32 inner solves
+    // inside FP64 refinement
+    int64_t nnz;
+    float *A32, *dinvA32;
+    float* fv[10];
     // coarse level and its solve
     SellView Ac;
     const double *Cxc, *Cyc, *Kc, *cxy;
@@ -116,48 +125,57 @@ __host__ __device__ inline int cheb_steps_for(double tol) {
     return n;
 }
 
+// Mixed instances: the momentum system runs up to kBatchIrSweeps FP64-residual sweeps around
+// an FP32 BiCGStab (each asked for kBatchInnerTol of its right-hand side, or what is left to
+// the tolerance), then the FP64 BiCGStab unless a sweep's residual already met the tolerance.
+constexpr int kBatchIrSweeps = 3;
+constexpr double kBatchInnerTol = 1e-4;
+constexpr int kBatchInnerMaxit = 200;
+
 // Chebyshev semi-iteration for B x = rhs (NC interleaved components), x = 0 at the start;
-// Jacobi preconditioning, bounds [1/2, 2] of D^-1 B; one cluster barrier per step
-template <int NC>
-__device__ void cluster_chebyshev(const SellView& B, const double* __restrict__ val, const double* __restrict__ dinv,
-                                  const double* __restrict__ rhs, double* __restrict__ x, double* __restrict__ r,
-                                  double* __restrict__ d0, double* __restrict__ d1, int steps, int crank, int csize,
+// Jacobi preconditioning, bounds [1/2, 2] of D^-1 B; one cluster barrier per step.  (It stays
+// FP64 in mixed instances too: FP32 sweeps inside FP64 refinement took longer here, the
+// cluster's steps being bound by latency rather than by the FP64 pipe.)
+template <int NC, class T = double>
+__device__ void cluster_chebyshev(const SellView& B, const T* __restrict__ val, const T* __restrict__ dinv,
+                                  const T* __restrict__ rhs, T* __restrict__ x, T* __restrict__ r,
+                                  T* __restrict__ d0, T* __restrict__ d1, int steps, int crank, int csize,
                                   cgrp_bs::cluster_group& cl) {
     const double theta = 1.25, delta = 0.75, sigma = theta / delta;
     const int n = B.n, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5, wid = threadIdx.x >> 5;
     for (int i = crank * blockDim.x + threadIdx.x; i < n; i += csize * blockDim.x) {
-        const double di = dinv[i];
+        const T di = dinv[i];
 #pragma unroll
         for (int c = 0; c < NC; ++c) {
-            const double ri = rhs[NC * i + c];
-            x[NC * i + c] = 0.0;
+            const T ri = rhs[NC * i + c];
+            x[NC * i + c] = T(0);
             r[NC * i + c] = ri;
-            d0[NC * i + c] = di * ri / theta;
+            d0[NC * i + c] = di * ri / T(theta);
         }
     }
     cl.sync();
     double rho = 1.0 / sigma;
-    double* dc = d0;
-    double* dn = d1;
+    T* dc = d0;
+    T* dn = d1;
     for (int k = 0; k < steps; ++k) {
         const double rho_n = 1.0 / (2.0 * sigma - rho);
-        const double c1 = rho_n * rho, c2 = 2.0 * rho_n / delta;
+        const T c1 = (T)(rho_n * rho), c2 = (T)(2.0 * rho_n / delta);
         for (int sl = crank * nwarp + wid; sl < B.nslices; sl += csize * nwarp) {
             const int i = sl * 32 + lane;
-            double wv[NC];
+            T wv[NC];
 #pragma unroll
-            for (int c = 0; c < NC; ++c) wv[c] = 0.0;
-            sell_accum<NC>(B, val, sl, lane, [&](int j, double (&o)[NC]) {
+            for (int c = 0; c < NC; ++c) wv[c] = T(0);
+            sell_accum<NC>(B, val, sl, lane, [&](int j, T (&o)[NC]) {
 #pragma unroll
                 for (int c = 0; c < NC; ++c) o[c] = dc[NC * j + c];
             }, wv);
             if (i < n) {
-                const double di = dinv[i];
+                const T di = dinv[i];
 #pragma unroll
                 for (int c = 0; c < NC; ++c) {
-                    const double dd = dc[NC * i + c];
+                    const T dd = dc[NC * i + c];
                     x[NC * i + c] += dd;
-                    const double rn = r[NC * i + c] - wv[c];
+                    const T rn = r[NC * i + c] - wv[c];
                     r[NC * i + c] = rn;
                     dn[NC * i + c] = c1 * dd + c2 * di * rn;
                 }
@@ -165,10 +183,181 @@ __device__ void cluster_chebyshev(const SellView& B, const double* __restrict__ 
         }
         cl.sync();
         rho = rho_n;
-        double* t = dc;
+        T* t = dc;
         dc = dn;
         dn = t;
     }
+}
+
+// BiCGStab with Jacobi for the two velocity components of one instance, on its cluster.  T:
+// FP64, or FP32 for the inner solve of a refinement sweep (its per-thread partial sums are then
+// FP32, the cluster sums FP64).  x starts from V.x, or from 0 with zero_x.  A breakdown (rho or
+// omega vanishing before convergence) restarts from the true residual, at most `restarts`
+// times.  Converged when <r, r> <= tol2 <b, b> for each component.  Returns the iterations;
+// status, the last <r, r> and <b, b> go out.
+template <class T>
+__device__ int cluster_bicgstab(const SellView& A, const T* __restrict__ val, const T* __restrict__ dinv,
+                                const T* __restrict__ b, const BicgVecsT<T>& V, double tol2, int maxit, int restarts,
+                                bool zero_x, ClusterSum8& cs, cgrp_bs::cluster_group& cl, int crank, int csize,
+                                int& status, double (&rr)[2], double (&bb)[2]) {
+    const int n = A.n, lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    const int tid = crank * blockDim.x + threadIdx.x, nthr = csize * blockDim.x;
+    double rho[2] = {0.0, 0.0}, alpha[2] = {0.0, 0.0}, omega[2] = {0.0, 0.0}, beta[2] = {0.0, 0.0};
+    int done[2] = {0, 0}, it = 0;
+    status = 0;
+    for (int restart = 0; restart <= restarts; ++restart) {
+        {   // r = b - A x, rhat = r, p = v = 0
+            const bool zx = zero_x && restart == 0;
+            T acc[4] = {T(0), T(0), T(0), T(0)};
+            for (int sl = crank * nwarp + wid; sl < A.nslices; sl += csize * nwarp) {
+                const int i = sl * 32 + lane;
+                T ax[2] = {T(0), T(0)};
+                if (!zx) spmv2_row(A, val, V.x, sl, lane, ax);
+                if (i < n) {
+#pragma unroll
+                    for (int c = 0; c < 2; ++c) {
+                        const T bv = b[2 * i + c], rv = bv - ax[c];
+                        if (zx) V.x[2 * i + c] = T(0);
+                        V.r[2 * i + c] = rv;
+                        V.rhat[2 * i + c] = rv;
+                        V.p[2 * i + c] = T(0);
+                        V.v[2 * i + c] = T(0);
+                        acc[c] += rv * rv;
+                        acc[2 + c] += bv * bv;
+                    }
+                }
+            }
+            const double accd[4] = {(double)acc[0], (double)acc[1], (double)acc[2], (double)acc[3]};
+            double tot[4];
+            cs.sum(accd, tot);
+            for (int c = 0; c < 2; ++c) {
+                rho[c] = tot[c];
+                rr[c] = tot[c];
+                if (restart == 0) bb[c] = tot[2 + c];
+                done[c] = !(rr[c] > tol2 * bb[c]);
+                alpha[c] = omega[c] = beta[c] = 0.0;
+            }
+        }
+        bool broke = false;
+        while (!(done[0] && done[1]) && it < maxit && !broke) {
+            // p = r + beta (p - omega v), y = D^-1 p
+            for (int i = tid; i < n; i += nthr) {
+                const T di = dinv[i];
+#pragma unroll
+                for (int c = 0; c < 2; ++c) {
+                    if (done[c]) continue;
+                    const T pv = V.r[2 * i + c] + (T)beta[c] * (V.p[2 * i + c] - (T)omega[c] * V.v[2 * i + c]);
+                    V.p[2 * i + c] = pv;
+                    V.y[2 * i + c] = di * pv;
+                }
+            }
+            cl.sync();
+            {   // v = A y, alpha = rho / <rhat, v>
+                T acc[2] = {T(0), T(0)};
+                for (int sl = crank * nwarp + wid; sl < A.nslices; sl += csize * nwarp) {
+                    const int i = sl * 32 + lane;
+                    T ax[2];
+                    spmv2_row(A, val, V.y, sl, lane, ax);
+                    if (i < n) {
+#pragma unroll
+                        for (int c = 0; c < 2; ++c) {
+                            if (done[c]) continue;
+                            V.v[2 * i + c] = ax[c];
+                            acc[c] += V.rhat[2 * i + c] * ax[c];
+                        }
+                    }
+                }
+                const double accd[2] = {(double)acc[0], (double)acc[1]};
+                double tot[2];
+                cs.sum(accd, tot);
+                for (int c = 0; c < 2; ++c) {
+                    if (done[c]) continue;
+                    if (!isfinite(tot[c])) {
+                        done[c] = 1;
+                        status = CGP_ENONFINITE;
+                    } else if (tot[c] != 0.0) {
+                        alpha[c] = rho[c] / tot[c];
+                    } else {
+                        broke = true;
+                    }
+                }
+            }
+            if (broke) break;
+            // s = r - alpha v, z = D^-1 s
+            for (int i = tid; i < n; i += nthr) {
+                const T di = dinv[i];
+#pragma unroll
+                for (int c = 0; c < 2; ++c) {
+                    if (done[c]) continue;
+                    const T sv = V.r[2 * i + c] - (T)alpha[c] * V.v[2 * i + c];
+                    V.s[2 * i + c] = sv;
+                    V.z[2 * i + c] = di * sv;
+                }
+            }
+            cl.sync();
+            {   // t = A z, omega = <t, s> / <t, t>
+                T acc[4] = {T(0), T(0), T(0), T(0)};
+                for (int sl = crank * nwarp + wid; sl < A.nslices; sl += csize * nwarp) {
+                    const int i = sl * 32 + lane;
+                    T ax[2];
+                    spmv2_row(A, val, V.z, sl, lane, ax);
+                    if (i < n) {
+#pragma unroll
+                        for (int c = 0; c < 2; ++c) {
+                            if (done[c]) continue;
+                            V.t[2 * i + c] = ax[c];
+                            acc[c] += ax[c] * V.s[2 * i + c];
+                            acc[2 + c] += ax[c] * ax[c];
+                        }
+                    }
+                }
+                const double accd[4] = {(double)acc[0], (double)acc[1], (double)acc[2], (double)acc[3]};
+                double tot[4];
+                cs.sum(accd, tot);
+                for (int c = 0; c < 2; ++c)
+                    omega[c] = (!done[c] && tot[2 + c] > 0.0 && isfinite(tot[2 + c])) ? tot[c] / tot[2 + c] : 0.0;
+            }
+            {   // x += alpha y + omega z, r = s - omega t, <rhat, r>, <r, r>
+                T acc[4] = {T(0), T(0), T(0), T(0)};
+                for (int i = tid; i < n; i += nthr) {
+#pragma unroll
+                    for (int c = 0; c < 2; ++c) {
+                        if (done[c]) continue;
+                        V.x[2 * i + c] += (T)alpha[c] * V.y[2 * i + c] + (T)omega[c] * V.z[2 * i + c];
+                        const T rv = V.s[2 * i + c] - (T)omega[c] * V.t[2 * i + c];
+                        V.r[2 * i + c] = rv;
+                        acc[c] += V.rhat[2 * i + c] * rv;
+                        acc[2 + c] += rv * rv;
+                    }
+                }
+                const double accd[4] = {(double)acc[0], (double)acc[1], (double)acc[2], (double)acc[3]};
+                double tot[4];
+                cs.sum(accd, tot);
+                for (int c = 0; c < 2; ++c) {
+                    if (done[c]) continue;
+                    if (!isfinite(tot[c]) || !isfinite(tot[2 + c])) {
+                        status = CGP_ENONFINITE;
+                        done[c] = 1;
+                        continue;
+                    }
+                    rr[c] = tot[2 + c];
+                    if (rr[c] <= tol2 * bb[c]) {
+                        done[c] = 1;
+                    } else if (omega[c] == 0.0 || tot[c] == 0.0) {
+                        broke = true;
+                    } else {
+                        beta[c] = (tot[c] / rho[c]) * (alpha[c] / omega[c]);
+                        rho[c] = tot[c];
+                    }
+                }
+            }
+            ++it;
+        }
+        if (!broke) break;
+        if (restart == restarts) status = CGP_EBREAKDOWN;
+    }
+    if (!(done[0] && done[1]) && !status) status = CGP_ENOTCONV;
+    return it;
 }
 
 static __global__ void __launch_bounds__(512, 1) k_batch_step(const BatchStepArgs* __restrict__ args,
@@ -211,15 +400,21 @@ static __global__ void __launch_bounds__(512, 1) k_batch_step(const BatchStepArg
                                     a.M, a.CxT, a.CyT, a.P, a.w, a.h, a.tag, a.xy, bc, tn, dt, a.A, a.dinvA, a.b,
                                     a.Ut, nullptr);
         cl.sync();
-        // ---- BiCGStab (two components), x = U~ from w; a breakdown (rho or omega vanishing
-        // before convergence) restarts from the true residual, at most kRestarts times
+        // ---- the momentum solve (two components), x = U~ from w.  Mixed instances: FP64
+        // residual sweeps around an FP32 BiCGStab on the FP32 copy of A, then the FP64
+        // BiCGStab unless a sweep's residual met the tolerance; FP64 instances: the FP64
+        // BiCGStab alone (a breakdown restarts it from the true residual, at most 4 times).
         const BicgVecs V = a.bv;
-        double rho[2], alpha[2] = {0.0, 0.0}, omega[2] = {0.0, 0.0}, beta[2] = {0.0, 0.0}, bb[2] = {0.0, 0.0};
-        double rr[2] = {0.0, 0.0};
-        int done[2] = {0, 0}, it = 0, status = 0;
-        constexpr int kRestarts = 4;
-        for (int restart = 0; restart <= kRestarts; ++restart) {
-            {   // r = b - A x, rhat = r, p = v = 0
+        double rr[2] = {0.0, 0.0}, bb[2] = {0.0, 0.0};
+        int it = 0, status = 0;
+        bool polish = true;
+        if (a.A32) {
+            for (int64_t e = tid; e < a.nnz; e += nthr) a.A32[e] = (float)a.A[e];
+            for (int i = tid; i < nf; i += nthr) a.dinvA32[i] = (float)a.dinvA[i];
+            cl.sync();
+            const BicgVecsT<float> W{a.fv[0], a.fv[1], a.fv[2], a.fv[3], a.fv[4], a.fv[5], a.fv[6], a.fv[7], a.fv[8]};
+            float* r32 = a.fv[9];
+            for (int sw = 0; sw < kBatchIrSweeps; ++sw) {
                 double acc[4] = {0.0, 0.0, 0.0, 0.0};
                 for (int sl = crank * nwarp + wid; sl < a.Af.nslices; sl += csize * nwarp) {
                     const int i = sl * 32 + lane;
@@ -229,10 +424,7 @@ static __global__ void __launch_bounds__(512, 1) k_batch_step(const BatchStepArg
 #pragma unroll
                         for (int c = 0; c < 2; ++c) {
                             const double bv = a.b[2 * i + c], rv = bv - ax[c];
-                            V.r[2 * i + c] = rv;
-                            V.rhat[2 * i + c] = rv;
-                            V.p[2 * i + c] = 0.0;
-                            V.v[2 * i + c] = 0.0;
+                            r32[2 * i + c] = (float)rv;
                             acc[c] += rv * rv;
                             acc[2 + c] += bv * bv;
                         }
@@ -240,130 +432,42 @@ static __global__ void __launch_bounds__(512, 1) k_batch_step(const BatchStepArg
                 }
                 double tot[4];
                 cs.sum(acc, tot);
-                for (int c = 0; c < 2; ++c) {
-                    rho[c] = tot[c];
-                    rr[c] = tot[c];
-                    if (restart == 0) bb[c] = tot[2 + c];
-                    done[c] = !(rr[c] > a.tol_mom2 * bb[c]);
-                    alpha[c] = omega[c] = beta[c] = 0.0;
+                if (sw == 0) {
+                    bb[0] = tot[2];
+                    bb[1] = tot[3];
                 }
-            }
-            bool broke = false;
-            while (!(done[0] && done[1]) && it < a.max_it_mom && !broke) {
-                // p = r + beta (p - omega v), y = D^-1 p
+                rr[0] = tot[0];
+                rr[1] = tot[1];
+                if (!isfinite(tot[0]) || !isfinite(tot[1])) break;   // the FP64 solve reports it
+                if (rr[0] <= a.tol_mom2 * bb[0] && rr[1] <= a.tol_mom2 * bb[1]) {
+                    polish = false;
+                    break;
+                }
+                // the inner solve aims at kBatchInnerTol, or at what is left to the tolerance
+                // (a factor 2 of margin in the norm) when that is less
+                double t2 = kBatchInnerTol * kBatchInnerTol, need = 1.0;
+                for (int c = 0; c < 2; ++c)
+                    if (rr[c] > a.tol_mom2 * bb[c]) need = fmin(need, 0.25 * a.tol_mom2 * bb[c] / rr[c]);
+                t2 = fmax(t2, need);
+                int st_in = 0;
+                double rr_in[2], bb_in[2];
+                it += cluster_bicgstab<float>(a.Af, a.A32, a.dinvA32, r32, W, t2, kBatchInnerMaxit, 0, true, cs, cl,
+                                              crank, csize, st_in, rr_in, bb_in);
+                if (st_in == CGP_ENONFINITE) break;
                 for (int i = tid; i < nf; i += nthr) {
-                    const double di = a.dinvA[i];
 #pragma unroll
-                    for (int c = 0; c < 2; ++c) {
-                        if (done[c]) continue;
-                        const double pv = V.r[2 * i + c] + beta[c] * (V.p[2 * i + c] - omega[c] * V.v[2 * i + c]);
-                        V.p[2 * i + c] = pv;
-                        V.y[2 * i + c] = di * pv;
-                    }
+                    for (int c = 0; c < 2; ++c) V.x[2 * i + c] += (double)W.x[2 * i + c];
                 }
                 cl.sync();
-                {   // v = A y, alpha = rho / <rhat, v>
-                    double acc[2] = {0.0, 0.0};
-                    for (int sl = crank * nwarp + wid; sl < a.Af.nslices; sl += csize * nwarp) {
-                        const int i = sl * 32 + lane;
-                        double ax[2];
-                        spmv2_row(a.Af, a.A, V.y, sl, lane, ax);
-                        if (i < nf) {
-#pragma unroll
-                            for (int c = 0; c < 2; ++c) {
-                                if (done[c]) continue;
-                                V.v[2 * i + c] = ax[c];
-                                acc[c] += V.rhat[2 * i + c] * ax[c];
-                            }
-                        }
-                    }
-                    double tot[2];
-                    cs.sum(acc, tot);
-                    for (int c = 0; c < 2; ++c) {
-                        if (done[c]) continue;
-                        if (!isfinite(tot[c])) {
-                            done[c] = 1;
-                            status = CGP_ENONFINITE;
-                        } else if (tot[c] != 0.0) {
-                            alpha[c] = rho[c] / tot[c];
-                        } else {
-                            broke = true;
-                        }
-                    }
-                }
-                if (broke) break;
-                // s = r - alpha v, z = D^-1 s
-                for (int i = tid; i < nf; i += nthr) {
-                    const double di = a.dinvA[i];
-#pragma unroll
-                    for (int c = 0; c < 2; ++c) {
-                        if (done[c]) continue;
-                        const double sv = V.r[2 * i + c] - alpha[c] * V.v[2 * i + c];
-                        V.s[2 * i + c] = sv;
-                        V.z[2 * i + c] = di * sv;
-                    }
-                }
-                cl.sync();
-                {   // t = A z, omega = <t, s> / <t, t>
-                    double acc[4] = {0.0, 0.0, 0.0, 0.0};
-                    for (int sl = crank * nwarp + wid; sl < a.Af.nslices; sl += csize * nwarp) {
-                        const int i = sl * 32 + lane;
-                        double ax[2];
-                        spmv2_row(a.Af, a.A, V.z, sl, lane, ax);
-                        if (i < nf) {
-#pragma unroll
-                            for (int c = 0; c < 2; ++c) {
-                                if (done[c]) continue;
-                                V.t[2 * i + c] = ax[c];
-                                acc[c] += ax[c] * V.s[2 * i + c];
-                                acc[2 + c] += ax[c] * ax[c];
-                            }
-                        }
-                    }
-                    double tot[4];
-                    cs.sum(acc, tot);
-                    for (int c = 0; c < 2; ++c)
-                        omega[c] = (!done[c] && tot[2 + c] > 0.0 && isfinite(tot[2 + c])) ? tot[c] / tot[2 + c] : 0.0;
-                }
-                {   // x += alpha y + omega z, r = s - omega t, <rhat, r>, <r, r>
-                    double acc[4] = {0.0, 0.0, 0.0, 0.0};
-                    for (int i = tid; i < nf; i += nthr) {
-#pragma unroll
-                        for (int c = 0; c < 2; ++c) {
-                            if (done[c]) continue;
-                            V.x[2 * i + c] += alpha[c] * V.y[2 * i + c] + omega[c] * V.z[2 * i + c];
-                            const double rv = V.s[2 * i + c] - omega[c] * V.t[2 * i + c];
-                            V.r[2 * i + c] = rv;
-                            acc[c] += V.rhat[2 * i + c] * rv;
-                            acc[2 + c] += rv * rv;
-                        }
-                    }
-                    double tot[4];
-                    cs.sum(acc, tot);
-                    for (int c = 0; c < 2; ++c) {
-                        if (done[c]) continue;
-                        if (!isfinite(tot[c]) || !isfinite(tot[2 + c])) {
-                            status = CGP_ENONFINITE;
-                            done[c] = 1;
-                            continue;
-                        }
-                        rr[c] = tot[2 + c];
-                        if (rr[c] <= a.tol_mom2 * bb[c]) {
-                            done[c] = 1;
-                        } else if (omega[c] == 0.0 || tot[c] == 0.0) {
-                            broke = true;
-                        } else {
-                            beta[c] = (tot[c] / rho[c]) * (alpha[c] / omega[c]);
-                            rho[c] = tot[c];
-                        }
-                    }
-                }
-                ++it;
             }
-            if (!broke) break;
-            if (restart == kRestarts) status = CGP_EBREAKDOWN;
         }
-        if (!(done[0] && done[1]) && !status) status = CGP_ENOTCONV;
+        if (polish) {
+            double bb64[2];
+            it += cluster_bicgstab<double>(a.Af, a.A, a.dinvA, a.b, V, a.tol_mom2, a.max_it_mom, 4, false, cs, cl, crank,
+                                           csize, status, rr, bb64);
+            bb[0] = bb64[0];
+            bb[1] = bb64[1];
+        }
         // ---- Eqs. 22-23: r = -3/(2 dt) (Cx_c u~ + Cy_c v~) at the coarse vertices (the fine
         // prefix); phi data on PHI_ZERO vertices (zero, or lifted for a traction boundary)
         {

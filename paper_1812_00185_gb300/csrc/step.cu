@@ -1302,6 +1302,13 @@ void fill_batch_step_args(Solver& s, void* dst) {
     a.lumped = s.prm.mass_mode == CGP_MASS_LUMPED;
     a.max_it_mom = s.prm.max_it_mom;
     a.cheb_steps = cheb_steps_for(s.prm.tol_mass);
+    if (s.Af) {
+        a.nnz = F.nnz_sell;
+        a.A32 = s.Af;
+        a.dinvA32 = s.dinvAf;
+        for (int k = 0; k < 9; ++k) a.fv[k] = s.fv[k];
+        a.fv[9] = s.frhs;
+    }
     a.tdev = s.tdev;
     a.stats = s.stats;
     a.ks = s.ks;
