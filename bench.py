@@ -281,8 +281,9 @@ def run_gpu(args, rank, world):
                 forms[other] = {k: res[k] for k in keys}
                 s2.close()
 
-    # end to end through the C ABI: pinned host state in, one step, state out, every step;
-    # it replays the first steps of the timed region from the state they started from
+    # end to end through the C ABI: pinned host state in (U^n, U^{n-1}, P^n), one step, state
+    # out (U^{n+1}, P^{n+1}), every step; it replays the first steps of the timed region from the
+    # state they started from
     Uh = torch.empty((nv_f, 2), dtype=torch.float64, pin_memory=True)
     Uph = torch.empty((nv_f, 2), dtype=torch.float64, pin_memory=True)
     Ph = torch.empty(nv_f, dtype=torch.float64, pin_memory=True)
@@ -295,11 +296,14 @@ def run_gpu(args, rank, world):
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     ev0.record(stream)
+    cur, prev = Uh.numpy(), Uph.numpy()
     for _ in range(e2e_steps):
-        cg.cgp_set_fields(s.handle, Uh.numpy(), Uph.numpy(), Ph.numpy(), tcur, where=cg.CGP_HOST)
+        cg.cgp_set_fields(s.handle, cur, prev, Ph.numpy(), tcur, where=cg.CGP_HOST)
         cg.cgp_step(s.handle, 1)
-        Uph.copy_(Uh)
-        _, _, tcur, _, _ = cg.cgp_get_fields(s.handle, U=Uh.numpy(), P=Ph.numpy(), where=cg.CGP_HOST)
+        # the new U goes into the buffer of U^{n-1}, which this step no longer needs; the two
+        # pinned buffers then swap roles (U^n becomes the next step's U^{n-1})
+        _, _, tcur, _, _ = cg.cgp_get_fields(s.handle, U=prev, P=Ph.numpy(), where=cg.CGP_HOST)
+        cur, prev = prev, cur
     ev1.record(stream)
     torch.cuda.synchronize()
     e2e_ms = ev0.elapsed_time(ev1) / e2e_steps

@@ -735,7 +735,7 @@ static __global__ void __launch_bounds__(kOnchipThreads, 1) k_pcg_onchip(CoarseP
         st->status = status ? status : (converged ? 0 : CGP_ENOTCONV);
         st->done = 1;
         st->pad[0] = outer;
-        st->pad[1] = used_alt;
+        st->pad[1] = used_alt | (alt_on ? 2 : 0);   // bit 1: the network ran (its gate was open)
     }
     oc_barrier();   // no CTA leaves while another may still access its shared memory
 }

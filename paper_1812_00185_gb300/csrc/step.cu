@@ -239,7 +239,7 @@ __global__ void __launch_bounds__(kBlock) k_div(SellView A, const double* __rest
 __global__ void k_finish(int nf, double* __restrict__ U, double* __restrict__ Uprev, const double* __restrict__ Ut,
                          const double* __restrict__ delta, double* __restrict__ P, const double* __restrict__ phi,
                          const double* __restrict__ q, int chi, double inv_re, double* __restrict__ tdev, double dt,
-                         DeviceStats* stats, const KrylovState* ks, int fixed_launches, int pois_loop) {
+                         DeviceStats* stats, const KrylovState* ks, int fixed_launches, int pois_loop, int net) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nf; i += gridDim.x * blockDim.x) {
         const double2 u = reinterpret_cast<const double2*>(U)[i];
         const double2 ut = reinterpret_cast<const double2*>(Ut)[i];
@@ -261,8 +261,11 @@ __global__ void k_finish(int nf, double* __restrict__ U, double* __restrict__ Up
         // FP32 inner loops of the mixed form: 5 kernels per BiCGStab trip (the Chebyshev mass
         // solves have a fixed launch count)
         l += 5 * (int64_t)ks[KS_MOM].trips;
+        // the learned guess's network: `net` launches every step, or (net < 0) -net launches in
+        // the steps whose coarse solve found the judge's gate open (its IF node ran)
+        if (net > 0 || (net < 0 && (ks[KS_POIS].pad[1] & 2))) l += net > 0 ? net : -net;
         stats->launches += l;
-        if (ks[KS_POIS].pad[1]) stats->guess_used += 1;
+        if (ks[KS_POIS].pad[1] & 1) stats->guess_used += 1;
         stats->sum_outer += ks[KS_POIS].pad[0];
         for (int k = 0; k < KS_COUNT; ++k) {
             const int it = ks[k].iter + (k != KS_POIS ? ks[k].inner : 0);   // FP64 + FP32 inner iterations
@@ -1110,8 +1113,9 @@ int step_post(Ctx& c, bool mass_done) {
     // Eq. 26: pressure
     if (p.chi && !mass_done) CGP_TRY(rotational_term(c));
     const bool one_launch = s.coarse_kind != CGP_COARSE_KERNELS;
-    const int coarse_fixed = (one_launch ? 1 : 2 + (s.pure_neumann ? 2 : 0)) +
-                             ((p.guess == CGP_GUESS_LEARNED && s.guess_ready) ? 10 : 0) + (s.proj ? 3 : 0);
+    const int coarse_fixed = (one_launch ? 1 : 2 + (s.pure_neumann ? 2 : 0)) + (s.proj ? 3 : 0);
+    // the network's five launches, behind the judge's IF node where the on-chip solve judges it
+    const int net = (p.guess == CGP_GUESS_LEARNED && s.guess_ready) ? (s.onchip_bytes ? -5 : 5) : 0;
     // mixed: the FP32 copy of A; momentum: kIrSweeps x (residual, inner init, update); each
     // Chebyshev mass solve: kChebSweeps x (residual, init, kChebSteps steps, update)
     const int ir_fixed = mixed ? 1 + 3 * kIrSweeps +
@@ -1124,7 +1128,7 @@ int step_post(Ctx& c, bool mass_done) {
         pt_fixed;
     PL(c, CGP_PROF_FINISH,
        k_finish<<<gv, kBlock, 0, c.st>>>(F.nv, s.U, s.Uprev, s.Ut, s.delta, s.P, s.phi, s.qrot, p.chi, 1.0 / p.Re,
-                                         s.tdev, p.dt, s.stats, s.ks, fixed, one_launch ? 0 : 1));
+                                         s.tdev, p.dt, s.stats, s.ks, fixed, one_launch ? 0 : 1, net));
     CGP_LAUNCH_CHECK();
     return CGP_OK;
 }
