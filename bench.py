@@ -396,7 +396,7 @@ def run_gpu(args, rank, world):
         transfer = [transfer_bandwidth(cg, torch, n, peak) for n in args.pcg_n if n >= 2048]
     batch = None
     if not args.quick and args.batch > 0:
-        batch = batch_throughput(cg, torch, args.batch, args.batch_steps, 3)
+        batch = batch_throughput(cg, torch, args.batch, args.batch_steps, 3, args.batch_cluster, args.batch_threads)
 
     s.close()
     mesh.close()
@@ -537,13 +537,14 @@ def transfer_bandwidth(cg, torch, n_side, peak):
     return out
 
 
-def batch_throughput(cg, torch, n_inst, steps, warmup):
-    """The batched form: n_inst uneven lid-driven cavities (seeded sizes 32^2..256^2 x 2
-    triangles, Re in [10, 400], 1-3 coarsening levels, dt = 0.005, rotational form, FP32-inner
-    coarse solves) advanced by one graph per step with one persistent launch for all coarse
-    solves."""
+def batch_throughput(cg, torch, n_inst, steps, warmup, cluster_size=0, threads=0):
+    """The batched form: the first n_inst of the 256 seeded uneven lid-driven cavities (sizes
+    32^2..256^2 x 2 triangles, Re in [10, 400], 1-3 coarsening levels, dt = 0.005, rotational
+    form, mixed precision), advanced by the library's batched step (by default one persistent
+    clustered launch per step, its cluster shape autotuned unless cluster_size / threads fix
+    it)."""
     from workloads import batch_instances, square_mesh
-    specs = batch_instances(n_inst)
+    specs = batch_instances(256)[:n_inst] if n_inst <= 256 else batch_instances(n_inst)
     specs_sorted = specs
     t0 = time.time()
     meshes, solvers = [], []
@@ -561,7 +562,7 @@ def batch_throughput(cg, torch, n_inst, steps, warmup):
     torch.cuda.synchronize()
     t_setup = time.time() - t0
     t0 = time.time()
-    b = cg.cgp_batch_create(solvers)
+    b = cg.cgp_batch_create(solvers, cluster_size=cluster_size, threads=threads)
     info = cg.cgp_batch_info(b)
     mode = "whole step" if cg.cgp_batch_mode(b) == cg.CGP_BATCH_WHOLE_STEP else "graph branches"
     t_tune = time.time() - t0
@@ -854,7 +855,13 @@ def main():
     ap.add_argument("--form", default="mixed_learned",
                     choices=["fp64", "mixed", "learned", "mixed_learned", "mixed_zero", "mixed_jacobi", "mixed_proj",
                              "fp64_proj"])
-    ap.add_argument("--batch", type=int, default=256, help="instances of the batched form (0: skip)")
+    ap.add_argument("--batch", type=int, default=256,
+                    help="instances of the batched form (the first of the 256 seeded ones; 0: skip)")
+    ap.add_argument("--batch-only", action="store_true",
+                    help="print only the batched-form measurement (--batch instances, --batch-steps timed "
+                         "steps after --warmup)")
+    ap.add_argument("--batch-cluster", type=int, default=0, help="batched form: cluster size (0: autotuned)")
+    ap.add_argument("--batch-threads", type=int, default=0, help="batched form: threads per CTA (0: autotuned)")
     ap.add_argument("--batch-steps", type=int, default=10,
                     help="timed batched steps (the cavity instances of the batch diverge within 100 steps, "
                          "in the oracle too: see the design notes)")
@@ -931,6 +938,14 @@ def main():
                               "rows": jobelin_tables(cg, torch)}), flush=True)
         if args.c5:
             print(json.dumps(c5_study(cg, torch)), flush=True)
+        return 0
+    if args.batch_only:
+        if rank != 0:
+            return 0
+        import torch
+        from paper_1812_00185_gb300 import binding as cg
+        print(json.dumps(batch_throughput(cg, torch, args.batch, args.batch_steps, args.warmup, args.batch_cluster,
+                                          args.batch_threads)), flush=True)
         return 0
     if args.pcg_only:
         if rank != 0:
