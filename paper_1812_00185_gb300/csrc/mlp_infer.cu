@@ -41,14 +41,17 @@ __global__ void __launch_bounds__(128) k_inf_layer1(int n, const int32_t* __rest
     if (gate && *gate > 0) return;   // the solve's judge has switched the network off for now
     __shared__ float w[kHid][8];
     __shared__ float bias[kHid];
+    __shared__ double inv_scale[2];   // one FP64 reciprocal per CTA: this GPU's FP64 divide is slow
     for (int e = threadIdx.x; e < kHid * 8; e += blockDim.x) w[e / 8][e % 8] = __bfloat162float(W1[e]);
     for (int e = threadIdx.x; e < kHid; e += blockDim.x) bias[e] = b1[e];
+    if (threadIdx.x < 2) inv_scale[threadIdx.x] = 1.0 / (double)scale[threadIdx.x];
     __syncthreads();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
+    const double is0 = inv_scale[0], is1 = inv_scale[1];
     auto feat = [&](int j, float (&f)[4]) {
-        f[0] = (float)(r[j] / (double)scale[0]);
-        f[1] = (float)(q[j] / (double)scale[1]);
+        f[0] = (float)(r[j] * is0);
+        f[1] = (float)(q[j] * is1);
         f[2] = (float)xy[2 * j];
         f[3] = (float)xy[2 * j + 1];
     };
