@@ -35,16 +35,38 @@ constexpr int kL2Smem = (2 * kL2Rows + kHid) * kL2Ld * 2;   // A hi, A lo, W2
 __global__ void __launch_bounds__(128) k_inf_layer1(int n, const int32_t* __restrict__ rowptr,
                                                     const int32_t* __restrict__ col, const double* __restrict__ r,
                                                     const double* __restrict__ q, const double* __restrict__ xy,
-                                                    const float* __restrict__ scale,
+                                                    const double* __restrict__ spart, int nblk,
+                                                    float* __restrict__ scale,
                                                     const __nv_bfloat16* __restrict__ W1, const float* __restrict__ b1,
                                                     float* __restrict__ h1, const int* __restrict__ gate) {
     if (gate && *gate > 0) return;   // the solve's judge has switched the network off for now
     __shared__ float w[kHid][8];
     __shared__ float bias[kHid];
-    __shared__ double inv_scale[2];   // one FP64 reciprocal per CTA: this GPU's FP64 divide is slow
+    __shared__ double inv_scale[2];
     for (int e = threadIdx.x; e < kHid * 8; e += blockDim.x) w[e / 8][e % 8] = __bfloat162float(W1[e]);
     for (int e = threadIdx.x; e < kHid; e += blockDim.x) bias[e] = b1[e];
-    if (threadIdx.x < 2) inv_scale[threadIdx.x] = 1.0 / (double)scale[threadIdx.x];
+    if (threadIdx.x < 32) {
+        // the feature scales: RMS of r and of q from the per-block partial sums (the same
+        // sums, in the same order, as the training path's k_mlp_scales_fin); block 0 keeps
+        // them for the output layer
+        double s0 = 0.0, s1 = 0.0;
+        for (int k = threadIdx.x; k < nblk; k += 32) {
+            s0 += spart[2 * k];
+            s1 += spart[2 * k + 1];
+        }
+        s0 = warp_sum(s0);
+        s1 = warp_sum(s1);
+        if (threadIdx.x == 0) {
+            const double sr = sqrt(s0 / n), sq = sqrt(s1 / n);
+            const float f0 = sr > 0.0 ? (float)sr : 1.0f, f1 = sq > 0.0 ? (float)sq : 1.0f;
+            inv_scale[0] = 1.0 / (double)f0;   // one FP64 reciprocal per CTA: this GPU's FP64 divide is slow
+            inv_scale[1] = 1.0 / (double)f1;
+            if (blockIdx.x == 0) {
+                scale[0] = f0;
+                scale[1] = f1;
+            }
+        }
+    }
     __syncthreads();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -277,9 +299,8 @@ int mlp_forward(const MlpBuffers& B, const Level& L, const double* r, const doub
         const double* qb = q + (size_t)b * n;
         float* sc = B.scale + 2 * b;
         k_mlp_scales<<<dim3(kScaleBlocks, 1), kBlock, 0, st>>>(n, rb, qb, B.spart);
-        k_mlp_scales_fin<<<1, 32, 0, st>>>(n, kScaleBlocks, B.spart, sc);
-        k_inf_layer1<<<blocks_for(n, 128), 128, 0, st>>>(n, L.rowptr, L.col, rb, qb, L.xy, sc, B.params_bf + kOffW1,
-                                                         B.params + kOffB1, B.hv, gate);
+        k_inf_layer1<<<blocks_for(n, 128), 128, 0, st>>>(n, L.rowptr, L.col, rb, qb, L.xy, B.spart, kScaleBlocks, sc,
+                                                         B.params_bf + kOffW1, B.params + kOffB1, B.hv, gate);
         k_inf_layer2<<<blocks_for(n, kL2Rows), 256, kL2Smem, st>>>(n, L.rowptr, L.col, B.hv, B.params_bf + kOffW2,
                                                                    B.params + kOffB2, B.m1, gate);
         if (pred)
