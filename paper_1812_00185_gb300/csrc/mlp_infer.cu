@@ -1,9 +1,10 @@
 // Inference of the learned-guess network (not in the paper): the forward pass of mlp.cu's
-// network in five launches, with the one dense contraction (the 64 -> 64 layer) on the tensor
+// network in four launches, with the one dense contraction (the 64 -> 64 layer) on the tensor
 // cores.  The training kernels in mlp.cu keep every activation for the backward pass; this
 // path keeps none and serves the step (batch 1) and cgp_mlp_forward.
 //
-//   scales    s_r, s_q = RMS of r and q (two kernels of mlp.cu, deterministic)
+//   scales    s_r, s_q = RMS of r and q: per-block partial sums (mlp.cu's k_mlp_scales), added
+//             in a fixed order at the start of layer 1 (deterministic)
 //   layer 1   per vertex: f_i = (r_i/s_r, q_i/s_q, x_i, y_i) and the 1-ring mean of f_j, 8 inputs
 //             -> 64 (CUDA cores), h1 = relu(.) stored vertex-major [vertex][64] in FP32
 //   layer 2   per 128-vertex tile: x_i = [h1_i; mean h1_j] (128) gathered into shared memory,

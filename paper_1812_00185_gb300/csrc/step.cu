@@ -895,7 +895,7 @@ CoarsePcgArgs coarse_args(Solver& s) {
 
 // the learned prediction of Phi_c (before the coarse solve, which judges it).  Captured into
 // a graph, the network's launches sit in an IF node whose condition the projection kernel
-// before it sets (`cond`), so while the judge has the network off a step skips its five grids.
+// before it sets (`cond`), so while the judge has the network off a step skips its four grids.
 static int learned_guess(Ctx& c, unsigned long long cond) {
     Solver& s = *c.s;
     if (!(s.prm.guess == CGP_GUESS_LEARNED && s.guess_ready)) return CGP_OK;
@@ -1114,8 +1114,8 @@ int step_post(Ctx& c, bool mass_done) {
     if (p.chi && !mass_done) CGP_TRY(rotational_term(c));
     const bool one_launch = s.coarse_kind != CGP_COARSE_KERNELS;
     const int coarse_fixed = (one_launch ? 1 : 2 + (s.pure_neumann ? 2 : 0)) + (s.proj ? 3 : 0);
-    // the network's five launches, behind the judge's IF node where the on-chip solve judges it
-    const int net = (p.guess == CGP_GUESS_LEARNED && s.guess_ready) ? (s.onchip_bytes ? -5 : 5) : 0;
+    // the network's four launches, behind the judge's IF node where the on-chip solve judges it
+    const int net = (p.guess == CGP_GUESS_LEARNED && s.guess_ready) ? (s.onchip_bytes ? -4 : 4) : 0;
     // mixed: the FP32 copy of A; momentum: kIrSweeps x (residual, inner init, update); each
     // Chebyshev mass solve: kChebSweeps x (residual, init, kChebSteps steps, update)
     const int ir_fixed = mixed ? 1 + 3 * kIrSweeps +
