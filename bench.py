@@ -396,7 +396,8 @@ def run_gpu(args, rank, world):
         transfer = [transfer_bandwidth(cg, torch, n, peak) for n in args.pcg_n if n >= 2048]
     batch = None
     if not args.quick and args.batch > 0:
-        batch = batch_throughput(cg, torch, args.batch, args.batch_steps, 3, args.batch_cluster, args.batch_threads)
+        batch = batch_throughput(cg, torch, args.batch, args.batch_steps, 3, args.batch_cluster, args.batch_threads,
+                                 args.tol_inner)
 
     s.close()
     mesh.close()
@@ -537,7 +538,7 @@ def transfer_bandwidth(cg, torch, n_side, peak):
     return out
 
 
-def batch_throughput(cg, torch, n_inst, steps, warmup, cluster_size=0, threads=0):
+def batch_throughput(cg, torch, n_inst, steps, warmup, cluster_size=0, threads=0, tol_inner=0.0):
     """The batched form: the first n_inst of the 256 seeded uneven lid-driven cavities (sizes
     32^2..256^2 x 2 triangles, Re in [10, 400], 1-3 coarsening levels, dt = 0.005, rotational
     form, mixed precision), advanced by the library's batched step (by default one persistent
@@ -553,7 +554,7 @@ def batch_throughput(cg, torch, n_inst, steps, warmup, cluster_size=0, threads=0
         base = square_mesh(sp["n_fine"] >> sp["k"])
         m = cg.Mesh(base.xy, base.tri, base.tag, sp["k"])
         prm = cg.make_params(sp["Re"], 0.005, chi=1, k=sp["k"], tol_mom=1e-8, tol_poisson=1e-8, tol_mass=1e-10,
-                             precision=cg.CGP_MIXED, bc_kind=cg.CGP_BC_CAVITY)
+                             precision=cg.CGP_MIXED, bc_kind=cg.CGP_BC_CAVITY, tol_inner=tol_inner)
         s = cg.Solver(m, prm)
         meshes.append(m)
         solvers.append(s)
@@ -945,7 +946,7 @@ def main():
         import torch
         from paper_1812_00185_gb300 import binding as cg
         print(json.dumps(batch_throughput(cg, torch, args.batch, args.batch_steps, args.warmup, args.batch_cluster,
-                                          args.batch_threads)), flush=True)
+                                          args.batch_threads, args.tol_inner)), flush=True)
         return 0
     if args.pcg_only:
         if rank != 0:
