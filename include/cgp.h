@@ -110,7 +110,8 @@ typedef struct {
     int32_t bc_kind;           /* CGP_BC_* */
     double bc_param[4];
     int32_t use_graph;         /* 1: replay each step as a CUDA graph with device-side loop control */
-    double tol_inner;          /* CGP_MIXED: residual reduction asked of each FP32 inner solve (0 = 1e-3) */
+    double tol_inner;          /* CGP_MIXED: residual reduction asked of each FP32 inner coarse solve
+                                  (0: 1e-5; 1e-3 for the on-chip solve with Jacobi alone) */
     int32_t coarse_mode;       /* coarse Poisson solver: CGP_COARSE_* */
     int32_t cluster_size;      /* CTAs of the cluster solver (0 = largest that fits, else 2..16) */
     int32_t restrict_mode;     /* CGP_RESTRICT_*: how the right-hand side of Eq. 23 reaches the coarse level */

@@ -385,7 +385,8 @@ extern "C" int cgp_assemble(const cgp_mesh* mesh, const cgp_params* params, void
         cudaStreamCreateWithFlags(&s.branch, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&s.ev_fork, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&s.ev_join, cudaEventDisableTiming) != cudaSuccess ||
-        cudaMallocHost(&s.h_flag, sizeof(int)) != cudaSuccess) {
+        cudaMallocHost(&s.h_flag, sizeof(int)) != cudaSuccess ||
+        cudaMallocHost(&s.h_view, sizeof(Solver::HostView)) != cudaSuccess) {
         set_error("stream / pinned flag creation failed");
         return fail(CGP_ECUDA);
     }
@@ -451,5 +452,6 @@ extern "C" void cgp_solver_destroy(cgp_solver* h) {
     if (s.ev_fork) cudaEventDestroy(s.ev_fork);
     if (s.ev_join) cudaEventDestroy(s.ev_join);
     if (s.h_flag) cudaFreeHost(s.h_flag);
+    if (s.h_view) cudaFreeHost(s.h_view);
     delete h;
 }

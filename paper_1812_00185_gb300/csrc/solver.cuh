@@ -117,6 +117,10 @@ struct Solver {
     cudaGraphExec_t step_exec = nullptr;
     cudaGraph_t step_graph = nullptr;
     int* h_flag = nullptr;        // pinned host word for eager loop control
+    struct HostView {             // pinned host copies of the stats and the time (cgp_get_fields)
+        DeviceStats stats;
+        double t;
+    }* h_view = nullptr;
 };
 
 // Optional per-launch timing: every kernel launch of an eager step is bracketed by

@@ -235,6 +235,14 @@ __global__ void __launch_bounds__(kBlock) k_div(SellView A, const double* __rest
     }
 }
 
+// a new state's time (a kernel argument: no host staging) and zeroed run statistics
+__global__ void k_set_time(double* tdev, double t, DeviceStats* stats) {
+    static_assert(sizeof(DeviceStats) % sizeof(int64_t) == 0, "stats are zeroed as 64-bit words");
+    int64_t* w = reinterpret_cast<int64_t*>(stats);
+    for (int i = threadIdx.x; i < (int)(sizeof(DeviceStats) / sizeof(int64_t)); i += blockDim.x) w[i] = 0;
+    if (threadIdx.x == 0) *tdev = t;
+}
+
 // end of step: U^{n-1} <- U^n, U^{n+1} = U~ + delta (Eq. 25), P^{n+1} = P^n + phi_f - chi/Re q (Eq. 26)
 __global__ void k_finish(int nf, double* __restrict__ U, double* __restrict__ Uprev, const double* __restrict__ Ut,
                          const double* __restrict__ delta, double* __restrict__ P, const double* __restrict__ phi,
@@ -863,6 +871,16 @@ int choose_coarse_solver(Solver& s, cudaStream_t st) {
 
 // ---------------------------------------------------------------- pieces of a step
 // arguments of the one-launch coarse solver for this solver's current state
+// Reduction asked of each FP32 inner coarse solve when tol_inner is left at 0: 1e-5 (about
+// two refinement sweeps a solve) for the on-chip solve with the subdomain coarse correction
+// and for the Jacobi solves of the cluster and batched forms; 1e-3 for the on-chip solve
+// with Jacobi alone, whose FP32 recurrence stagnates before 1e-5 on its larger condition
+// number and then wastes its stagnation window at every restart.
+static double inner_tol_of(const Solver& s, bool onchip_solve) {
+    if (s.prm.tol_inner > 0) return s.prm.tol_inner;
+    return onchip_solve && !s.onchip.nsub ? 1e-3 : 1e-5;
+}
+
 CoarsePcgArgs coarse_args(Solver& s) {
     const Level& C = s.mesh->lev[s.lc];
     CoarsePcgArgs a;
@@ -879,7 +897,7 @@ CoarsePcgArgs coarse_args(Solver& s) {
     a.mlump = s.pure_neumann ? s.mlumpC : nullptr;
     a.st = &s.ks[KS_POIS];
     a.tol2 = s.prm.tol_poisson * s.prm.tol_poisson;
-    a.inner_tol = s.prm.tol_inner > 0 ? s.prm.tol_inner : 1e-3;
+    a.inner_tol = inner_tol_of(s, s.onchip_bytes != 0);
     a.maxit = s.prm.max_it_poisson;
     a.zero_x = s.prm.guess == CGP_GUESS_ZERO;
     a.project = s.pure_neumann;
@@ -1201,6 +1219,7 @@ size_t coarse_args_size() { return sizeof(CoarsePcgArgs); }
 
 void fill_coarse_args(Solver& s, void* dst) {
     CoarsePcgArgs a = coarse_args(s);
+    a.inner_tol = inner_tol_of(s, false);   // the batched solve is the cluster Jacobi PCG
     memcpy(dst, &a, sizeof(a));
 }
 
@@ -1292,6 +1311,7 @@ void fill_batch_step_args(Solver& s, void* dst) {
     a.cxy = C.xy;
     a.ctag = C.tag;
     a.coarse = coarse_args(s);
+    a.coarse.inner_tol = inner_tol_of(s, false);   // the whole-step kernel's coarse PCG is Jacobi
     a.pure_neumann = s.pure_neumann;
     a.nlev = s.lf - s.lc + 1;
     for (int l = 0; l < a.nlev; ++l) {
@@ -1456,11 +1476,12 @@ extern "C" int cgp_get_fields(cgp_solver* h, double* U, double* P, double* t, cg
     cudaStream_t st = (cudaStream_t)stream;
     if (U) CGP_TRY(copy_out(U, s.U, sizeof(double) * 2 * s.nf, where, st));
     if (P) CGP_TRY(copy_out(P, s.P, sizeof(double) * s.nf, where, st));
-    DeviceStats ds;
-    double th = 0.0;
-    CGP_CUDA(cudaMemcpyAsync(&ds, s.stats, sizeof(ds), cudaMemcpyDeviceToHost, st));
-    CGP_CUDA(cudaMemcpyAsync(&th, s.tdev, sizeof(double), cudaMemcpyDeviceToHost, st));
+    // stats and time land in pinned host memory (no staged pageable copies)
+    CGP_CUDA(cudaMemcpyAsync(&s.h_view->stats, s.stats, sizeof(DeviceStats), cudaMemcpyDeviceToHost, st));
+    CGP_CUDA(cudaMemcpyAsync(&s.h_view->t, s.tdev, sizeof(double), cudaMemcpyDeviceToHost, st));
     CGP_CUDA(cudaStreamSynchronize(st));
+    const DeviceStats ds = s.h_view->stats;
+    const double th = s.h_view->t;
     if (t) *t = th;
     if (stats) {
         stats->steps = ds.steps;
@@ -1495,8 +1516,8 @@ extern "C" int cgp_set_fields(cgp_solver* h, const double* U, const double* Upre
     CGP_TRY(copy_in(s.U, U, sizeof(double) * 2 * s.nf, where, st));
     CGP_TRY(copy_in(s.Uprev, Uprev ? Uprev : U, sizeof(double) * 2 * s.nf, where, st));
     CGP_TRY(copy_in(s.P, P, sizeof(double) * s.nf, where, st));
-    CGP_CUDA(cudaMemcpyAsync(s.tdev, &t, sizeof(double), cudaMemcpyHostToDevice, st));
-    CGP_CUDA(cudaMemsetAsync(s.stats, 0, sizeof(DeviceStats), st));
+    k_set_time<<<1, 32, 0, st>>>(s.tdev, t, s.stats);
+    CGP_LAUNCH_CHECK();
     CGP_CUDA(cudaStreamSynchronize(st));
     return CGP_OK;
 }
