@@ -155,11 +155,148 @@ class ClockSampler:
                 if v.lower() == "active":
                     reasons.add(n)
         out = {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
-               "reasons": sorted(reasons), "samples": len(sm)}
+               "reasons": sorted(reasons), "samples": len(sm), "source": "nvidia-smi"}
         if self.t0 is not None and self.t1 is not None:
             out["window_ms"] = round(1000.0 * (self.t1 - self.t0), 1)
             out["interval_ms"] = round(1000.0 * self.interval)
         return out
+
+
+class NvmlClockSampler:
+    """SM clock and clock-event reasons read through NVML (the driver's management library,
+    by ctypes) every `interval_ms` in a thread, so a timed region of ~100 ms still holds tens
+    of samples.  Same interface and summary as ClockSampler; `ok` is False when NVML cannot
+    be loaded or the device not found (the caller then falls back to nvidia-smi).  Only
+    reads: no setting of the GPU is touched."""
+
+    # bits of nvmlDeviceGetCurrentClocksEventReasons (NVML's public header)
+    BITS = {"sw_power_cap": 0x4, "hw_slowdown": 0x8, "sw_thermal_slowdown": 0x20, "hw_thermal_slowdown": 0x40}
+    CLOCK_SM = 1
+
+    def __init__(self, device, interval_ms=5, lib=None):
+        self.device = device
+        self.interval = interval_ms / 1000.0
+        self.lib = lib
+        self.ok = False
+        self.samples = []          # (unix time, sm MHz, reason bits)
+        self.max_mhz = None
+        self.t0 = self.t1 = None
+        self._done = threading.Event()
+        self._thread = None
+        self._inited = False
+
+    @staticmethod
+    def _bus_id(device):
+        try:
+            import torch
+            p = torch.cuda.get_device_properties(device)
+            return "%08X:%02X:%02X.0" % (p.pci_domain_id, p.pci_bus_id, p.pci_device_id)
+        except Exception:
+            return None
+
+    def __enter__(self):
+        import ctypes
+        try:
+            nv = self.lib or ctypes.CDLL("libnvidia-ml.so.1")
+            if nv.nvmlInit_v2() != 0:
+                return self
+            self.nv = nv
+            self._inited = True
+            h = ctypes.c_void_p()
+            bus = self._bus_id(self.device)
+            rc = nv.nvmlDeviceGetHandleByPciBusId_v2(bus.encode(), ctypes.byref(h)) if bus else 1
+            if rc != 0:
+                rc = nv.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(int(self.device)), ctypes.byref(h))
+            if rc != 0:
+                return self
+            self.h = h
+            self.reasons = getattr(nv, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+                nv.nvmlDeviceGetCurrentClocksThrottleReasons
+            mx = ctypes.c_uint()
+            if nv.nvmlDeviceGetMaxClockInfo(h, self.CLOCK_SM, ctypes.byref(mx)) == 0:
+                self.max_mhz = float(mx.value)
+            if self._sample() is None:
+                return self
+        except Exception:
+            return self
+        self.ok = True
+        self._thread = threading.Thread(target=self._run, daemon=True)
+        self._thread.start()
+        return self
+
+    def _sample(self):
+        import ctypes
+        c, r = ctypes.c_uint(), ctypes.c_ulonglong()
+        if self.nv.nvmlDeviceGetClockInfo(self.h, self.CLOCK_SM, ctypes.byref(c)) != 0:
+            return None
+        if self.reasons(self.h, ctypes.byref(r)) != 0:
+            return None
+        s = (time.time(), float(c.value), int(r.value))
+        self.samples.append(s)
+        return s
+
+    def _run(self):
+        while not self._done.wait(self.interval):
+            if self._sample() is None:
+                break
+
+    def start(self):
+        self.t0 = time.time()
+
+    def stop(self):
+        self.t1 = time.time()
+        end = self.t1 + 4 * self.interval + 0.5
+        while self.ok and not any(ts >= self.t1 for ts, _, _ in self.samples) and time.time() < end:
+            time.sleep(self.interval / 4)
+
+    def __exit__(self, *a):
+        self._done.set()
+        if self._thread is not None:
+            self._thread.join(timeout=2.0)
+        if self._inited:
+            self._inited = False
+            try:
+                self.nv.nvmlShutdown()
+            except Exception:
+                pass
+
+    def window(self):
+        """Samples between start() and stop(), else the first one after start()."""
+        rows = list(self.samples)
+        if self.t0 is None or self.t1 is None:
+            return rows
+        inside = [r for r in rows if self.t0 <= r[0] <= self.t1]
+        return inside or [r for r in rows if r[0] >= self.t0][:1]
+
+    def summary(self):
+        rows = self.window()
+        sm = [r[1] for r in rows]
+        reasons = sorted({n for _, _, bits in rows for n, b in self.BITS.items() if bits & b})
+        out = {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": self.max_mhz,
+               "reasons": reasons, "samples": len(sm), "source": "nvml"}
+        if self.t0 is not None and self.t1 is not None:
+            out["window_ms"] = round(1000.0 * (self.t1 - self.t0), 1)
+            out["interval_ms"] = round(1000.0 * self.interval)
+        return out
+
+
+class clock_sampler:
+    """NVML sampling where the library loads, else nvidia-smi (ClockSampler)."""
+
+    def __init__(self, device):
+        self.device = device
+        self.s = None
+
+    def __enter__(self):
+        s = NvmlClockSampler(self.device).__enter__()
+        if not s.ok:
+            s.__exit__()
+            s = ClockSampler(self.device).__enter__()
+        self.s = s
+        return s
+
+    def __exit__(self, *a):
+        return self.s.__exit__(*a)
 
 
 def workload_problem(name):
@@ -239,7 +376,7 @@ def run_gpu(args, rank, world):
             cg.cgp_guess_set(s.handle, learned["net"])
         torch.cuda.synchronize()
         t_asm = time.time() - t0
-        with ClockSampler(dev) as clk:
+        with clock_sampler(dev) as clk:
             s.step(warmup)
             U0, P0, t0_sim, st0, _ = s.fields()
             # state at the start of the timed region (fields and the previous increment the coarse guess uses)

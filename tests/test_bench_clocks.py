@@ -1,7 +1,8 @@
-"""The bench's clock record keeps the nvidia-smi samples taken inside the timed region.
+"""The bench's clock record keeps the samples taken inside the timed region.
 
-A fake nvidia-smi (a Python script printing the same CSV fields, timestamp first) stands
-in for the real one, so this runs on the CPU."""
+A fake nvidia-smi (a Python script printing the same CSV fields, timestamp first) and a
+fake NVML (the calls the NVML sampler makes) stand in for the real ones, so this runs on
+the CPU."""
 
 import sys
 import textwrap
@@ -60,3 +61,88 @@ def test_missing_tool_gives_an_empty_record():
         clk.stop()
     s = clk.summary()
     assert s["samples"] == 0 and s["sm_mhz"] is None and s["reasons"] == []
+
+
+class FakeNvml:
+    """Stands in for libnvidia-ml: the calls the NVML sampler makes, by ctypes convention
+    (results written through byref arguments, 0 = success)."""
+
+    def __init__(self, reasons=0x4, init_rc=0):
+        self.n = 0
+        self.reason_bits = reasons
+        self.init_rc = init_rc
+        self.shut = False
+
+    def nvmlInit_v2(self):
+        return self.init_rc
+
+    def nvmlShutdown(self):
+        self.shut = True
+        return 0
+
+    def nvmlDeviceGetHandleByPciBusId_v2(self, bus, h):
+        h._obj.value = 1
+        return 0
+
+    def nvmlDeviceGetHandleByIndex_v2(self, i, h):
+        h._obj.value = 1
+        return 0
+
+    def nvmlDeviceGetMaxClockInfo(self, h, kind, out):
+        out._obj.value = 2070
+        return 0
+
+    def nvmlDeviceGetClockInfo(self, h, kind, out):
+        assert kind == 1   # the SM clock
+        out._obj.value = 1965 if self.n % 2 else 1995
+        self.n += 1
+        return 0
+
+    def nvmlDeviceGetCurrentClocksEventReasons(self, h, out):
+        out._obj.value = self.reason_bits
+        return 0
+
+
+def test_nvml_samples_inside_the_window():
+    nv = FakeNvml()
+    with bench.NvmlClockSampler(0, interval_ms=5, lib=nv) as clk:
+        assert clk.ok
+        time.sleep(0.05)                 # samples before the region are dropped
+        clk.start()
+        time.sleep(0.2)
+        clk.stop()
+    s = clk.summary()
+    assert 15 <= s["samples"] <= 60, s
+    assert s["sm_mhz"] in (1965.0, 1980.0, 1995.0) and s["sm_max_mhz"] == 2070.0
+    assert s["reasons"] == ["sw_power_cap"] and s["source"] == "nvml"
+    assert all(clk.t0 <= r[0] <= clk.t1 for r in clk.window())
+    assert nv.shut
+
+
+def test_nvml_reason_bits_map_to_names():
+    with bench.NvmlClockSampler(0, interval_ms=5, lib=FakeNvml(reasons=0x8 | 0x40 | 0x1)) as clk:
+        clk.start()
+        time.sleep(0.03)
+        clk.stop()
+    assert clk.summary()["reasons"] == ["hw_slowdown", "hw_thermal_slowdown"]
+
+
+def test_nvml_failure_is_reported_not_raised():
+    with bench.NvmlClockSampler(0, lib=FakeNvml(init_rc=1)) as clk:
+        assert not clk.ok
+        clk.start()
+        clk.stop()
+    assert clk.summary()["samples"] == 0
+
+
+def test_sampler_falls_back_to_nvidia_smi_without_nvml(monkeypatch):
+    class NoNvml(bench.NvmlClockSampler):
+        def __init__(self, device):
+            super().__init__(device, lib=FakeNvml(init_rc=1))
+    monkeypatch.setattr(bench, "NvmlClockSampler", NoNvml)
+    monkeypatch.setattr(bench.ClockSampler, "_command", lambda self, ms: [sys.executable, "-c", "pass"])
+    with bench.clock_sampler(0) as clk:
+        assert isinstance(clk, bench.ClockSampler)
+        clk.start()
+        clk.stop()
+    assert clk.summary()["source"] == "nvidia-smi"
