@@ -93,13 +93,39 @@ __global__ void __launch_bounds__(kBlock) k_coarse_rhs(SellView Ac, const double
                                                       double* __restrict__ rc, KrylovState* st, int pure_neumann,
                                                       double* partials, unsigned int* ticket) {
     const int lane = threadIdx.x & 31;
+    const double2* __restrict__ U2 = reinterpret_cast<const double2*>(Ut);
     double acc[1] = {0.0};
     CGP_SLICE_LOOP(Ac, sl) {
         const int i = sl * 32 + lane;
-        double sx[1] = {0.0}, sy[1] = {0.0};
-        sell_accum<1>(Ac, Cxc, sl, lane, [&](int j, double (&o)[1]) { o[0] = Ut[2 * j]; }, sx);
-        sell_accum<1>(Ac, Cyc, sl, lane, [&](int j, double (&o)[1]) { o[0] = Ut[2 * j + 1]; }, sy);
-        const double s = sx[0] + sy[0];
+        // Cx and Cy share the coarse pattern: one pass reads each column index once and
+        // gathers (u~, v~) of a column as one 16-byte load; each of the two sums keeps the
+        // entry order of a row
+        const int base = __ldg(Ac.ptr + sl), w = (__ldg(Ac.ptr + sl + 1) - base) >> 5;
+        double sx = 0.0, sy = 0.0;
+        for (int k0 = 0; k0 < w; k0 += 8) {
+            int cj[8];
+            double ax[8], ay[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                cj[u] = 0;
+                ax[u] = ay[u] = 0.0;
+                if (k0 + u < w) {
+                    const int e = base + 32 * (k0 + u) + lane;
+                    cj[u] = __ldg(Ac.col + e);
+                    ax[u] = __ldg(Cxc + e);
+                    ay[u] = __ldg(Cyc + e);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                if (k0 + u < w) {
+                    const double2 uv = U2[cj[u]];
+                    sx += ax[u] * uv.x;
+                    sy += ay[u] * uv.y;
+                }
+            }
+        }
+        const double s = sx + sy;
         if (i < Ac.n) {
             double r = (tag[i] & CGP_PHI_ZERO) ? 0.0 : -1.5 / dt * s;
             rc[i] = r;
