@@ -896,7 +896,6 @@ int choose_coarse_solver(Solver& s, cudaStream_t st) {
 }
 
 // ---------------------------------------------------------------- pieces of a step
-// arguments of the one-launch coarse solver for this solver's current state
 // Reduction asked of each FP32 inner coarse solve when tol_inner is left at 0: 1e-5 (about
 // two refinement sweeps a solve) for the on-chip solve with the subdomain coarse correction
 // and for the Jacobi solves of the cluster and batched forms; 1e-3 for the on-chip solve
@@ -907,6 +906,7 @@ static double inner_tol_of(const Solver& s, bool onchip_solve) {
     return onchip_solve && !s.onchip.nsub ? 1e-3 : 1e-5;
 }
 
+// arguments of the one-launch coarse solver for this solver's current state
 CoarsePcgArgs coarse_args(Solver& s) {
     const Level& C = s.mesh->lev[s.lc];
     CoarsePcgArgs a;
